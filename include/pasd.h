@@ -1,0 +1,196 @@
+/*
+ * pasd.h - C ABI of the GB300 (sm_103a) PASD solver for tensor robust PCA.
+ *
+ * The method is Parallel Active Subspace Decomposition (Jiang & Ng, arXiv
+ * 1712.09999): split an observed N-way tensor T into a low-rank part X and a
+ * sparse part E (Eq. 1), by running the ADMM of Algorithm 1 on the
+ * reformulation of Eq. 3, in which every mode-n unfolding of the low-rank part
+ * is U_n V_n with U_n an I_n x R_n column-orthonormal "active subspace" and V_n
+ * a small R_n x prod_{m!=n} I_m factor.
+ *
+ * Conventions shared by every entry point
+ *  - Tensors are dense float32 in C order (the last index is contiguous),
+ *    D = prod_n I_n elements, addressed by plain device pointers that the
+ *    caller owns. Unless an entry point says otherwise, pointers are DEVICE
+ *    pointers on the device the context was created for.
+ *  - Streams are passed as `void*` holding a cudaStream_t (NULL = the legacy
+ *    default stream). Work is enqueued on that stream; entry points that say
+ *    "synchronous" also wait for it.
+ *  - Every entry point returns a pasd_status; nothing throws across the ABI.
+ *    On failure a human-readable reason is available from pasd_last_error()
+ *    (thread-local, valid until the next call on the same thread).
+ *  - The library owns all solver state (U_n, V_n in factored form, E, the
+ *    multipliers, workspaces); the caller owns T, L and E.
+ */
+#ifndef PASD_H
+#define PASD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PASD_OK = 0,               /* converged (stop rule met)                          */
+    PASD_PENDING = 1,          /* served solve still running (pasd_poll only)        */
+    PASD_NOT_CONVERGED = 2,    /* max_iter loop bodies ran without meeting the rule  */
+    PASD_ERR_INVALID_ARG = -1, /* bad parameters, shapes or pointers                 */
+    PASD_ERR_OOM = -2,         /* device allocation failed or HBM budget exceeded    */
+    PASD_ERR_CUDA = -3,        /* a CUDA runtime call failed                         */
+    PASD_ERR_NONFINITE = -4,   /* a NaN/Inf appeared in the iterate                  */
+    PASD_ERR_TIMEOUT = -5,     /* a bounded wait ran out                             */
+    PASD_ERR_BUSY = -6,        /* the submit queue is full                           */
+    PASD_ERR_UNKNOWN_TICKET = -7,
+    PASD_ERR_UNSUPPORTED = -8  /* shape/rank outside the built kernels' limits       */
+} pasd_status;
+
+typedef enum {
+    PASD_PREC_FP32 = 0,   /* FP32 storage and arithmetic on the hot path            */
+    PASD_PREC_MIXED = 1   /* BF16 split hi+lo products, FP32 accumulation, then a
+                             closing run of FP32 iterations                         */
+} pasd_precision;
+
+typedef enum {
+    PASD_STOP_INF_ABS = 0,     /* Algorithm 1: max_n ||T - Z_n - E||_inf < tol        */
+    PASD_STOP_FRO_REL = 1,     /* max_n ||T - Z_n - E||_F / ||T||_F < tol             */
+    PASD_STOP_FIXED_ITERS = 2  /* run exactly max_iter loop bodies                    */
+} pasd_stop;
+
+#define PASD_MAX_ORDER 8
+#define PASD_MAX_RANK 64
+
+/* Problem statement (Eq. 1 / Eq. 3 and the inputs of Algorithm 1).
+ * A zero in an optional field selects the paper's default. */
+typedef struct {
+    int32_t order;                        /* N >= 2                                    */
+    int64_t dims[PASD_MAX_ORDER];         /* I_1..I_N (C order)                        */
+    int32_t rank_bound[PASD_MAX_ORDER];   /* R_n, 1 <= R_n <= min(I_n, PASD_MAX_RANK)   */
+    double alpha[PASD_MAX_ORDER];         /* output weights alpha_n > 0; 0 -> 1/N       */
+    double lambda;                        /* > 0: lambda_n = alpha_n / lambda          */
+    double lambda_n[PASD_MAX_ORDER];      /* used when lambda <= 0: per-mode nuclear
+                                             weights; 0 -> sqrt(max(I_n, D/I_n)) / N   */
+    double mu0;                           /* 0 -> 1e-4                                  */
+    double mu_max;                        /* 0 -> 1e10                                  */
+    double rho;                           /* 0 -> 1.1 (must be > 1)                     */
+    double tol;                           /* 0 -> 1e-5                                  */
+    int32_t stop_rule;                    /* pasd_stop                                  */
+    int32_t max_iter;                     /* 0 -> 1000                                  */
+    int32_t precision;                    /* pasd_precision                             */
+    int32_t check_every;                  /* loop bodies between host reads of the
+                                             device stop flag; 0 -> 8                  */
+    uint32_t flags;                       /* reserved, must be 0                        */
+} pasd_params;
+
+typedef struct {
+    int32_t status;                       /* pasd_status of the solve                  */
+    int32_t iters;                        /* completed loop bodies                     */
+    double res_inf;                       /* max_n ||T - Z_n - E||_inf at exit         */
+    double res_fro_rel;                   /* max_n ||T - Z_n - E||_F / ||T||_F         */
+    double objective;                     /* sum_n lambda_n ||V_n||_* + ||E||_1 (Eq. 3)*/
+    double nuclear[PASD_MAX_ORDER];       /* ||V_n||_*                                 */
+    double l1_E;                          /* ||E||_1                                    */
+    double mu_final;                      /* mu after the last loop body               */
+    int32_t kept[PASD_MAX_ORDER];         /* singular values kept by the last SVT      */
+    double latency_s;                     /* served solves: submit -> retire, seconds  */
+} pasd_result;
+
+typedef struct pasd_ctx pasd_ctx;
+typedef struct pasd_plan pasd_plan_t;
+
+/* Context on one CUDA device. `hbm_budget_bytes` bounds the summed footprint
+ * of the solver state the served path keeps resident (0 -> 90% of free HBM).
+ * Creates the served-path scheduler thread lazily on the first pasd_submit. */
+pasd_status pasd_ctx_create(int device, size_t hbm_budget_bytes, pasd_ctx** out);
+/* Waits for served solves still in flight, then frees everything. */
+pasd_status pasd_ctx_destroy(pasd_ctx* ctx);
+
+/* Fills `p` with the paper's defaults (Algorithm 1 initialisation and the
+ * Sec. 5.1 settings: mu0 = 1e-4, mu_max = 1e10, rho = 1.1, tol = 1e-5,
+ * max_iter = 1000, lambda_n = sqrt(max(I_n, prod_{m!=n} I_m)) / N, alpha_n = 1/N)
+ * for a tensor of `order` modes with sizes `dims` and rank bounds `ranks`. */
+pasd_status pasd_params_default(pasd_params* p, int32_t order, const int64_t* dims,
+                                const int32_t* ranks);
+
+/* Validates the problem and lays out the solver state for it. Allocates no
+ * device memory (that happens on first use); `footprint_bytes` (may be NULL)
+ * receives the device bytes the state will take. Errors: INVALID_ARG when
+ * N < 2, any R_n > I_n (the Stiefel set St(I_n, R_n) is empty) or R_n < 1,
+ * a weight <= 0, rho <= 1 or mu_max < mu0; UNSUPPORTED when R_n > PASD_MAX_RANK. */
+pasd_status pasd_plan(pasd_ctx* ctx, const pasd_params* p, pasd_plan_t** out,
+                      size_t* footprint_bytes);
+pasd_status pasd_plan_destroy(pasd_plan_t* plan);
+
+/* Algorithm 1 end to end, synchronous on `stream`: initialise, iterate until
+ * the stop rule or max_iter, then write the output X = sum_n alpha_n Z_n /
+ * sum_n alpha_n into L and the sparse part into E (both D floats, device).
+ * L and E are written only when the result is PASD_OK or PASD_NOT_CONVERGED.
+ * T must stay valid and unchanged until the call returns. */
+pasd_status pasd_solve(pasd_plan_t* plan, const float* T, float* L, float* E,
+                       pasd_result* result, void* stream);
+
+/* Same as pasd_solve, but T, L and E are HOST buffers (D floats each); the
+ * host<->device copies are part of the call. */
+pasd_status pasd_solve_host(pasd_plan_t* plan, const float* T_host, float* L_host,
+                            float* E_host, pasd_result* result, void* stream);
+
+/* Served path (continuous batching). Queues one solve of `plan` on device
+ * tensors T, L, E; the caller keeps them alive and untouched until pasd_poll
+ * returns something other than PASD_PENDING. A solve is admitted when its
+ * plan's footprint fits the context's HBM budget; admitted solves advance
+ * together, each on its own stream, and retire as they converge.
+ * One plan serves one solve at a time. Errors: BUSY when the queue is full. */
+pasd_status pasd_submit(pasd_ctx* ctx, pasd_plan_t* plan, const float* T, float* L,
+                        float* E, uint64_t* ticket);
+/* PASD_PENDING while the solve is queued or running; otherwise its final
+ * status, with `out` filled (out may be NULL). A ticket can be polled to
+ * completion once; afterwards it is UNKNOWN_TICKET. */
+pasd_status pasd_poll(pasd_ctx* ctx, uint64_t ticket, pasd_result* out);
+
+/* Stepwise form of pasd_solve (asynchronous on `stream`):
+ *   pasd_begin   - Algorithm 1 initialisation for observation T (device);
+ *   pasd_iterate - enqueue `iters` loop bodies; bodies after the stop rule
+ *                  holds are skipped on the device;
+ *   pasd_finish  - write L and E (device) and fill `result` (synchronous). */
+pasd_status pasd_begin(pasd_plan_t* plan, const float* T, void* stream);
+pasd_status pasd_iterate(pasd_plan_t* plan, int32_t iters, void* stream);
+pasd_status pasd_finish(pasd_plan_t* plan, float* L, float* E, pasd_result* result,
+                        void* stream);
+
+/* Read-only export of solver state to HOST memory (synchronous on `stream`),
+ * for inspection and testing. `mode` selects n for per-mode items.
+ *   PASD_STATE_U      U_n                      I_n x R_n       float32 (row-major)
+ *   PASD_STATE_A      U_n^T G_n (SVT argument)  R_n x P_n       float32, column order of
+ *                     the unfolding = C order over the other modes
+ *   PASD_STATE_W      eigenvectors of A_n A_n^T, columns by descending eigenvalue,
+ *                                              R_n x R_n       float32
+ *   PASD_STATE_SIGMA  singular values of A_n    R_n            float32, descending
+ *   PASD_STATE_F      SVT factors max(1 - tau/sigma, 0)  R_n   float32
+ *   PASD_STATE_E      E                        D              float32
+ *   PASD_STATE_Y      multiplier Y_n           D              float32
+ *   PASD_STATE_MU     mu (current)             1              float64
+ *   PASD_STATE_KEPT   kept count per mode      N              int32
+ *   PASD_STATE_TRACE  per-iteration records    iters x PASD_TRACE_STRIDE float64:
+ *                     [k, res_inf, res_fro_rel, objective, mu_used, kept_1..kept_8]
+ * V_n = W diag(F) W^T A_n and Z_n = fold_n(U_n V_n). `bytes` must equal the
+ * item's size (TRACE: a multiple of the record size, at most iters records). */
+enum {
+    PASD_STATE_U = 0, PASD_STATE_A = 1, PASD_STATE_W = 2, PASD_STATE_SIGMA = 3,
+    PASD_STATE_F = 4, PASD_STATE_E = 5, PASD_STATE_Y = 6, PASD_STATE_MU = 7,
+    PASD_STATE_KEPT = 8, PASD_STATE_TRACE = 9
+};
+#define PASD_TRACE_STRIDE 13
+pasd_status pasd_state_get(pasd_plan_t* plan, int32_t item, int32_t mode, void* dst_host,
+                           size_t bytes, void* stream);
+
+/* Number of kernel launches the last pasd_iterate enqueued per loop body. */
+int32_t pasd_launches_per_iter(const pasd_plan_t* plan);
+
+const char* pasd_status_string(pasd_status s);
+const char* pasd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PASD_H */

@@ -1,0 +1,743 @@
+// Host runtime behind include/pasd.h: contexts, plans (layout + lazy device
+// arena), the per-iteration CUDA graph, the synchronous solve loop, the
+// served path (continuous batching over per-solve streams) and state export.
+#include "../../include/pasd.h"
+#include "pasd_impl.cuh"
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+using namespace pasd;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static pasd_status fail(pasd_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+#define CUDA_TRY(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? PASD_ERR_OOM : PASD_ERR_CUDA,  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));             \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// structures
+// ---------------------------------------------------------------------------
+struct Job {
+    uint64_t ticket;
+    pasd_plan_t* plan;
+    const float* T;
+    float* L;
+    float* E;
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+struct pasd_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    size_t hbm_budget = 0;
+    // served path
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Job> queue;
+    std::map<uint64_t, pasd_result> done;
+    std::map<uint64_t, int> state;   // 0 queued, 1 running
+    std::thread worker;
+    bool worker_started = false;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    size_t max_queue = 4096;
+};
+
+struct pasd_plan {
+    pasd_ctx* ctx = nullptr;
+    pasd_params p{};
+    int N = 0;
+    int64_t D = 0;
+    ModeGeom m[PASD_MAXN];
+    double lam[PASD_MAXN];
+    double alpha[PASD_MAXN];
+    FusedGeom fg{};
+    int ncta_ap[PASD_MAXN];
+    int n_mp[PASD_MAXN];
+    size_t footprint = 0;
+    // device arena
+    char* arena = nullptr;
+    DevScalars* sc = nullptr;
+    float *E = nullptr, *G[PASD_MAXN], *A[PASD_MAXN], *U[PASD_MAXN], *Wz[PASD_MAXN];
+    float *W[PASD_MAXN], *F[PASD_MAXN], *sigma[PASD_MAXN];
+    float *gram[PASD_MAXN], *mp[PASD_MAXN], *scratch[PASD_MAXN];
+    float *part = nullptr, *sq_part = nullptr;
+    int32_t* kept = nullptr;
+    double* trace = nullptr;
+    float* dev_io = nullptr;     // staging for pasd_solve_host: T, L, E
+    float* y_tmp = nullptr;
+    // launch descriptors
+    SmallArgs small{};
+    ApassArgs ap[PASD_MAXN];
+    FusedArgs fu{};
+    FinalizeArgs fin{};
+    // graph
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool use_graph = true;
+    DevScalars* host_sc = nullptr;   // pinned mirror
+    cudaStream_t own_stream = nullptr;   // served path
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+};
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" pasd_status pasd_ctx_create(int device, size_t hbm_budget_bytes, pasd_ctx** out) {
+    if (!out) return fail(PASD_ERR_INVALID_ARG, "out is NULL");
+    int count = 0;
+    CUDA_TRY(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) return fail(PASD_ERR_INVALID_ARG, "no such device");
+    CUDA_TRY(cudaSetDevice(device));
+    pasd_ctx* c = new pasd_ctx();
+    c->device = device;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) { delete c; return fail(PASD_ERR_CUDA, cudaGetErrorString(e)); }
+    c->num_sms = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    c->hbm_budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+    *out = c;
+    return PASD_OK;
+}
+
+static void worker_main(pasd_ctx* c);
+
+extern "C" pasd_status pasd_ctx_destroy(pasd_ctx* c) {
+    if (!c) return fail(PASD_ERR_INVALID_ARG, "ctx is NULL");
+    {
+        std::unique_lock<std::mutex> lk(c->mu);
+        c->stop = true;
+    }
+    c->cv.notify_all();
+    if (c->worker.joinable()) c->worker.join();
+    delete c;
+    return PASD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// params and plan
+// ---------------------------------------------------------------------------
+extern "C" pasd_status pasd_params_default(pasd_params* p, int32_t order, const int64_t* dims,
+                                           const int32_t* ranks) {
+    if (!p || !dims || !ranks) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    if (order < 2 || order > PASD_MAX_ORDER) return fail(PASD_ERR_INVALID_ARG, "order out of range");
+    std::memset(p, 0, sizeof(*p));
+    p->order = order;
+    for (int n = 0; n < order; ++n) { p->dims[n] = dims[n]; p->rank_bound[n] = ranks[n]; }
+    p->mu0 = 1e-4; p->mu_max = 1e10; p->rho = 1.1; p->tol = 1e-5; p->max_iter = 1000;
+    p->stop_rule = PASD_STOP_INF_ABS; p->precision = PASD_PREC_FP32; p->check_every = 8;
+    return PASD_OK;
+}
+
+static int rank_bucket(int R) {
+    static const int b[] = {4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64};
+    for (int v : b) if (R <= v) return v;
+    return -1;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_t** out,
+                                 size_t* footprint_bytes) {
+    if (!c || !pin || !out) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    pasd_params p = *pin;
+    const int N = p.order;
+    if (N < 2 || N > PASD_MAX_ORDER) return fail(PASD_ERR_INVALID_ARG, "order must be in [2, 8]");
+    int64_t D = 1;
+    for (int n = 0; n < N; ++n) {
+        if (p.dims[n] < 1) return fail(PASD_ERR_INVALID_ARG, "dims must be >= 1");
+        if (p.rank_bound[n] < 1) return fail(PASD_ERR_INVALID_ARG, "rank bound must be >= 1");
+        if (p.rank_bound[n] > p.dims[n])
+            return fail(PASD_ERR_INVALID_ARG, "rank bound R_n > I_n: St(I_n, R_n) is empty");
+        if (p.rank_bound[n] > PASD_MAX_RANK)
+            return fail(PASD_ERR_UNSUPPORTED, "rank bound above PASD_MAX_RANK");
+        D *= p.dims[n];
+    }
+    if (p.mu0 == 0) p.mu0 = 1e-4;
+    if (p.mu_max == 0) p.mu_max = 1e10;
+    if (p.rho == 0) p.rho = 1.1;
+    if (p.tol == 0) p.tol = 1e-5;
+    if (p.max_iter == 0) p.max_iter = 1000;
+    if (p.check_every <= 0) p.check_every = 8;
+    if (!(p.mu0 > 0) || !(p.rho > 1) || !(p.mu_max >= p.mu0) || !(p.tol > 0) || p.max_iter < 1)
+        return fail(PASD_ERR_INVALID_ARG, "need mu0 > 0, rho > 1, mu_max >= mu0, tol > 0, max_iter >= 1");
+    if (p.stop_rule < 0 || p.stop_rule > 2) return fail(PASD_ERR_INVALID_ARG, "bad stop rule");
+    if (p.precision != PASD_PREC_FP32 && p.precision != PASD_PREC_MIXED)
+        return fail(PASD_ERR_INVALID_ARG, "bad precision");
+    if (p.flags != 0) return fail(PASD_ERR_INVALID_ARG, "flags must be 0");
+
+    pasd_plan_t* pl = new pasd_plan_t();
+    pl->ctx = c;
+    pl->N = N;
+    pl->D = D;
+    double asum = 0;
+    for (int n = 0; n < N; ++n) {
+        double a = p.alpha[n];
+        if (a < 0) { delete pl; return fail(PASD_ERR_INVALID_ARG, "alpha_n must be > 0"); }
+        if (a == 0) a = 1.0 / N;
+        pl->alpha[n] = a;
+        asum += a;
+    }
+    for (int n = 0; n < N; ++n) {
+        ModeGeom& g = pl->m[n];
+        g.I = p.dims[n];
+        g.pre = 1;
+        for (int m = 0; m < n; ++m) g.pre *= p.dims[m];
+        g.post = 1;
+        for (int m = n + 1; m < N; ++m) g.post *= p.dims[m];
+        g.P = g.pre * g.post;
+        g.R = p.rank_bound[n];
+        g.Rp = rank_bucket(g.R);
+        double lam;
+        if (p.lambda > 0) lam = pl->alpha[n] / p.lambda;
+        else if (p.lambda_n[n] > 0) lam = p.lambda_n[n];
+        else if (p.lambda_n[n] < 0) { delete pl; return fail(PASD_ERR_INVALID_ARG, "lambda_n must be > 0"); }
+        else lam = std::sqrt((double)std::max<int64_t>(g.I, g.P)) / N;
+        pl->lam[n] = lam;
+    }
+    pl->p = p;
+    int64_t Is[PASD_MAXN];
+    int Rps[PASD_MAXN];
+    for (int n = 0; n < N; ++n) { Is[n] = pl->m[n].I; Rps[n] = pl->m[n].Rp; }
+    size_t smem_limit = std::min<size_t>(c->smem_optin, 200 * 1024);
+    if (!plan_fused_geom(pl->fg, N, Is, Rps, c->num_sms, smem_limit)) {
+        delete pl;
+        return fail(PASD_ERR_UNSUPPORTED, "no tile shape fits shared memory for these ranks");
+    }
+    for (int n = 0; n < N; ++n) {
+        pl->ncta_ap[n] = apass_ncta(pl->m[n].P);
+        pl->n_mp[n] = pl->fg.nregions / pl->fg.Q[n];
+    }
+    // footprint
+    size_t f = align256(sizeof(DevScalars));
+    f += align256(D * 4);                                   // E
+    for (int n = 0; n < N; ++n) {
+        const ModeGeom& g = pl->m[n];
+        f += align256(D * 4);                               // G_n
+        f += align256((size_t)g.P * g.Rp * 4);              // A_n
+        f += 2 * align256((size_t)g.I * g.Rp * 4);          // U_n, Wz_n
+        f += align256((size_t)g.Rp * g.Rp * 4) + 2 * align256(g.Rp * 4);
+        f += align256((size_t)pl->ncta_ap[n] * g.Rp * g.Rp * 4);
+        f += align256((size_t)pl->n_mp[n] * g.I * g.Rp * 4);
+        f += align256((size_t)4 * g.I * g.Rp * 4);
+    }
+    f += align256((size_t)pl->fg.nregions * (3 + N) * 4);
+    f += align256(1024 * 4) + align256(PASD_MAXN * 4);
+    f += align256((size_t)p.max_iter * PASD_TRACE_STRIDE * 8);
+    pl->footprint = f;
+    if (footprint_bytes) *footprint_bytes = f;
+    const char* ng = std::getenv("PASD_NO_GRAPH");
+    pl->use_graph = !(ng && ng[0] == '1');
+    *out = pl;
+    return PASD_OK;
+}
+
+static void enqueue_iteration(pasd_plan_t* pl, cudaStream_t s) {
+    launch_polar(pl->small, s);
+    for (int n = 0; n < pl->N; ++n) launch_apass(pl->ap[n], s);
+    launch_svt(pl->small, s);
+    launch_fused(pl->fu, s);
+    launch_finalize(pl->fin, s);
+}
+
+static pasd_status ensure_allocated(pasd_plan_t* pl) {
+    if (pl->arena) return PASD_OK;
+    CUDA_TRY(cudaSetDevice(pl->ctx->device));
+    char* base = nullptr;
+    CUDA_TRY(cudaMalloc(&base, pl->footprint));
+    pl->arena = base;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char* p = base + off; off += align256(bytes); return p; };
+    const int N = pl->N;
+    const int64_t D = pl->D;
+    pl->sc = reinterpret_cast<DevScalars*>(take(sizeof(DevScalars)));
+    pl->E = reinterpret_cast<float*>(take(D * 4));
+    for (int n = 0; n < N; ++n) {
+        const ModeGeom& g = pl->m[n];
+        pl->G[n] = reinterpret_cast<float*>(take(D * 4));
+        pl->A[n] = reinterpret_cast<float*>(take((size_t)g.P * g.Rp * 4));
+        pl->U[n] = reinterpret_cast<float*>(take((size_t)g.I * g.Rp * 4));
+        pl->Wz[n] = reinterpret_cast<float*>(take((size_t)g.I * g.Rp * 4));
+        pl->W[n] = reinterpret_cast<float*>(take((size_t)g.Rp * g.Rp * 4));
+        pl->F[n] = reinterpret_cast<float*>(take(g.Rp * 4));
+        pl->sigma[n] = reinterpret_cast<float*>(take(g.Rp * 4));
+        pl->gram[n] = reinterpret_cast<float*>(take((size_t)pl->ncta_ap[n] * g.Rp * g.Rp * 4));
+        pl->mp[n] = reinterpret_cast<float*>(take((size_t)pl->n_mp[n] * g.I * g.Rp * 4));
+        pl->scratch[n] = reinterpret_cast<float*>(take((size_t)4 * g.I * g.Rp * 4));
+    }
+    pl->part = reinterpret_cast<float*>(take((size_t)pl->fg.nregions * (3 + N) * 4));
+    pl->sq_part = reinterpret_cast<float*>(take(1024 * 4));
+    pl->kept = reinterpret_cast<int32_t*>(take(PASD_MAXN * 4));
+    pl->trace = reinterpret_cast<double*>(take((size_t)pl->p.max_iter * PASD_TRACE_STRIDE * 8));
+    CUDA_TRY(cudaMemset(pl->arena, 0, pl->footprint));
+    CUDA_TRY(cudaMallocHost(&pl->host_sc, sizeof(DevScalars)));
+    CUDA_TRY(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&pl->ev, cudaEventDisableTiming));
+
+    // launch descriptors
+    SmallArgs& sa = pl->small;
+    sa.N = N;
+    sa.sc = pl->sc;
+    for (int n = 0; n < N; ++n) {
+        const ModeGeom& g = pl->m[n];
+        SmallModeArgs& m = sa.m[n];
+        m.I = g.I; m.R = g.R; m.Rp = g.Rp; m.lambda = pl->lam[n];
+        m.U = pl->U[n]; m.Wz = pl->Wz[n]; m.W = pl->W[n]; m.F = pl->F[n]; m.sigma = pl->sigma[n];
+        m.gram_part = pl->gram[n]; m.n_gram = pl->ncta_ap[n];
+        m.mp_part = pl->mp[n]; m.n_mp = pl->n_mp[n];
+        m.scratch = pl->scratch[n];
+        m.kept = pl->kept + n;
+        ApassArgs& a = pl->ap[n];
+        a.G = pl->G[n]; a.U = pl->U[n]; a.A = pl->A[n]; a.gram_part = pl->gram[n]; a.sc = pl->sc;
+        a.I = g.I; a.pre = g.pre; a.post = g.post; a.P = g.P; a.R = g.R; a.Rp = g.Rp;
+        a.ncta = pl->ncta_ap[n];
+    }
+    FusedArgs& fu = pl->fu;
+    fu.g = pl->fg;
+    fu.sc = pl->sc;
+    fu.E = pl->E;
+    double asum = 0;
+    for (int n = 0; n < N; ++n) asum += pl->alpha[n];
+    for (int n = 0; n < N; ++n) {
+        fu.G[n] = pl->G[n]; fu.A[n] = pl->A[n]; fu.Wz[n] = pl->Wz[n]; fu.mp_part[n] = pl->mp[n];
+        fu.alpha_w[n] = (float)(pl->alpha[n] / asum);
+    }
+    fu.part = pl->part;
+    fu.part_stride = 3 + N;
+    fu.rho = pl->p.rho;
+    fu.mu_max = pl->p.mu_max;
+    fu.output = 0;
+    fu.L = nullptr;
+    FinalizeArgs& fi = pl->fin;
+    fi.N = N; fi.sc = pl->sc; fi.part = pl->part; fi.nparts = pl->fg.nregions; fi.stride = 3 + N;
+    for (int n = 0; n < N; ++n) fi.lambda[n] = pl->lam[n];
+    fi.rho = pl->p.rho; fi.mu_max = pl->p.mu_max; fi.tol = pl->p.tol;
+    fi.stop_rule = pl->p.stop_rule; fi.max_iter = pl->p.max_iter; fi.trace = pl->trace;
+
+    if (pl->use_graph) {
+        CUDA_TRY(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed));
+        enqueue_iteration(pl, pl->cap_stream);
+        CUDA_TRY(cudaStreamEndCapture(pl->cap_stream, &pl->graph));
+        CUDA_TRY(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+    }
+    return PASD_OK;
+}
+
+extern "C" pasd_status pasd_plan_destroy(pasd_plan_t* pl) {
+    if (!pl) return fail(PASD_ERR_INVALID_ARG, "plan is NULL");
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    if (pl->own_stream) cudaStreamDestroy(pl->own_stream);
+    if (pl->ev) cudaEventDestroy(pl->ev);
+    if (pl->host_sc) cudaFreeHost(pl->host_sc);
+    if (pl->arena) cudaFree(pl->arena);
+    if (pl->dev_io) cudaFree(pl->dev_io);
+    if (pl->y_tmp) cudaFree(pl->y_tmp);
+    delete pl;
+    return PASD_OK;
+}
+
+extern "C" int32_t pasd_launches_per_iter(const pasd_plan_t* pl) {
+    return pl ? pl->N + 4 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// stepwise solve
+// ---------------------------------------------------------------------------
+extern "C" pasd_status pasd_begin(pasd_plan_t* pl, const float* T, void* stream) {
+    if (!pl || !T) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    pasd_status st = ensure_allocated(pl);
+    if (st != PASD_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = pl->N;
+    CUDA_TRY(cudaMemsetAsync(pl->E, 0, pl->D * 4, s));
+    for (int n = 0; n < N; ++n) CUDA_TRY(cudaMemcpyAsync(pl->G[n], T, pl->D * 4, cudaMemcpyDeviceToDevice, s));
+    int64_t Is[PASD_MAXN];
+    int Rs[PASD_MAXN], Rps[PASD_MAXN];
+    for (int n = 0; n < N; ++n) { Is[n] = pl->m[n].I; Rs[n] = pl->m[n].R; Rps[n] = pl->m[n].Rp; }
+    launch_init_state(pl->sc, T, pl->p.mu0, N, pl->U, Is, Rs, Rps, pl->W, pl->F, pl->kept, s);
+    launch_norm_fro(T, pl->D, pl->sq_part, 1024, pl->sc, s);
+    CUDA_TRY(cudaGetLastError());
+    return PASD_OK;
+}
+
+extern "C" pasd_status pasd_iterate(pasd_plan_t* pl, int32_t iters, void* stream) {
+    if (!pl || iters < 0) return fail(PASD_ERR_INVALID_ARG, "bad argument");
+    if (!pl->arena) return fail(PASD_ERR_INVALID_ARG, "pasd_begin has not run");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < iters; ++i) {
+        if (pl->use_graph) CUDA_TRY(cudaGraphLaunch(pl->exec, s));
+        else enqueue_iteration(pl, s);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return PASD_OK;
+}
+
+static pasd_status read_scalars(pasd_plan_t* pl, cudaStream_t s) {
+    CUDA_TRY(cudaMemcpyAsync(pl->host_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return PASD_OK;
+}
+
+static void fill_result(pasd_plan_t* pl, pasd_result* r) {
+    const DevScalars& h = *pl->host_sc;
+    std::memset(r, 0, sizeof(*r));
+    r->status = h.done ? h.status : PASD_NOT_CONVERGED;
+    r->iters = h.k;
+    r->res_inf = h.res_inf;
+    r->res_fro_rel = h.res_fro_rel;
+    r->objective = h.objective;
+    r->l1_E = h.l1_E;
+    r->mu_final = h.mu;
+    for (int n = 0; n < pl->N; ++n) { r->kept[n] = h.kept[n]; r->nuclear[n] = h.nuclear[n]; }
+}
+
+extern "C" pasd_status pasd_finish(pasd_plan_t* pl, float* L, float* E, pasd_result* res,
+                                   void* stream) {
+    if (!pl || !L || !E) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    if (!pl->arena) return fail(PASD_ERR_INVALID_ARG, "pasd_begin has not run");
+    cudaStream_t s = (cudaStream_t)stream;
+    pasd_status st = read_scalars(pl, s);
+    if (st != PASD_OK) return st;
+    pasd_result r;
+    fill_result(pl, &r);
+    if (res) *res = r;
+    if (r.status != PASD_OK && r.status != PASD_NOT_CONVERGED) {
+        return fail((pasd_status)r.status, "solve failed: non-finite values in the iterate");
+    }
+    // output: L = sum_n alpha_n Z_n / sum alpha_n, E (Algorithm 1, Output)
+    FusedArgs fo = pl->fu;
+    fo.output = 1;
+    fo.L = L;
+    launch_fused(fo, s);   // the output pass ignores the stop flag
+    CUDA_TRY(cudaMemcpyAsync(E, pl->E, pl->D * 4, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    return (pasd_status)r.status;
+}
+
+static pasd_status run_loop(pasd_plan_t* pl, cudaStream_t s) {
+    const int chunk = pl->p.check_every;
+    const int max_iter = pl->p.max_iter;
+    int launched = 0;
+    // keep one chunk in flight while the previous chunk's flag is checked
+    pasd_status st = pasd_iterate(pl, std::min(chunk, max_iter), s);
+    if (st != PASD_OK) return st;
+    launched += std::min(chunk, max_iter);
+    for (;;) {
+        CUDA_TRY(cudaMemcpyAsync(pl->host_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaEventRecord(pl->ev, s));
+        if (launched < max_iter) {
+            int n = std::min(chunk, max_iter - launched);
+            st = pasd_iterate(pl, n, s);
+            if (st != PASD_OK) return st;
+            launched += n;
+        }
+        CUDA_TRY(cudaEventSynchronize(pl->ev));
+        if (pl->host_sc->done) break;
+        if (launched >= max_iter) {
+            CUDA_TRY(cudaStreamSynchronize(s));
+            break;
+        }
+    }
+    return PASD_OK;
+}
+
+extern "C" pasd_status pasd_solve(pasd_plan_t* pl, const float* T, float* L, float* E,
+                                  pasd_result* res, void* stream) {
+    if (!pl || !T || !L || !E) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    pasd_status st = pasd_begin(pl, T, stream);
+    if (st != PASD_OK) return st;
+    st = run_loop(pl, s);
+    if (st != PASD_OK) return st;
+    return pasd_finish(pl, L, E, res, stream);
+}
+
+extern "C" pasd_status pasd_solve_host(pasd_plan_t* pl, const float* Th, float* Lh, float* Eh,
+                                       pasd_result* res, void* stream) {
+    if (!pl || !Th || !Lh || !Eh) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!pl->dev_io) CUDA_TRY(cudaMalloc(&pl->dev_io, (size_t)3 * pl->D * 4));
+    float* Td = pl->dev_io;
+    float* Ld = Td + pl->D;
+    float* Ed = Ld + pl->D;
+    CUDA_TRY(cudaMemcpyAsync(Td, Th, pl->D * 4, cudaMemcpyHostToDevice, s));
+    pasd_status st = pasd_solve(pl, Td, Ld, Ed, res, stream);
+    if (st != PASD_OK && st != PASD_NOT_CONVERGED) return st;
+    CUDA_TRY(cudaMemcpyAsync(Lh, Ld, pl->D * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(Eh, Ed, pl->D * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// state export
+// ---------------------------------------------------------------------------
+extern "C" pasd_status pasd_state_get(pasd_plan_t* pl, int32_t item, int32_t mode, void* dst,
+                                      size_t bytes, void* stream) {
+    if (!pl || !dst) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    if (!pl->arena) return fail(PASD_ERR_INVALID_ARG, "no state yet");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = pl->N;
+    bool per_mode = item == PASD_STATE_U || item == PASD_STATE_A || item == PASD_STATE_W ||
+                    item == PASD_STATE_SIGMA || item == PASD_STATE_F || item == PASD_STATE_Y;
+    if (per_mode && (mode < 0 || mode >= N)) return fail(PASD_ERR_INVALID_ARG, "mode out of range");
+    auto copy2d = [&](const float* src, int64_t rows, int cols, int ld) -> pasd_status {
+        if (bytes != (size_t)rows * cols * 4) return fail(PASD_ERR_INVALID_ARG, "size mismatch");
+        CUDA_TRY(cudaMemcpy2DAsync(dst, cols * 4, src, ld * 4, cols * 4, rows, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return PASD_OK;
+    };
+    switch (item) {
+        case PASD_STATE_U: return copy2d(pl->U[mode], pl->m[mode].I, pl->m[mode].R, pl->m[mode].Rp);
+        case PASD_STATE_W: return copy2d(pl->W[mode], pl->m[mode].R, pl->m[mode].R, pl->m[mode].Rp);
+        case PASD_STATE_SIGMA: return copy2d(pl->sigma[mode], 1, pl->m[mode].R, pl->m[mode].Rp);
+        case PASD_STATE_F: return copy2d(pl->F[mode], 1, pl->m[mode].R, pl->m[mode].Rp);
+        case PASD_STATE_A: {
+            // device layout [pre][Rp][post] -> host [R][pre*post] (unfolding column order)
+            const ModeGeom& g = pl->m[mode];
+            if (bytes != (size_t)g.R * g.P * 4) return fail(PASD_ERR_INVALID_ARG, "size mismatch");
+            float* h = (float*)dst;
+            for (int r = 0; r < g.R; ++r) {
+                // rows r of every a-block: pre blocks of `post` contiguous floats
+                CUDA_TRY(cudaMemcpy2DAsync(h + (size_t)r * g.P, g.post * 4, pl->A[mode] + (size_t)r * g.post,
+                                           (size_t)g.Rp * g.post * 4, g.post * 4, g.pre,
+                                           cudaMemcpyDeviceToHost, s));
+            }
+            CUDA_TRY(cudaStreamSynchronize(s));
+            return PASD_OK;
+        }
+        case PASD_STATE_E:
+            if (bytes != (size_t)pl->D * 4) return fail(PASD_ERR_INVALID_ARG, "size mismatch");
+            CUDA_TRY(cudaMemcpyAsync(dst, pl->E, bytes, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            return PASD_OK;
+        case PASD_STATE_Y: {
+            if (bytes != (size_t)pl->D * 4) return fail(PASD_ERR_INVALID_ARG, "size mismatch");
+            if (!pl->y_tmp) CUDA_TRY(cudaMalloc(&pl->y_tmp, pl->D * 4));
+            pasd_status st = read_scalars(pl, s);
+            if (st != PASD_OK) return st;
+            launch_export_y(pl->G[mode], pl->host_sc->T, pl->E, pl->sc, pl->y_tmp, pl->D, s);
+            CUDA_TRY(cudaMemcpyAsync(dst, pl->y_tmp, bytes, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            return PASD_OK;
+        }
+        case PASD_STATE_MU: {
+            if (bytes != 8) return fail(PASD_ERR_INVALID_ARG, "size mismatch");
+            pasd_status st = read_scalars(pl, s);
+            if (st != PASD_OK) return st;
+            std::memcpy(dst, &pl->host_sc->mu, 8);
+            return PASD_OK;
+        }
+        case PASD_STATE_KEPT: {
+            if (bytes != (size_t)N * 4) return fail(PASD_ERR_INVALID_ARG, "size mismatch");
+            pasd_status st = read_scalars(pl, s);
+            if (st != PASD_OK) return st;
+            std::memcpy(dst, pl->host_sc->kept, bytes);
+            return PASD_OK;
+        }
+        case PASD_STATE_TRACE: {
+            pasd_status st = read_scalars(pl, s);
+            if (st != PASD_OK) return st;
+            size_t rec = PASD_TRACE_STRIDE * 8;
+            if (bytes % rec != 0 || bytes / rec > (size_t)pl->host_sc->k)
+                return fail(PASD_ERR_INVALID_ARG, "size mismatch");
+            CUDA_TRY(cudaMemcpyAsync(dst, pl->trace, bytes, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            return PASD_OK;
+        }
+        default: return fail(PASD_ERR_INVALID_ARG, "unknown state item");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// served path: continuous batching over per-solve streams
+// ---------------------------------------------------------------------------
+struct Active {
+    Job job;
+    int launched = 0;
+    bool flag_pending = false;
+};
+
+static void worker_main(pasd_ctx* c) {
+    cudaSetDevice(c->device);
+    std::vector<Active> active;
+    size_t in_use = 0;
+    for (;;) {
+        // admission
+        {
+            std::unique_lock<std::mutex> lk(c->mu);
+            if (active.empty() && c->queue.empty()) {
+                if (c->stop) break;
+                c->cv.wait_for(lk, std::chrono::milliseconds(2));
+                if (c->stop && c->queue.empty()) break;
+            }
+            for (auto it = c->queue.begin(); it != c->queue.end();) {
+                pasd_plan_t* pl = it->plan;
+                size_t need = pl->footprint;
+                if (!pl->busy && in_use + need <= c->hbm_budget) {
+                    Active a;
+                    a.job = *it;
+                    pl->busy = true;
+                    in_use += need;
+                    c->state[it->ticket] = 1;
+                    active.push_back(a);
+                    it = c->queue.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        // start newly admitted solves
+        for (auto& a : active) {
+            pasd_plan_t* pl = a.job.plan;
+            if (a.launched == 0 && !a.flag_pending) {
+                if (!pl->own_stream) cudaStreamCreateWithFlags(&pl->own_stream, cudaStreamNonBlocking);
+                pasd_status st = pasd_begin(pl, a.job.T, pl->own_stream);
+                if (st != PASD_OK) {
+                    pasd_result r{};
+                    r.status = st;
+                    std::unique_lock<std::mutex> lk(c->mu);
+                    c->done[a.job.ticket] = r;
+                    c->state.erase(a.job.ticket);
+                    pl->busy = false;
+                    a.launched = -1;
+                    continue;
+                }
+            }
+        }
+        // advance every active solve by one chunk, one stream each
+        for (auto& a : active) {
+            if (a.launched < 0 || a.flag_pending) continue;
+            pasd_plan_t* pl = a.job.plan;
+            int n = std::min(pl->p.check_every, pl->p.max_iter - a.launched);
+            if (n > 0) {
+                pasd_iterate(pl, n, pl->own_stream);
+                a.launched += n;
+            }
+            cudaMemcpyAsync(pl->host_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, pl->own_stream);
+            cudaEventRecord(pl->ev, pl->own_stream);
+            a.flag_pending = true;
+        }
+        // retire finished ones
+        bool progressed = false;
+        for (auto& a : active) {
+            if (a.launched < 0) continue;
+            pasd_plan_t* pl = a.job.plan;
+            if (!a.flag_pending) continue;
+            if (cudaEventQuery(pl->ev) != cudaSuccess) continue;
+            a.flag_pending = false;
+            progressed = true;
+            if (pl->host_sc->done || a.launched >= pl->p.max_iter) {
+                pasd_result r{};
+                pasd_status st = pasd_finish(pl, a.job.L, a.job.E, &r, pl->own_stream);
+                r.status = st;
+                r.latency_s = std::chrono::duration<double>(std::chrono::steady_clock::now() -
+                                                            a.job.t_submit).count();
+                std::unique_lock<std::mutex> lk(c->mu);
+                c->done[a.job.ticket] = r;
+                c->state.erase(a.job.ticket);
+                pl->busy = false;
+                a.launched = -1;
+            }
+        }
+        for (auto it = active.begin(); it != active.end();) {
+            if (it->launched < 0) {
+                in_use -= it->job.plan->footprint;
+                it = active.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        if (!progressed && !active.empty()) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+extern "C" pasd_status pasd_submit(pasd_ctx* c, pasd_plan_t* pl, const float* T, float* L,
+                                   float* E, uint64_t* ticket) {
+    if (!c || !pl || !T || !L || !E || !ticket) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    if (pl->ctx != c) return fail(PASD_ERR_INVALID_ARG, "plan belongs to another context");
+    if (pl->footprint > c->hbm_budget) return fail(PASD_ERR_OOM, "plan footprint exceeds the HBM budget");
+    std::unique_lock<std::mutex> lk(c->mu);
+    if (c->queue.size() >= c->max_queue) return fail(PASD_ERR_BUSY, "submit queue is full");
+    Job j;
+    j.ticket = c->next_ticket++;
+    j.plan = pl;
+    j.T = T;
+    j.L = L;
+    j.E = E;
+    j.t_submit = std::chrono::steady_clock::now();
+    c->queue.push_back(j);
+    c->state[j.ticket] = 0;
+    *ticket = j.ticket;
+    if (!c->worker_started) {
+        c->worker_started = true;
+        c->worker = std::thread(worker_main, c);
+    }
+    lk.unlock();
+    c->cv.notify_all();
+    return PASD_OK;
+}
+
+extern "C" pasd_status pasd_poll(pasd_ctx* c, uint64_t ticket, pasd_result* out) {
+    if (!c) return fail(PASD_ERR_INVALID_ARG, "ctx is NULL");
+    std::unique_lock<std::mutex> lk(c->mu);
+    auto it = c->done.find(ticket);
+    if (it != c->done.end()) {
+        pasd_result r = it->second;
+        c->done.erase(it);
+        if (out) *out = r;
+        return (pasd_status)r.status;
+    }
+    if (c->state.count(ticket)) return PASD_PENDING;
+    return fail(PASD_ERR_UNKNOWN_TICKET, "unknown ticket");
+}
+
+extern "C" const char* pasd_status_string(pasd_status s) {
+    switch (s) {
+        case PASD_OK: return "PASD_OK";
+        case PASD_PENDING: return "PASD_PENDING";
+        case PASD_NOT_CONVERGED: return "PASD_NOT_CONVERGED";
+        case PASD_ERR_INVALID_ARG: return "PASD_ERR_INVALID_ARG";
+        case PASD_ERR_OOM: return "PASD_ERR_OOM";
+        case PASD_ERR_CUDA: return "PASD_ERR_CUDA";
+        case PASD_ERR_NONFINITE: return "PASD_ERR_NONFINITE";
+        case PASD_ERR_TIMEOUT: return "PASD_ERR_TIMEOUT";
+        case PASD_ERR_BUSY: return "PASD_ERR_BUSY";
+        case PASD_ERR_UNKNOWN_TICKET: return "PASD_ERR_UNKNOWN_TICKET";
+        case PASD_ERR_UNSUPPORTED: return "PASD_ERR_UNSUPPORTED";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* pasd_last_error(void) { return g_last_error.c_str(); }

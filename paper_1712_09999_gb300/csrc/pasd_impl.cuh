@@ -1,0 +1,169 @@
+// Internal definitions shared by the PASD kernels and the host runtime.
+//
+// Notation follows the paper (Jiang & Ng, arXiv 1712.09999): mode n of an
+// N-way C-order tensor has size I_n; pre_n = prod_{m<n} I_m, post_n =
+// prod_{m>n} I_m, P_n = pre_n * post_n. The mode-n unfolding X_(n) (Sec. 2.1)
+// is read in place as the 3-D view [pre_n, I_n, post_n]; its column index is
+// j = a * post_n + b (C order over the other modes).
+//
+// Device-resident solver state of one plan (all float32 unless noted):
+//   E                 D         sparse part
+//   G_n               D each    G_n = T - E + Y_n / mu (the argument of Eq. 9 - Eq. 13);
+//                               the multipliers are kept in this scaled, shifted form
+//   U_n               I_n x Rp  active subspace (row-major, columns >= R_n are zero)
+//   A_n               [pre_n][Rp][post_n]   A_n = U_n^T G_n, the SVT argument of Eq. 13
+//   W_n, F_n, S_n     eigen-system of A_n A_n^T (R x R), SVT factors, kept count
+//   Wz_n              I_n x Rp  U_n W diag(F) W^T, so that Z_n = fold_n(Wz_n A_n)
+//   partial buffers   per-CTA Gram and G_n A_n^T sums, reduced in a fixed order
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define PASD_MAXN 8
+#define PASD_MAXR 64
+
+namespace pasd {
+
+// Scalars that live on the device so that a captured iteration graph can be
+// replayed without host involvement.
+struct DevScalars {
+    const float* T;        // observation (caller's device buffer)
+    double mu;             // mu^k (used by every sub-step of iteration k)
+    double t_norm_fro;     // ||T||_F
+    int32_t k;             // completed loop bodies
+    int32_t done;          // 1 -> every kernel returns immediately
+    int32_t status;        // pasd_status once done
+    int32_t kept[PASD_MAXN];
+    double nuclear[PASD_MAXN];
+    double res_inf, res_fro_rel, objective, l1_E, mu_used;
+    int32_t nonfinite;
+    int32_t pad_;
+};
+
+struct ModeGeom {
+    int64_t I, pre, post, P;
+    int R, Rp;       // rank bound and its round-up to a multiple of 4
+};
+
+// ----------------------------------------------------------------------------
+// A-pass: A_n = U_n^T G_n (+ per-CTA Gram partials of A_n A_n^T)
+// ----------------------------------------------------------------------------
+constexpr int AP_THREADS = 128;
+constexpr int AP_BN = 256;       // columns of the unfolding per CTA (2 per thread)
+constexpr int AP_BK = 16;        // rows of the contraction per pipeline stage
+constexpr int AP_STAGES = 4;
+
+struct ApassArgs {
+    const float* G;      // G_n (D floats)
+    const float* U;      // I x Rp
+    float* A;            // [pre][Rp][post]
+    float* gram_part;    // [ncta][Rp][Rp]
+    const DevScalars* sc;
+    int64_t I, pre, post, P;
+    int R, Rp;
+    int ncta;
+};
+
+void launch_apass(const ApassArgs& a, cudaStream_t s);
+size_t apass_smem_bytes(int Rp, bool rowmajor);
+int apass_ncta(int64_t P);
+
+// ----------------------------------------------------------------------------
+// Small per-mode kernels (one CTA per mode): polar (U-step), SVT, finalize
+// ----------------------------------------------------------------------------
+struct SmallModeArgs {
+    int64_t I;
+    int R, Rp;
+    double lambda;         // lambda_n
+    float* U;              // I x Rp
+    float* Wz;             // I x Rp
+    float* W;              // Rp x Rp (columns = eigenvectors, by descending eigenvalue)
+    float* F;              // Rp
+    float* sigma;          // Rp
+    const float* gram_part; int n_gram;     // [n_gram][Rp][Rp]
+    const float* mp_part; int n_mp;         // [n_mp][I][Rp]  (G A^T partials)
+    float* scratch;        // 4 * I * Rp floats
+    int32_t* kept;         // device int (per mode)
+};
+
+struct SmallArgs {
+    int N;
+    SmallModeArgs m[PASD_MAXN];
+    DevScalars* sc;
+};
+
+void launch_polar(const SmallArgs& a, cudaStream_t s);
+void launch_svt(const SmallArgs& a, cudaStream_t s);
+
+struct FinalizeArgs {
+    int N;
+    DevScalars* sc;
+    const float* part;     // [nparts][stride]: resmax, l1, nonfinite, res2[N]
+    int nparts, stride;
+    double lambda[PASD_MAXN];
+    double rho, mu_max, tol;
+    int stop_rule, max_iter;
+    double* trace;         // [max_iter][13]
+};
+void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+void launch_init_state(DevScalars* sc, const float* T, double mu0, int N, float** U,
+                       const int64_t* I, const int* R, const int* Rp, float** W, float** F,
+                       int32_t* kept, cudaStream_t s);
+void launch_norm_fro(const float* T, int64_t D, float* part, int nparts, DevScalars* sc,
+                     cudaStream_t s);
+void launch_export_y(const float* G, const float* T, const float* E, const DevScalars* sc,
+                     float* Y, int64_t D, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Fused elementwise pass: Z_n, E-step (Eq. 15), multipliers, residuals and the
+// G_n A_n^T partials of the next U-step, over power-of-two tiles ("boxes").
+// ----------------------------------------------------------------------------
+constexpr int FU_THREADS = 256;
+
+struct FusedGeom {
+    int N;
+    int64_t I[PASD_MAXN];
+    int64_t stride[PASD_MAXN];     // element stride of mode n (= post_n)
+    int64_t astr[PASD_MAXN][PASD_MAXN];  // for mode n, stride of mode m<n inside pre_n
+    int Rp[PASD_MAXN];
+    int b[PASD_MAXN], sh[PASD_MAXN];     // box extents (powers of two) and log2
+    int esh[PASD_MAXN];                  // bit offset of l_m inside the element index e
+    int csh[PASD_MAXN][PASD_MAXN];       // for mode n: bit offset of l_m (m != n) inside c
+    int C[PASD_MAXN];                    // B / b_n
+    int B;                               // elements per tile
+    int mb[PASD_MAXN];                   // micro-box extent per mode (1 or 2), prod = B / FU_THREADS
+    int mbsh[PASD_MAXN];                 // bit offset of the micro-box coordinate in the thread id
+    int64_t nt[PASD_MAXN];               // tiles per mode
+    int Q[PASD_MAXN];                    // region grid
+    int nregions;
+    int ext_max[PASD_MAXN];              // max rows of mode n a region spans
+    int macc_off[PASD_MAXN];             // offsets (floats) into the region accumulator
+    int macc_floats;
+    int as_off[PASD_MAXN], ws_off[PASD_MAXN];   // smem layout (floats)
+    int gs_off, red_off, macc_base;
+    int smem_floats;
+    int64_t mp_combo_stride[PASD_MAXN];  // floats per combo in mp_part[n] (= I_n * Rp_n)
+};
+
+struct FusedArgs {
+    FusedGeom g;
+    DevScalars* sc;
+    float* E;
+    float* G[PASD_MAXN];
+    const float* A[PASD_MAXN];
+    const float* Wz[PASD_MAXN];
+    float* mp_part[PASD_MAXN];
+    float* part;           // [nregions][stride] reduction partials
+    int part_stride;
+    double rho, mu_max;
+    // output mode (writes L = sum alpha_n Z_n / sum alpha_n, no state update)
+    int output;
+    float* L;
+    float alpha_w[PASD_MAXN];
+};
+
+bool plan_fused_geom(FusedGeom& g, int N, const int64_t* I, const int* Rp, int num_sms,
+                     size_t smem_limit);
+void launch_fused(const FusedArgs& a, cudaStream_t s);
+
+}  // namespace pasd
