@@ -184,8 +184,19 @@ enum {
 pasd_status pasd_state_get(pasd_plan_t* plan, int32_t item, int32_t mode, void* dst_host,
                            size_t bytes, void* stream);
 
-/* Number of kernel launches the last pasd_iterate enqueued per loop body. */
+/* Number of kernel launches pasd_iterate enqueues per loop body. */
 int32_t pasd_launches_per_iter(const pasd_plan_t* plan);
+
+/* Kernel timing for measurement: runs `iters` loop bodies on `stream` as plain
+ * launches (not the captured graph), brackets each kernel group with CUDA
+ * events on that stream, synchronizes, and writes the summed milliseconds per
+ * group into kernel_ms[0 .. PASD_PROFILE_SLOTS-1] in this order:
+ *   0 polar (U-step), 1 A-pass (all modes), 2 SVT, 3 fused elementwise pass,
+ *   4 finalize.
+ * The solver state advances exactly as with pasd_iterate. */
+#define PASD_PROFILE_SLOTS 5
+pasd_status pasd_profile_iterations(pasd_plan_t* plan, int32_t iters, double* kernel_ms,
+                                    void* stream);
 
 const char* pasd_status_string(pasd_status s);
 const char* pasd_last_error(void);

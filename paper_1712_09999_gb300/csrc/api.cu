@@ -366,6 +366,38 @@ extern "C" pasd_status pasd_plan_destroy(pasd_plan_t* pl) {
     return PASD_OK;
 }
 
+extern "C" pasd_status pasd_profile_iterations(pasd_plan_t* pl, int32_t iters, double* ms,
+                                               void* stream) {
+    if (!pl || !ms || iters < 0) return fail(PASD_ERR_INVALID_ARG, "bad argument");
+    if (!pl->arena) return fail(PASD_ERR_INVALID_ARG, "pasd_begin has not run");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t ev[PASD_PROFILE_SLOTS + 1];
+    for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
+    for (int k = 0; k < PASD_PROFILE_SLOTS; ++k) ms[k] = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        CUDA_TRY(cudaEventRecord(ev[0], s));
+        launch_polar(pl->small, s);
+        CUDA_TRY(cudaEventRecord(ev[1], s));
+        for (int n = 0; n < pl->N; ++n) launch_apass(pl->ap[n], s);
+        CUDA_TRY(cudaEventRecord(ev[2], s));
+        launch_svt(pl->small, s);
+        CUDA_TRY(cudaEventRecord(ev[3], s));
+        launch_fused(pl->fu, s);
+        CUDA_TRY(cudaEventRecord(ev[4], s));
+        launch_finalize(pl->fin, s);
+        CUDA_TRY(cudaEventRecord(ev[5], s));
+        CUDA_TRY(cudaEventSynchronize(ev[5]));
+        for (int k = 0; k < PASD_PROFILE_SLOTS; ++k) {
+            float t = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+            ms[k] += t;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    CUDA_TRY(cudaGetLastError());
+    return PASD_OK;
+}
+
 extern "C" int32_t pasd_launches_per_iter(const pasd_plan_t* pl) {
     return pl ? pl->N + 4 : 0;
 }

@@ -108,10 +108,13 @@ __device__ void block_jacobi(float* A, float* V, float* A2, float* V2, int* pc, 
 __device__ void sort_desc(const float* A, int n, int ld, int* perm) {
     const int t = threadIdx.x;
     if (t < n) {
+        // NaN sorts last, so the ranks always form a permutation
         float v = A[t * ld + t];
+        if (v != v) v = -INFINITY;
         int r = 0;
         for (int j = 0; j < n; ++j) {
             float w = A[j * ld + j];
+            if (w != w) w = -INFINITY;
             r += (w > v) || (w == v && j < t);
         }
         perm[r] = t;

@@ -87,6 +87,8 @@ _SIGS = {
     "pasd_state_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_size_t, ctypes.c_void_p]),
     "pasd_launches_per_iter": (ctypes.c_int32, [ctypes.c_void_p]),
+    "pasd_profile_iterations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "pasd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pasd_last_error": (ctypes.c_char_p, []),
 }
@@ -231,6 +233,16 @@ def pasd_state_get(plan: int, item: int, mode: int, out, stream=None) -> None:
 
 def pasd_launches_per_iter(plan: int) -> int:
     return int(lib().pasd_launches_per_iter(plan))
+
+
+PROFILE_SLOTS = ("polar", "apass", "svt", "fused", "finalize")
+
+
+def pasd_profile_iterations(plan: int, iters: int, stream=None) -> dict:
+    """Per-kernel-group milliseconds summed over `iters` loop bodies (CUDA events)."""
+    ms = (ctypes.c_double * len(PROFILE_SLOTS))()
+    _check(lib().pasd_profile_iterations(plan, iters, ms, _stream(stream)), "pasd_profile_iterations")
+    return dict(zip(PROFILE_SLOTS, list(ms)))
 
 
 def pasd_status_string(status: int) -> str:

@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Acceptance (FP32 path): the number of kept singular values is identical per
+mode and per iteration, and the relative Frobenius differences of L and E are
+at most 1e-5; the recovery error of a converged solve is within 1e-4 of the
+oracle's.
+"""
+import numpy as np
+import pytest
+
+from oracle import pasd_oracle as O
+from paper_1712_09999_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+STOPS = {0: "inf", 1: "fro_rel", 2: "fixed"}
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1712_09999_gb300 import pasd as P
+    ctx = P.pasd_ctx_create(0)
+    yield torch, P, ctx
+    P.pasd_ctx_destroy(ctx)
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def _gpu_solve(env, T, ranks, stop, max_iter, **kw):
+    torch, P, ctx = env
+    params = P.make_params(T.shape, ranks, stop=stop, max_iter=max_iter, **kw)
+    plan, _ = P.pasd_plan(ctx, params)
+    Td = torch.from_numpy(T).cuda()
+    L = torch.empty_like(Td)
+    E = torch.empty_like(Td)
+    res = P.pasd_solve(plan, Td, L, E)
+    trace = np.zeros((res.iters, P.TRACE_STRIDE))
+    P.pasd_state_get(plan, P.STATE_TRACE, 0, trace)
+    out = dict(res=res, L=L.cpu().numpy(), E=E.cpu().numpy(), trace=trace, plan=plan)
+    return out
+
+
+def _oracle(T, ranks, stop, max_iter, lam_pair=None):
+    if lam_pair is None:
+        p = O.Params(ranks=ranks, lambdas=O.paper_lambdas(T.shape), stop=STOPS[stop], max_iter=max_iter)
+    else:
+        alpha, lam = lam_pair
+        p = O.Params.from_alpha_lambda(ranks, alpha, lam, stop=STOPS[stop], max_iter=max_iter)
+    return O.pasd(T, p)
+
+
+def _check_parity(g, ref, n_modes):
+    gk = g["trace"][:, 5:5 + n_modes].astype(int).tolist()
+    rk = [s.kept for s in ref.trace]
+    assert g["res"].iters == ref.iters
+    assert gk == rk, "kept counts differ (first at %s)" % next(i for i, (a, b) in enumerate(zip(gk, rk)) if a != b)
+    assert _rel(g["L"], ref.L) <= TOL
+    assert _rel(g["E"], ref.E) <= TOL
+
+
+@pytest.mark.parametrize("stop,iters", [(2, 150), (0, 1000)])
+def test_small_cube_matches_oracle(env, stop, iters):
+    pr = synth.planted((24, 20, 16), (3, 3, 2), 0.1, 7, scale="std", amp=5.0)
+    ref = _oracle(pr.T, (4, 4, 3), stop, iters)
+    g = _gpu_solve(env, pr.T, (4, 4, 3), stop, iters)
+    _check_parity(g, ref, 3)
+
+
+def test_cube50_workload_fixed_and_converged(env):
+    # 50^3, Tucker core 5^3, 10% corruption U[-10,10]*std(L0), R_n = 10,
+    # lambda = 1/sqrt(50*50), alpha_n = 1/3, fixed 100 iterations, then to convergence.
+    pr = synth.cube_small(0)
+    lp = ((1 / 3,) * 3, 1 / 50)
+    kw = dict(alpha=lp[0], lam=lp[1])
+    ref = _oracle(pr.T, (10,) * 3, 2, 100, lp)
+    g = _gpu_solve(env, pr.T, (10,) * 3, 2, 100, **kw)
+    _check_parity(g, ref, 3)
+    ref = _oracle(pr.T, (10,) * 3, 0, 1000, lp)
+    g = _gpu_solve(env, pr.T, (10,) * 3, 0, 1000, **kw)
+    _check_parity(g, ref, 3)
+    assert ref.converged and g["res"].status == 0
+    assert abs(O.rse(g["L"], pr.L0) - O.rse(ref.L, pr.L0)) <= 1e-4
+    assert O.rse(g["L"], pr.L0) < 1e-5
+
+
+@pytest.mark.parametrize("dims,tucker,ranks", [
+    ((37, 29, 23), (3, 2, 2), (5, 4, 3)),        # ragged tiles, odd contiguous mode
+    ((12, 10, 3, 20), (2, 2, 2, 2), (3, 3, 2, 4)),  # 4-way with a tiny mode
+    ((60, 45), (4, 4), (6, 6)),                   # matrix case (N = 2)
+    ((6, 7, 5, 4, 9), (2, 2, 2, 2, 2), (2, 3, 2, 2, 3)),  # 5-way
+    ((9, 8, 7), (2, 2, 2), (9, 8, 7)),            # R_n = I_n (HoRPCA case)
+])
+def test_shapes_match_oracle(env, dims, tucker, ranks):
+    pr = synth.planted(dims, tucker, 0.1, 3, scale="std", amp=5.0)
+    ref = _oracle(pr.T, ranks, 0, 1000)
+    g = _gpu_solve(env, pr.T, ranks, 0, 1000)
+    _check_parity(g, ref, len(dims))
+
+
+def _gpu_state(env, plan, shape, ranks):
+    torch, P, ctx = env
+    N = len(shape)
+    D = int(np.prod(shape))
+    st = {}
+    for n in range(N):
+        I, R = shape[n], ranks[n]
+        u = np.zeros((I, R), np.float32); P.pasd_state_get(plan, P.STATE_U, n, u)
+        a = np.zeros((R, D // I), np.float32); P.pasd_state_get(plan, P.STATE_A, n, a)
+        w = np.zeros((R, R), np.float32); P.pasd_state_get(plan, P.STATE_W, n, w)
+        f = np.zeros(R, np.float32); P.pasd_state_get(plan, P.STATE_F, n, f)
+        s = np.zeros(R, np.float32); P.pasd_state_get(plan, P.STATE_SIGMA, n, s)
+        y = np.zeros(shape, np.float32); P.pasd_state_get(plan, P.STATE_Y, n, y)
+        st[n] = dict(U=u.astype(np.float64), A=a.astype(np.float64), W=w.astype(np.float64),
+                     F=f.astype(np.float64), sigma=s, Y=y.astype(np.float64))
+    e = np.zeros(shape, np.float32); P.pasd_state_get(plan, P.STATE_E, 0, e)
+    mu = np.zeros(1, np.float64); P.pasd_state_get(plan, P.STATE_MU, 0, mu)
+    kept = np.zeros(N, np.int32); P.pasd_state_get(plan, P.STATE_KEPT, 0, kept)
+    return st, e.astype(np.float64), float(mu[0]), kept.tolist()
+
+
+def test_full_size_single_step_parity(env):
+    # 200^3 workload (Tucker core 10^3, 20% corruption U[-1,1]*max|L0|, R_n = 20,
+    # lambda = 1/200, alpha = 1/3): run the GPU past the activation, hand its state
+    # to the oracle, and compare one loop body of each.
+    torch, P, ctx = env
+    pr = synth.cube_200(1)
+    T = pr.T
+    shape, ranks = T.shape, (20, 20, 20)
+    params = P.make_params(shape, ranks, alpha=(1 / 3,) * 3, lam=1 / 200, stop=P.STOP_FIXED_ITERS,
+                           max_iter=1000)
+    plan, _ = P.pasd_plan(ctx, params)
+    Td = torch.from_numpy(T).cuda()
+    P.pasd_begin(plan, Td)
+    P.pasd_iterate(plan, 115)
+    torch.cuda.synchronize()
+    st, e, mu, kept = _gpu_state(env, plan, shape, ranks)
+    assert max(kept) > 0, "state is still idle"
+    t64 = T.astype(np.float64)
+    ost = O.State(U=[], V=[], null=[], E=e, Y=[], mu=mu, k=115)
+    for n in range(3):
+        s = st[n]
+        k = kept[n]
+        ost.U.append(s["U"])
+        ost.V.append((s["W"] * s["F"]) @ (s["W"].T @ s["A"]))
+        ost.null.append(s["W"][:, k:])
+        ost.Y.append(s["Y"])
+    p = O.Params.from_alpha_lambda(ranks, (1 / 3,) * 3, 1 / 200, stop="fixed", max_iter=1000)
+    info = O.step(t64, ost, p)
+    P.pasd_iterate(plan, 1)
+    torch.cuda.synchronize()
+    st2, e2, mu2, kept2 = _gpu_state(env, plan, shape, ranks)
+    assert kept2 == info.kept
+    assert mu2 == pytest.approx(ost.mu, rel=1e-12)
+    assert _rel(e2, ost.E) <= TOL
+    for n in range(3):
+        s = st2[n]
+        z = O.fold(s["U"] @ ((s["W"] * s["F"]) @ (s["W"].T @ s["A"])), n, shape)
+        assert _rel(z, info.Z[n]) <= TOL
+        # multipliers: compare to their own scale
+        assert np.max(np.abs(s["Y"] - ost.Y[n])) <= 1e-4 * np.max(np.abs(ost.Y[n])) + 1e-6
+        k = info.kept[n]
+        assert np.allclose(s["sigma"][:k], info.sigma[n][:k], rtol=1e-4)
+        assert np.allclose(s["U"].T @ s["U"], np.eye(ranks[n]), atol=1e-5)
+    P.pasd_plan_destroy(plan)
+
+
+def test_multiplier_bound_and_orthonormality_on_gpu(env):
+    # ||sum_n Y_n||_inf <= 1 (App. A) and U_n^T U_n = I along a GPU run.
+    torch, P, ctx = env
+    pr = synth.planted((40, 36, 32), (3, 3, 3), 0.15, 9, scale="std", amp=5.0)
+    shape, ranks = pr.T.shape, (5, 5, 4)
+    plan, _ = P.pasd_plan(ctx, P.make_params(shape, ranks, stop=P.STOP_FIXED_ITERS, max_iter=400))
+    Td = torch.from_numpy(pr.T).cuda()
+    P.pasd_begin(plan, Td)
+    for _ in range(8):
+        P.pasd_iterate(plan, 25)
+        torch.cuda.synchronize()
+        st, e, mu, kept = _gpu_state(env, plan, shape, ranks)
+        ysum = sum(st[n]["Y"] for n in range(3))
+        slack = 1e-4 + 64 * np.finfo(np.float32).eps * mu * np.abs(pr.T).max()
+        assert np.max(np.abs(ysum)) <= 1.0 + slack
+        for n in range(3):
+            assert np.allclose(st[n]["U"].T @ st[n]["U"], np.eye(ranks[n]), atol=1e-5)
+    P.pasd_plan_destroy(plan)
+
+
+def test_stepwise_and_host_paths_equal_solve(env):
+    torch, P, ctx = env
+    pr = synth.planted((30, 26, 22), (3, 3, 3), 0.1, 12, scale="std", amp=5.0)
+    shape, ranks = pr.T.shape, (4, 4, 4)
+    params = P.make_params(shape, ranks, stop=P.STOP_INF_ABS, max_iter=1000)
+    plan, _ = P.pasd_plan(ctx, params)
+    Td = torch.from_numpy(pr.T).cuda()
+    L1 = torch.empty_like(Td); E1 = torch.empty_like(Td)
+    r1 = P.pasd_solve(plan, Td, L1, E1)
+    # stepwise
+    L2 = torch.empty_like(Td); E2 = torch.empty_like(Td)
+    P.pasd_begin(plan, Td)
+    P.pasd_iterate(plan, r1.iters + 20)     # bodies after the stop rule are skipped
+    r2 = P.pasd_finish(plan, L2, E2)
+    assert r2.iters == r1.iters
+    assert torch.equal(L1, L2) and torch.equal(E1, E2)
+    # host buffers
+    Lh = np.zeros(shape, np.float32); Eh = np.zeros(shape, np.float32)
+    r3 = P.pasd_solve_host(plan, np.ascontiguousarray(pr.T), Lh, Eh)
+    assert r3.iters == r1.iters
+    assert np.array_equal(Lh, L1.cpu().numpy()) and np.array_equal(Eh, E1.cpu().numpy())
+    P.pasd_plan_destroy(plan)
+
+
+def test_served_results_equal_alone(env):
+    # Continuous batching: solves submitted together overlap on the device; each
+    # result equals the same solve run alone.
+    torch, P, ctx = env
+    probs = [synth.planted(d, (3, 3, 3), 0.1, 20 + i, scale="std", amp=5.0)
+             for i, d in enumerate([(32, 30, 28), (40, 24, 36), (28, 28, 28), (50, 20, 30)])]
+    plans, alone, bufs = [], [], []
+    for pr in probs:
+        plan, _ = P.pasd_plan(ctx, P.make_params(pr.T.shape, (4, 4, 4), max_iter=1000))
+        Td = torch.from_numpy(pr.T).cuda()
+        L = torch.empty_like(Td); E = torch.empty_like(Td)
+        P.pasd_solve(plan, Td, L, E)
+        alone.append((L.clone(), E.clone()))
+        L.zero_(); E.zero_()
+        plans.append(plan)
+        bufs.append((Td, L, E))
+    torch.cuda.synchronize()
+    tickets = [P.pasd_submit(ctx, plans[i], *bufs[i]) for i in range(len(probs))]
+    import time
+    t0 = time.time()
+    pending = set(tickets)
+    results = {}
+    while pending and time.time() - t0 < 60:
+        for t in list(pending):
+            st, r = P.pasd_poll(ctx, t)
+            if st != P.PENDING:
+                results[t] = (st, r)
+                pending.discard(t)
+        time.sleep(0.001)
+    assert not pending
+    for i, t in enumerate(tickets):
+        st, r = results[t]
+        assert st == P.OK
+        assert r.latency_s > 0
+        assert torch.equal(bufs[i][1], alone[i][0]) and torch.equal(bufs[i][2], alone[i][1])
+    for plan in plans:
+        P.pasd_plan_destroy(plan)
+
+
+def test_invalid_and_nonfinite_inputs(env):
+    torch, P, ctx = env
+    with pytest.raises(P.PasdError) as ei:
+        P.pasd_plan(ctx, P.make_params((10, 8, 6), (4, 9, 2)))    # R_2 > I_2
+    assert ei.value.status == P.ERR_INVALID_ARG
+    with pytest.raises(P.PasdError) as ei:
+        P.pasd_plan(ctx, P.make_params((10, 8, 6), (4, 4, 2), rho=0.9))
+    assert ei.value.status == P.ERR_INVALID_ARG
+    pr = synth.planted((20, 18, 16), (2, 2, 2), 0.1, 2, scale="std", amp=5.0)
+    t = pr.T.copy()
+    t[3, 4, 5] = np.nan
+    plan, _ = P.pasd_plan(ctx, P.make_params(t.shape, (3, 3, 3), max_iter=50))
+    Td = torch.from_numpy(t).cuda()
+    L = torch.full_like(Td, 7.0); E = torch.full_like(Td, 7.0)
+    with pytest.raises(P.PasdError) as ei:
+        P.pasd_solve(plan, Td, L, E)
+    assert ei.value.status == P.ERR_NONFINITE
+    assert bool(torch.all(L == 7.0)) and bool(torch.all(E == 7.0))   # outputs untouched
+    P.pasd_plan_destroy(plan)
