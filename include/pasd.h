@@ -187,6 +187,19 @@ pasd_status pasd_state_get(pasd_plan_t* plan, int32_t item, int32_t mode, void* 
 /* Number of kernel launches pasd_iterate enqueues per loop body. */
 int32_t pasd_launches_per_iter(const pasd_plan_t* plan);
 
+/* The mode-n product of the V-step (Eq. 13) as a standalone operation: for a
+ * C-order float32 tensor X viewed as [pre][I][post] (the mode-n unfolding X_(n)
+ * has I rows and pre*post columns, Sec. 2.1), computes
+ *   A    = U^T X_(n)   stored as [pre][R][post]  (device, pre*R*post floats)
+ *   gram = A A^T       R x R row-major           (device; may be NULL)
+ * with U an I x R row-major device matrix. The unfolding is read in place.
+ * R must be one of 4, 8, ..., 32, 40, 48, 56, 64 (pad U with zero columns for
+ * other ranks); otherwise UNSUPPORTED. Scratch for the per-CTA Gram partial
+ * sums (ceil(pre*post/256) * R * R floats) is allocated and freed inside the
+ * call; the call is synchronous on `stream`. */
+pasd_status pasd_mode_product(const float* X, int64_t pre, int64_t I, int64_t post, const float* U,
+                              int32_t R, float* A, float* gram, void* stream);
+
 /* Kernel timing for measurement: runs `iters` loop bodies on `stream` as plain
  * launches (not the captured graph), brackets each kernel group with CUDA
  * events on that stream, synchronizes, and writes the summed milliseconds per

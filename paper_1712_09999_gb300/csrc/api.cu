@@ -28,6 +28,7 @@ static pasd_status fail(pasd_status s, const std::string& msg) {
     g_last_error = msg;
     return s;
 }
+void pasd_set_error(const std::string& msg) { g_last_error = msg; }
 #define CUDA_TRY(call)                                                                   \
     do {                                                                                 \
         cudaError_t e_ = (call);                                                         \

@@ -89,6 +89,9 @@ _SIGS = {
     "pasd_launches_per_iter": (ctypes.c_int32, [ctypes.c_void_p]),
     "pasd_profile_iterations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "pasd_mode_product": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
     "pasd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pasd_last_error": (ctypes.c_char_p, []),
 }
@@ -233,6 +236,12 @@ def pasd_state_get(plan: int, item: int, mode: int, out, stream=None) -> None:
 
 def pasd_launches_per_iter(plan: int) -> int:
     return int(lib().pasd_launches_per_iter(plan))
+
+
+def pasd_mode_product(X, pre: int, I: int, post: int, U, R: int, A, gram=None, stream=None) -> None:
+    """A = U^T X_(n) (stored [pre][R][post]) and gram = A A^T, synchronous."""
+    _check(lib().pasd_mode_product(_ptr(X), pre, I, post, _ptr(U), R, _ptr(A), _ptr(gram), _stream(stream)),
+           "pasd_mode_product")
 
 
 PROFILE_SLOTS = ("polar", "apass", "svt", "fused", "finalize")
