@@ -200,6 +200,24 @@ int32_t pasd_launches_per_iter(const pasd_plan_t* plan);
 pasd_status pasd_mode_product(const float* X, int64_t pre, int64_t I, int64_t post, const float* U,
                               int32_t R, float* A, float* gram, void* stream);
 
+/* Allocation-free variant of pasd_mode_product, for callers that cannot
+ * allocate device memory where they need the product (a framework allocator
+ * that must own every device byte, or a latency-critical loop in which
+ * cudaMalloc/cudaFree would synchronise the device). The paper has no
+ * counterpart; this is an interface convenience.
+ * Same arguments, results and rank rule as pasd_mode_product, but the Gram
+ * partial sums go to a fixed 4 MiB scratch array compiled into the library
+ * (held on every device that loads the library until the process exits), so
+ * the call allocates nothing and is asynchronous on `stream`. Limit:
+ * ceil(pre*post/256) * R * R <= 1048576, else UNSUPPORTED (outputs untouched).
+ * The first call on a device looks up the scratch's device address (with that
+ * device current); make it before any stream capture. All calls share the
+ * scratch and it keeps the last call's contents: calls whose work overlaps on
+ * the GPU race on it and must be serialised by the caller. */
+pasd_status pasd_mode_product_noalloc(const float* X, int64_t pre, int64_t I, int64_t post,
+                                      const float* U, int32_t R, float* A, float* gram,
+                                      void* stream);
+
 /* Kernel timing for measurement: runs `iters` loop bodies on `stream` as plain
  * launches (not the captured graph), brackets each kernel group with CUDA
  * events on that stream, synchronizes, and writes the summed milliseconds per

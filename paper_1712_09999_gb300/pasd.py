@@ -92,6 +92,9 @@ _SIGS = {
     "pasd_mode_product": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p]),
+    "pasd_mode_product_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                                 ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pasd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pasd_last_error": (ctypes.c_char_p, []),
 }
@@ -242,6 +245,12 @@ def pasd_mode_product(X, pre: int, I: int, post: int, U, R: int, A, gram=None, s
     """A = U^T X_(n) (stored [pre][R][post]) and gram = A A^T, synchronous."""
     _check(lib().pasd_mode_product(_ptr(X), pre, I, post, _ptr(U), R, _ptr(A), _ptr(gram), _stream(stream)),
            "pasd_mode_product")
+
+
+def pasd_mode_product_noalloc(X, pre: int, I: int, post: int, U, R: int, A, gram=None, stream=None) -> None:
+    """pasd_mode_product with fixed library scratch instead of an allocation; asynchronous."""
+    _check(lib().pasd_mode_product_noalloc(_ptr(X), pre, I, post, _ptr(U), R, _ptr(A), _ptr(gram),
+                                           _stream(stream)), "pasd_mode_product_noalloc")
 
 
 PROFILE_SLOTS = ("polar", "apass", "svt", "fused", "finalize")
