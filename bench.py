@@ -56,15 +56,24 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+FUSED_SOURCES = ("fused_tma.cu", "fused.cu")   # the kernel and its tile planner
+
+
+def _fused_src_hash():
+    h = hashlib.sha256()
+    for f in FUSED_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1712_09999_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def _fused_traffic():
     """dram bytes per fused-pass launch from the committed ncu summary, if the
-    kernel source still matches the one that was profiled; else None."""
+    kernel sources still match the ones that were profiled; else None."""
     p = os.path.join(ROOT, "profiles", "fused_pass_200cube_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    src = open(os.path.join(ROOT, "paper_1712_09999_gb300", "csrc", "fused.cu"), "rb").read()
-    if hashlib.sha256(src).hexdigest() != d.get("fused_cu_sha256"):
+    if _fused_src_hash() != d.get("fused_src_sha256"):
         return None
     return d.get("traffic_bytes_per_launch")
 
@@ -235,17 +244,24 @@ def run_ours(args):
     # dominant kernel: per-kernel CUDA-event durations over active-phase bodies
     P.pasd_begin(plan, T, stream)
     P.pasd_iterate(plan, max(0, k_conv - 60), stream)
+    k0 = max(0, k_conv - 60)
     prof = P.pasd_profile_iterations(plan, 30, stream)
     fused_ms = prof["fused"] / 30
     D = int(np.prod(DIMS))
     N = len(DIMS)
-    alg_bytes = (2 * N + 3) * 4 * D + 4 * sum(R * (D // I) for R, I in zip(RANKS, DIMS))
+    # algorithmic bytes of one fused pass: read T, E, G_1..G_N, write E, G_1..G_N,
+    # read the kept rows of each Vrot_n once (mean kept count over the profiled bodies)
+    tr = np.zeros((k0 + 30, P.TRACE_STRIDE))
+    P.pasd_state_get(plan, P.STATE_TRACE, 0, tr)
+    kept_mean = tr[k0:, 5:5 + N].mean(axis=0)
+    alg_bytes = (2 * N + 3) * 4 * D + 4 * sum(float(s) * (D // I) for s, I in zip(kept_mean, DIMS))
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (fused_ms / 1000.0) / 1e9
     traffic = _fused_traffic()
     roofline = {"bound": "hbm", "kernel": "fused elementwise pass (refold, E-shrink, multipliers, G A^T)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                "profiled_bodies": [k0 + 1, k0 + 30], "kept_mean": kept_mean.tolist(),
                 "launch_ms": fused_ms,
                 "kernel_ms_per_iter": {k: v / 30 for k, v in prof.items()}}
 
@@ -286,8 +302,38 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_workload(args):
+    """For ncu: plan the 200^3 workload, run `pre` loop bodies, then `iters` more, exit.
+    Launch order per body: polar, A-pass (one launch per group of modes with the
+    same padded rank), SVT, Vrot, fused pass, finalize; pasd_begin launches 3
+    kernels first."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1712_09999_gb300 import pasd as P
+    from paper_1712_09999_gb300 import synth
+    torch.cuda.set_device(0)
+    pr = synth.cube_200(1)
+    T = torch.from_numpy(pr.T).cuda()
+    ctx = P.pasd_ctx_create(0)
+    plan, _ = P.pasd_plan(ctx, P.make_params(DIMS, RANKS, alpha=ALPHA, lam=LAMBDA,
+                                             stop=P.STOP_FIXED_ITERS, max_iter=args.pre + args.iters + 1))
+    P.pasd_begin(plan, T)
+    P.pasd_iterate(plan, args.pre)
+    P.pasd_iterate(plan, args.iters)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_workload": "200^3", "pre": args.pre, "iters": args.iters,
+                      "launches_per_iter": P.pasd_launches_per_iter(plan)}))
+    P.pasd_plan_destroy(plan)
+    P.pasd_ctx_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-workload", action="store_true",
+                    help="run loop bodies of the 200^3 workload for an external profiler and exit")
+    ap.add_argument("--pre", type=int, default=120)
+    ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
@@ -296,6 +342,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.profile_workload:
+        run_profile_workload(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -48,8 +48,9 @@ typedef enum {
 
 typedef enum {
     PASD_PREC_FP32 = 0,   /* FP32 storage and arithmetic on the hot path            */
-    PASD_PREC_MIXED = 1   /* BF16 split hi+lo products, FP32 accumulation, then a
-                             closing run of FP32 iterations                         */
+    PASD_PREC_MIXED = 1   /* reserved for BF16 split hi+lo products with FP32
+                             accumulation; accepted, and currently runs exactly the
+                             FP32 path                                              */
 } pasd_precision;
 
 typedef enum {
@@ -222,10 +223,10 @@ pasd_status pasd_mode_product_noalloc(const float* X, int64_t pre, int64_t I, in
  * launches (not the captured graph), brackets each kernel group with CUDA
  * events on that stream, synchronizes, and writes the summed milliseconds per
  * group into kernel_ms[0 .. PASD_PROFILE_SLOTS-1] in this order:
- *   0 polar (U-step), 1 A-pass (all modes), 2 SVT, 3 fused elementwise pass,
- *   4 finalize.
+ *   0 polar (U-step), 1 A-pass (all modes), 2 SVT, 3 Vrot (small factor in the
+ *   SVT eigenbasis), 4 fused elementwise pass, 5 finalize.
  * The solver state advances exactly as with pasd_iterate. */
-#define PASD_PROFILE_SLOTS 5
+#define PASD_PROFILE_SLOTS 6
 pasd_status pasd_profile_iterations(pasd_plan_t* plan, int32_t iters, double* kernel_ms,
                                     void* stream);
 

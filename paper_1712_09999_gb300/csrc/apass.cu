@@ -13,6 +13,8 @@
 // by the copy, so they contribute nothing to A or to the Gram sums.
 #include "pasd_impl.cuh"
 
+#include <algorithm>
+
 namespace pasd {
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
@@ -52,15 +54,13 @@ size_t apass_smem_bytes(int Rp, bool rowmajor) {
 int apass_ncta(int64_t P) { return (int)((P + AP_BN - 1) / AP_BN); }
 
 template <int RP, int V>
-__global__ void __launch_bounds__(AP_THREADS) apass_kernel(ApassArgs a) {
-    if (a.sc->done) return;
+__device__ __forceinline__ void apass_body(const ApassArgs& a, int cta, float* smem) {
     using L = ApLayout<V>;
-    extern __shared__ __align__(16) float smem[];
     float* Gs = smem;
     float* Us = smem + AP_STAGES * L::gs_stage;
 
     const int t = threadIdx.x;
-    const int64_t j0 = (int64_t)blockIdx.x * AP_BN;
+    const int64_t j0 = (int64_t)cta * AP_BN;
     const int64_t I = a.I, post = a.post, P = a.P;
     const float* __restrict__ G = a.G;
     const int nk = (int)((I + AP_BK - 1) / AP_BK);
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(AP_THREADS) apass_kernel(ApassArgs a) {
         for (int q = 0; q < 16; ++q) red[(sl * NBT + blk) * 16 + q] = g[q];
     }
     __syncthreads();
-    float* gp = a.gram_part + (size_t)blockIdx.x * RP * RP;
+    float* gp = a.gram_part + (size_t)cta * RP * RP;
     for (int o = t; o < NBT * 16; o += AP_THREADS) {
         int blk = o / 16, q = o % 16;
         float s = 0.f;
@@ -279,41 +279,83 @@ __global__ void __launch_bounds__(AP_THREADS) apass_kernel(ApassArgs a) {
     }
 }
 
+static int apass_variant(const ApassArgs& a) {
+    if (a.post == 1) return (a.I % 4 == 0) ? 2 : 3;
+    return (a.post % 4 == 0) ? 0 : 1;
+}
+
+// One launch covers every mode with the same padded rank: CTAs
+// [cta_start[k], cta_start[k+1]) work on mode group member k, so the modes'
+// products run concurrently.
+struct ApassMulti {
+    int count;
+    ApassArgs m[PASD_MAXN];
+    int variant[PASD_MAXN];
+    int cta_start[PASD_MAXN + 1];
+};
+
 template <int RP>
-static void launch_rp(const ApassArgs& a, cudaStream_t s) {
-    int V;
-    if (a.post == 1) V = (a.I % 4 == 0) ? 2 : 3;
-    else V = (a.post % 4 == 0) ? 0 : 1;
-    size_t smem = apass_smem_bytes(RP, V >= 2);
-    dim3 grid(a.ncta);
-    switch (V) {
-#define CASE(v)                                                                                  \
-    case v:                                                                                      \
-        cudaFuncSetAttribute(apass_kernel<RP, v>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)smem);                                                         \
-        apass_kernel<RP, v><<<grid, AP_THREADS, smem, s>>>(a);                                   \
-        break;
-        CASE(0) CASE(1) CASE(2) CASE(3)
-#undef CASE
+__global__ void __launch_bounds__(AP_THREADS) apass_kernel(const ApassMulti mm) {
+    extern __shared__ __align__(16) float smem[];
+    int k = 0;
+    while (k + 1 < mm.count && (int)blockIdx.x >= mm.cta_start[k + 1]) ++k;
+    const ApassArgs& a = mm.m[k];
+    if (a.sc->done) return;
+    const int cta = blockIdx.x - mm.cta_start[k];
+    switch (mm.variant[k]) {
+        case 0: apass_body<RP, 0>(a, cta, smem); break;
+        case 1: apass_body<RP, 1>(a, cta, smem); break;
+        case 2: apass_body<RP, 2>(a, cta, smem); break;
+        default: apass_body<RP, 3>(a, cta, smem); break;
     }
 }
 
-void launch_apass(const ApassArgs& a, cudaStream_t s) {
-    switch (a.Rp) {
-        case 4: launch_rp<4>(a, s); break;
-        case 8: launch_rp<8>(a, s); break;
-        case 12: launch_rp<12>(a, s); break;
-        case 16: launch_rp<16>(a, s); break;
-        case 20: launch_rp<20>(a, s); break;
-        case 24: launch_rp<24>(a, s); break;
-        case 28: launch_rp<28>(a, s); break;
-        case 32: launch_rp<32>(a, s); break;
-        case 40: launch_rp<40>(a, s); break;
-        case 48: launch_rp<48>(a, s); break;
-        case 56: launch_rp<56>(a, s); break;
-        case 64: launch_rp<64>(a, s); break;
+template <int RP>
+static void launch_rp(const ApassMulti& mm, cudaStream_t s) {
+    size_t smem = std::max(apass_smem_bytes(RP, false), apass_smem_bytes(RP, true));
+    cudaFuncSetAttribute(apass_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    apass_kernel<RP><<<mm.cta_start[mm.count], AP_THREADS, smem, s>>>(mm);
+}
+
+static void launch_multi(const ApassMulti& mm, int Rp, cudaStream_t s) {
+    switch (Rp) {
+        case 4: launch_rp<4>(mm, s); break;
+        case 8: launch_rp<8>(mm, s); break;
+        case 12: launch_rp<12>(mm, s); break;
+        case 16: launch_rp<16>(mm, s); break;
+        case 20: launch_rp<20>(mm, s); break;
+        case 24: launch_rp<24>(mm, s); break;
+        case 28: launch_rp<28>(mm, s); break;
+        case 32: launch_rp<32>(mm, s); break;
+        case 40: launch_rp<40>(mm, s); break;
+        case 48: launch_rp<48>(mm, s); break;
+        case 56: launch_rp<56>(mm, s); break;
+        case 64: launch_rp<64>(mm, s); break;
         default: break;
     }
 }
+
+int launch_apass_modes(const ApassArgs* a, int N, cudaStream_t s) {
+    bool done[PASD_MAXN] = {false};
+    int launches = 0;
+    for (int n = 0; n < N; ++n) {
+        if (done[n]) continue;
+        ApassMulti mm{};
+        mm.cta_start[0] = 0;
+        for (int k = n; k < N; ++k) {
+            if (done[k] || a[k].Rp != a[n].Rp) continue;
+            done[k] = true;
+            mm.m[mm.count] = a[k];
+            mm.variant[mm.count] = apass_variant(a[k]);
+            mm.cta_start[mm.count + 1] = mm.cta_start[mm.count] + a[k].ncta;
+            ++mm.count;
+        }
+        launch_multi(mm, a[n].Rp, s);
+        ++launches;
+    }
+    return launches;
+}
+
+void launch_apass(const ApassArgs& a, cudaStream_t s) { launch_apass_modes(&a, 1, s); }
 
 }  // namespace pasd

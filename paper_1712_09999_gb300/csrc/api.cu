@@ -75,16 +75,20 @@ struct pasd_plan {
     ModeGeom m[PASD_MAXN];
     double lam[PASD_MAXN];
     double alpha[PASD_MAXN];
-    FusedGeom fg{};
+    FusedGeom fg{};          // geometry in use
+    FusedGeom fg_plain{};    // single-buffer geometry (fallback when TMA is unavailable)
+    bool want_tma = false;
+    FusedTmaPlan* tma = nullptr;
+    float* Tc = nullptr;     // plan-owned copy of the observation
     int ncta_ap[PASD_MAXN];
     int n_mp[PASD_MAXN];
     size_t footprint = 0;
     // device arena
     char* arena = nullptr;
     DevScalars* sc = nullptr;
-    float *E = nullptr, *G[PASD_MAXN], *A[PASD_MAXN], *U[PASD_MAXN], *Wz[PASD_MAXN];
+    float *E = nullptr, *G[PASD_MAXN], *A[PASD_MAXN], *U[PASD_MAXN], *Urot[PASD_MAXN], *Vr[PASD_MAXN];
     float *W[PASD_MAXN], *F[PASD_MAXN], *sigma[PASD_MAXN];
-    float *gram[PASD_MAXN], *mp[PASD_MAXN], *scratch[PASD_MAXN];
+    float *gram[PASD_MAXN], *mp[PASD_MAXN], *scratch[PASD_MAXN], *Mred[PASD_MAXN];
     float *part = nullptr, *sq_part = nullptr;
     int32_t* kept = nullptr;
     double* trace = nullptr;
@@ -95,6 +99,7 @@ struct pasd_plan {
     ApassArgs ap[PASD_MAXN];
     FusedArgs fu{};
     FinalizeArgs fin{};
+    VrotArgs vr{};
     // graph
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -104,6 +109,7 @@ struct pasd_plan {
     cudaStream_t own_stream = nullptr;   // served path
     cudaEvent_t ev = nullptr;
     bool busy = false;
+    int ap_launches = 1;
 };
 
 // ---------------------------------------------------------------------------
@@ -229,28 +235,35 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     int Rps[PASD_MAXN];
     for (int n = 0; n < N; ++n) { Is[n] = pl->m[n].I; Rps[n] = pl->m[n].Rp; }
     size_t smem_limit = std::min<size_t>(c->smem_optin, 200 * 1024);
-    if (!plan_fused_geom(pl->fg, N, Is, Rps, c->num_sms, smem_limit)) {
+    if (!plan_fused_geom(pl->fg_plain, N, Is, Rps, c->num_sms, smem_limit)) {
         delete pl;
         return fail(PASD_ERR_UNSUPPORTED, "no tile shape fits shared memory for these ranks");
     }
+    const char* nt = std::getenv("PASD_NO_TMA");
+    pl->want_tma = !(nt && nt[0] == '1') &&
+                   plan_fused_tma(pl->fg, N, Is, Rps, c->num_sms, c->smem_optin);
+    if (!pl->want_tma) pl->fg = pl->fg_plain;
     for (int n = 0; n < N; ++n) {
         pl->ncta_ap[n] = apass_ncta(pl->m[n].P);
-        pl->n_mp[n] = pl->fg.nregions / pl->fg.Q[n];
+        pl->n_mp[n] = std::max(pl->fg.nregions / pl->fg.Q[n], pl->fg_plain.nregions / pl->fg_plain.Q[n]);
     }
+    int nparts = std::max(pl->fg.nregions, pl->fg_plain.nregions);
     // footprint
     size_t f = align256(sizeof(DevScalars));
+    f += align256(D * 4);                                   // T copy
     f += align256(D * 4);                                   // E
     for (int n = 0; n < N; ++n) {
         const ModeGeom& g = pl->m[n];
         f += align256(D * 4);                               // G_n
-        f += align256((size_t)g.P * g.Rp * 4);              // A_n
-        f += 2 * align256((size_t)g.I * g.Rp * 4);          // U_n, Wz_n
+        f += 2 * align256((size_t)g.P * g.Rp * 4);          // A_n, Vrot_n
+        f += 2 * align256((size_t)g.I * g.Rp * 4);          // U_n, Urot_n
         f += align256((size_t)g.Rp * g.Rp * 4) + 2 * align256(g.Rp * 4);
         f += align256((size_t)pl->ncta_ap[n] * g.Rp * g.Rp * 4);
         f += align256((size_t)pl->n_mp[n] * g.I * g.Rp * 4);
         f += align256((size_t)4 * g.I * g.Rp * 4);
+        f += align256((size_t)g.I * g.Rp * 4);              // Mred_n
     }
-    f += align256((size_t)pl->fg.nregions * (3 + N) * 4);
+    f += align256((size_t)nparts * (3 + N) * 4);
     f += align256(1024 * 4) + align256(PASD_MAXN * 4);
     f += align256((size_t)p.max_iter * PASD_TRACE_STRIDE * 8);
     pl->footprint = f;
@@ -261,11 +274,23 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     return PASD_OK;
 }
 
+static void launch_fused_pass(pasd_plan_t* pl, int output, float* L, cudaStream_t s) {
+    if (pl->tma) {
+        launch_fused_tma(pl->tma, output, L, s);
+    } else {
+        FusedArgs fo = pl->fu;
+        fo.output = output;
+        fo.L = L;
+        launch_fused(fo, s);
+    }
+}
+
 static void enqueue_iteration(pasd_plan_t* pl, cudaStream_t s) {
     launch_polar(pl->small, s);
-    for (int n = 0; n < pl->N; ++n) launch_apass(pl->ap[n], s);
+    pl->ap_launches = launch_apass_modes(pl->ap, pl->N, s);
     launch_svt(pl->small, s);
-    launch_fused(pl->fu, s);
+    launch_vrot(pl->vr, s);
+    launch_fused_pass(pl, 0, nullptr, s);
     launch_finalize(pl->fin, s);
 }
 
@@ -280,21 +305,24 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
     const int N = pl->N;
     const int64_t D = pl->D;
     pl->sc = reinterpret_cast<DevScalars*>(take(sizeof(DevScalars)));
+    pl->Tc = reinterpret_cast<float*>(take(D * 4));
     pl->E = reinterpret_cast<float*>(take(D * 4));
     for (int n = 0; n < N; ++n) {
         const ModeGeom& g = pl->m[n];
         pl->G[n] = reinterpret_cast<float*>(take(D * 4));
         pl->A[n] = reinterpret_cast<float*>(take((size_t)g.P * g.Rp * 4));
+        pl->Vr[n] = reinterpret_cast<float*>(take((size_t)g.P * g.Rp * 4));
         pl->U[n] = reinterpret_cast<float*>(take((size_t)g.I * g.Rp * 4));
-        pl->Wz[n] = reinterpret_cast<float*>(take((size_t)g.I * g.Rp * 4));
+        pl->Urot[n] = reinterpret_cast<float*>(take((size_t)g.I * g.Rp * 4));
         pl->W[n] = reinterpret_cast<float*>(take((size_t)g.Rp * g.Rp * 4));
         pl->F[n] = reinterpret_cast<float*>(take(g.Rp * 4));
         pl->sigma[n] = reinterpret_cast<float*>(take(g.Rp * 4));
         pl->gram[n] = reinterpret_cast<float*>(take((size_t)pl->ncta_ap[n] * g.Rp * g.Rp * 4));
         pl->mp[n] = reinterpret_cast<float*>(take((size_t)pl->n_mp[n] * g.I * g.Rp * 4));
         pl->scratch[n] = reinterpret_cast<float*>(take((size_t)4 * g.I * g.Rp * 4));
+        pl->Mred[n] = reinterpret_cast<float*>(take((size_t)g.I * g.Rp * 4));
     }
-    pl->part = reinterpret_cast<float*>(take((size_t)pl->fg.nregions * (3 + N) * 4));
+    pl->part = reinterpret_cast<float*>(take((size_t)std::max(pl->fg.nregions, pl->fg_plain.nregions) * (3 + N) * 4));
     pl->sq_part = reinterpret_cast<float*>(take(1024 * 4));
     pl->kept = reinterpret_cast<int32_t*>(take(PASD_MAXN * 4));
     pl->trace = reinterpret_cast<double*>(take((size_t)pl->p.max_iter * PASD_TRACE_STRIDE * 8));
@@ -311,9 +339,9 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
         const ModeGeom& g = pl->m[n];
         SmallModeArgs& m = sa.m[n];
         m.I = g.I; m.R = g.R; m.Rp = g.Rp; m.lambda = pl->lam[n];
-        m.U = pl->U[n]; m.Wz = pl->Wz[n]; m.W = pl->W[n]; m.F = pl->F[n]; m.sigma = pl->sigma[n];
+        m.U = pl->U[n]; m.Urot = pl->Urot[n]; m.W = pl->W[n]; m.F = pl->F[n]; m.sigma = pl->sigma[n];
         m.gram_part = pl->gram[n]; m.n_gram = pl->ncta_ap[n];
-        m.mp_part = pl->mp[n]; m.n_mp = pl->n_mp[n];
+        m.Mred = pl->Mred[n];
         m.scratch = pl->scratch[n];
         m.kept = pl->kept + n;
         ApassArgs& a = pl->ap[n];
@@ -328,7 +356,7 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
     double asum = 0;
     for (int n = 0; n < N; ++n) asum += pl->alpha[n];
     for (int n = 0; n < N; ++n) {
-        fu.G[n] = pl->G[n]; fu.A[n] = pl->A[n]; fu.Wz[n] = pl->Wz[n]; fu.mp_part[n] = pl->mp[n];
+        fu.G[n] = pl->G[n]; fu.A[n] = pl->Vr[n]; fu.Wz[n] = pl->Urot[n]; fu.mp_part[n] = pl->mp[n];
         fu.alpha_w[n] = (float)(pl->alpha[n] / asum);
     }
     fu.part = pl->part;
@@ -337,11 +365,42 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
     fu.mu_max = pl->p.mu_max;
     fu.output = 0;
     fu.L = nullptr;
+    VrotArgs& va = pl->vr;
+    va.N = N;
+    va.sc = pl->sc;
+    va.cta_start[0] = 0;
+    for (int n = 0; n < N; ++n) {
+        const ModeGeom& g = pl->m[n];
+        VrotMode& vm = va.m[n];
+        vm.A = pl->A[n]; vm.V = pl->Vr[n]; vm.W = pl->W[n]; vm.F = pl->F[n];
+        vm.P = g.P; vm.post = g.post; vm.R = g.R; vm.Rp = g.Rp;
+        va.cta_start[n + 1] = va.cta_start[n] + (int)((g.P + 255) / 256);
+    }
     FinalizeArgs& fi = pl->fin;
     fi.N = N; fi.sc = pl->sc; fi.part = pl->part; fi.nparts = pl->fg.nregions; fi.stride = 3 + N;
     for (int n = 0; n < N; ++n) fi.lambda[n] = pl->lam[n];
     fi.rho = pl->p.rho; fi.mu_max = pl->p.mu_max; fi.tol = pl->p.tol;
     fi.stop_rule = pl->p.stop_rule; fi.max_iter = pl->p.max_iter; fi.trace = pl->trace;
+    {
+        int maxRp = 4;
+        for (int n = 0; n < N; ++n) maxRp = std::max(maxRp, pl->m[n].Rp);
+        for (int n = 0; n < N; ++n) {
+            const ModeGeom& g = pl->m[n];
+            fi.mp_part[n] = pl->mp[n]; fi.I[n] = g.I; fi.R[n] = g.R; fi.Rp[n] = g.Rp; fi.Mred[n] = pl->Mred[n];
+            sa.m[n].polar_in_smem = polar_smem_bytes(maxRp, g.I) <= std::min<size_t>(pl->ctx->smem_optin, 200 * 1024);
+        }
+    }
+    if (pl->want_tma) {
+        char err[256] = {0};
+        pl->tma = make_fused_tma(fu, pl->Tc, err, sizeof(err));
+        if (!pl->tma) {
+            // tensor maps refused: use the single-buffer pass
+            pl->fg = pl->fg_plain;
+            fu.g = pl->fg;
+            fi.nparts = pl->fg.nregions;
+        }
+    }
+    for (int n = 0; n < N; ++n) fi.n_mp[n] = pl->fg.nregions / pl->fg.Q[n];
 
     if (pl->use_graph) {
         CUDA_TRY(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -354,6 +413,7 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
 
 extern "C" pasd_status pasd_plan_destroy(pasd_plan_t* pl) {
     if (!pl) return fail(PASD_ERR_INVALID_ARG, "plan is NULL");
+    if (pl->tma) destroy_fused_tma(pl->tma);
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
@@ -379,15 +439,17 @@ extern "C" pasd_status pasd_profile_iterations(pasd_plan_t* pl, int32_t iters, d
         CUDA_TRY(cudaEventRecord(ev[0], s));
         launch_polar(pl->small, s);
         CUDA_TRY(cudaEventRecord(ev[1], s));
-        for (int n = 0; n < pl->N; ++n) launch_apass(pl->ap[n], s);
+        launch_apass_modes(pl->ap, pl->N, s);
         CUDA_TRY(cudaEventRecord(ev[2], s));
         launch_svt(pl->small, s);
         CUDA_TRY(cudaEventRecord(ev[3], s));
-        launch_fused(pl->fu, s);
+        launch_vrot(pl->vr, s);
         CUDA_TRY(cudaEventRecord(ev[4], s));
-        launch_finalize(pl->fin, s);
+        launch_fused_pass(pl, 0, nullptr, s);
         CUDA_TRY(cudaEventRecord(ev[5], s));
-        CUDA_TRY(cudaEventSynchronize(ev[5]));
+        launch_finalize(pl->fin, s);
+        CUDA_TRY(cudaEventRecord(ev[6], s));
+        CUDA_TRY(cudaEventSynchronize(ev[6]));
         for (int k = 0; k < PASD_PROFILE_SLOTS; ++k) {
             float t = 0.f;
             CUDA_TRY(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
@@ -400,7 +462,7 @@ extern "C" pasd_status pasd_profile_iterations(pasd_plan_t* pl, int32_t iters, d
 }
 
 extern "C" int32_t pasd_launches_per_iter(const pasd_plan_t* pl) {
-    return pl ? pl->N + 4 : 0;
+    return pl ? pl->ap_launches + 5 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -412,13 +474,14 @@ extern "C" pasd_status pasd_begin(pasd_plan_t* pl, const float* T, void* stream)
     if (st != PASD_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int N = pl->N;
+    CUDA_TRY(cudaMemcpyAsync(pl->Tc, T, pl->D * 4, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemsetAsync(pl->E, 0, pl->D * 4, s));
-    for (int n = 0; n < N; ++n) CUDA_TRY(cudaMemcpyAsync(pl->G[n], T, pl->D * 4, cudaMemcpyDeviceToDevice, s));
+    for (int n = 0; n < N; ++n) CUDA_TRY(cudaMemcpyAsync(pl->G[n], pl->Tc, pl->D * 4, cudaMemcpyDeviceToDevice, s));
     int64_t Is[PASD_MAXN];
     int Rs[PASD_MAXN], Rps[PASD_MAXN];
     for (int n = 0; n < N; ++n) { Is[n] = pl->m[n].I; Rs[n] = pl->m[n].R; Rps[n] = pl->m[n].Rp; }
-    launch_init_state(pl->sc, T, pl->p.mu0, N, pl->U, Is, Rs, Rps, pl->W, pl->F, pl->kept, s);
-    launch_norm_fro(T, pl->D, pl->sq_part, 1024, pl->sc, s);
+    launch_init_state(pl->sc, pl->Tc, pl->p.mu0, N, pl->U, Is, Rs, Rps, pl->W, pl->F, pl->Urot, pl->kept, s);
+    launch_norm_fro(pl->Tc, pl->D, pl->sq_part, 1024, pl->sc, s);
     CUDA_TRY(cudaGetLastError());
     return PASD_OK;
 }
@@ -468,10 +531,7 @@ extern "C" pasd_status pasd_finish(pasd_plan_t* pl, float* L, float* E, pasd_res
         return fail((pasd_status)r.status, "solve failed: non-finite values in the iterate");
     }
     // output: L = sum_n alpha_n Z_n / sum alpha_n, E (Algorithm 1, Output)
-    FusedArgs fo = pl->fu;
-    fo.output = 1;
-    fo.L = L;
-    launch_fused(fo, s);   // the output pass ignores the stop flag
+    launch_fused_pass(pl, 1, L, s);   // the output pass ignores the stop flag
     CUDA_TRY(cudaMemcpyAsync(E, pl->E, pl->D * 4, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());

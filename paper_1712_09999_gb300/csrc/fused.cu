@@ -26,14 +26,20 @@
 #include "pasd_impl.cuh"
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 
 namespace pasd {
 
 static inline int ilog2(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
 static inline int pow2ceil(int64_t v) { int p = 1; while (p < v) p <<= 1; return p; }
 
-bool plan_fused_geom(FusedGeom& g, int N, const int64_t* I, const int* Rp, int num_sms,
-                     size_t smem_limit) {
+static inline int round32(int x) { return (x + 31) / 32 * 32; }
+
+// Chooses the tile box, the region grid and the shared-memory layout. `tma`
+// selects the layout of fused_tma.cu (two stages of [Xs | As_n | Ws_n], dense
+// boxes) instead of the single-buffer layout of this file.
+bool plan_geom_impl(FusedGeom& g, int N, const int64_t* I, const int* Rp, int num_sms,
+                    size_t smem_limit, bool tma) {
     g = FusedGeom{};
     g.N = N;
     for (int n = 0; n < N; ++n) { g.I[n] = I[n]; g.Rp[n] = Rp[n]; }
@@ -88,21 +94,41 @@ bool plan_fused_geom(FusedGeom& g, int N, const int64_t* I, const int* Rp, int n
         // thread-id bit offsets of the micro-box coordinates (last mode fastest)
         int off = 0;
         for (int n = N - 1; n >= 0; --n) { g.mbsh[n] = off; off += ilog2(b[n] / g.mb[n]); }
-        // tiles and regions
+        // tiles and regions: one CTA per region, one resident CTA per SM, so the
+        // kernel takes ceil(regions / SMs) waves, each as long as its largest
+        // region. Pick the region grid Q minimising waves x max tiles per region.
         for (int n = 0; n < N; ++n) { g.nt[n] = (I[n] + b[n] - 1) / b[n]; g.Q[n] = 1; }
-        int64_t target = 2LL * num_sms;
-        for (;;) {
-            int64_t nreg = 1;
-            for (int n = 0; n < N; ++n) nreg *= g.Q[n];
-            if (nreg >= target) break;
-            int pick = -1; int64_t best = 1;
-            for (int n = 0; n < N; ++n) {
-                if (g.Q[n] >= g.nt[n]) continue;
-                int64_t per = (g.nt[n] + g.Q[n] - 1) / g.Q[n];
-                if (per > best) { best = per; pick = n; }
+        {
+            const int64_t cap = 4LL * num_sms;
+            int64_t best_cost = INT64_MAX, best_reg = INT64_MAX;
+            int q[PASD_MAXN], bq[PASD_MAXN];
+            for (int n = 0; n < N; ++n) { q[n] = 1; bq[n] = 1; }
+            // odometer over Q_n in [1, min(nt_n, cap)], pruned by the region cap
+            for (;;) {
+                int64_t reg = 1, mx = 1;
+                for (int n = 0; n < N; ++n) {
+                    reg *= q[n];
+                    mx *= (g.nt[n] + q[n] - 1) / q[n];
+                }
+                if (reg <= cap) {
+                    int64_t waves = (reg + num_sms - 1) / num_sms;
+                    int64_t cost = waves * mx;
+                    if (cost < best_cost || (cost == best_cost && reg < best_reg)) {
+                        best_cost = cost; best_reg = reg;
+                        for (int n = 0; n < N; ++n) bq[n] = q[n];
+                    }
+                }
+                int k = N - 1;
+                while (k >= 0) {
+                    int64_t rest = 1;
+                    for (int n = 0; n < N; ++n) rest *= (n == k) ? 1 : q[n];
+                    if (q[k] < g.nt[k] && rest * (q[k] + 1) <= cap) { ++q[k]; break; }
+                    q[k] = 1;
+                    --k;
+                }
+                if (k < 0) break;
             }
-            if (pick < 0) break;
-            g.Q[pick] += 1;
+            for (int n = 0; n < N; ++n) g.Q[n] = bq[n];
         }
         g.nregions = 1;
         for (int n = 0; n < N; ++n) g.nregions *= g.Q[n];
@@ -114,6 +140,40 @@ bool plan_fused_geom(FusedGeom& g, int N, const int64_t* I, const int* Rp, int n
             g.mp_combo_stride[n] = I[n] * Rp[n];
         }
         g.macc_floats = macc;
+        g.nthreads = B / 8;
+        if (tma) {
+            bool fits = true;
+            for (int n = 0; n < N; ++n) fits = fits && b[n] <= 256;
+            if (!fits) continue;
+            int o = 0;
+            g.xs_off = o; o += round32((N + 2) * B);
+            for (int n = 0; n < N; ++n) { g.as_off[n] = o; o += round32(g.C[n] * Rp[n]); }
+            for (int n = 0; n < N; ++n) { g.ws_off[n] = o; o += round32(b[n] * Rp[n]); }
+            g.stage_floats = round32(o);
+            int64_t tx = (int64_t)(N + 2) * B, txo = 0;
+            for (int n = 0; n < N; ++n) txo += (int64_t)g.C[n] * Rp[n] + (int64_t)b[n] * Rp[n];
+            g.stage_tx_bytes = (uint32_t)(4 * (tx + txo));
+            g.out_tx_bytes = (uint32_t)(4 * txo);
+            // the kernel runs the M_n product at every kept height h = 4, 8, ..., Rp_n,
+            // and fewer rows mean more split-K slices: size for the largest
+            int red = 16;
+            for (int n = 0; n < N; ++n) {
+                int MR = (n == N - 1) ? 4 : (b[n] >= 2 ? 2 : 1);
+                for (int h = 4; h <= Rp[n]; h += 4) {
+                    int nmt = (b[n] / MR) * (h / 4);
+                    int ns = 1;
+                    while ((nmt * ns * 2) <= g.nthreads) ns *= 2;
+                    red = std::max(red, 16 * ns * nmt);
+                }
+            }
+            g.red_off = 2 * g.stage_floats;
+            g.macc_base = g.red_off + round32(red);
+            g.smem_floats = g.macc_base + round32(macc);
+            g.tma = 1;
+            // +1 KB so the kernel can align its stages to 1024 bytes
+            if ((size_t)g.smem_floats * 4 + 1024 <= smem_limit) return true;
+            continue;
+        }
         int o = 0;
         for (int n = 0; n < N; ++n) { g.as_off[n] = o; o += g.C[n] * (Rp[n] + 4); }
         for (int n = 0; n < N; ++n) { g.ws_off[n] = o; o += b[n] * Rp[n]; }
@@ -131,6 +191,11 @@ bool plan_fused_geom(FusedGeom& g, int N, const int64_t* I, const int* Rp, int n
         if ((size_t)o * 4 <= smem_limit) return true;
     }
     return false;
+}
+
+bool plan_fused_geom(FusedGeom& g, int N, const int64_t* I, const int* Rp, int num_sms,
+                     size_t smem_limit) {
+    return plan_geom_impl(g, N, I, Rp, num_sms, smem_limit, false);
 }
 
 __device__ __forceinline__ float dot4(const float4& w, const float4& a, float acc) {

@@ -1,0 +1,688 @@
+// TMA-fed, double-buffered fused elementwise pass (same arithmetic as
+// fused.cu, which stays as the path for N > 5 or a contiguous mode whose
+// length is not a multiple of 4).
+//
+// Per tile (a box of extents b_n), one elected thread issues bulk tensor
+// copies (cp.async.bulk.tensor) into the next stage while the CTA computes the
+// current one:
+//   Xs   : T, E, G_0..G_{N-1} boxes, C order of the box (element index e)
+//   As_n : the A_n columns the tile needs, a box of the N-D tensor A_n
+//          ([pre][Rp][post] viewed with I_n replaced by Rp), i.e. smem layout
+//          [c_hi][r][c_lo] (c_lo = the post-mode part of the column index)
+//          for n < N-1 and [c][r] for the contiguous mode
+//   Ws_n : rows o_n .. o_n + b_n of Wz_n ([l][r])
+// Out-of-range parts of a box are zero-filled by the copy engine, so the
+// arithmetic below needs no masks: a zero element stays zero through the
+// update and adds nothing to the residual sums or the G A^T products.
+// Results (E', G_n') overwrite E and G_n in the stage and go back to HBM as
+// bulk tensor stores, clipped to the tensor by the copy engine.
+#include "pasd_impl.cuh"
+
+#include <cuda.h>
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+namespace pasd {
+
+bool plan_geom_impl(FusedGeom& g, int N, const int64_t* I, const int* Rp, int num_sms,
+                    size_t smem_limit, bool tma);
+
+// Tensor maps only: passed as a __grid_constant__ parameter because the bulk
+// copies take their address. Everything else goes in a plain by-value
+// parameter (constant-bank operands, no memory loads).
+constexpr int kTmaMaxN = 4;            // the TMA pass handles N <= 4
+constexpr int kHeights = PASD_MAXR / 4;  // one map per row count 4, 8, ..., 64
+struct FusedTmaMaps {
+    CUtensorMap tm_x[kTmaMaxN + 2];          // T copy, E, G_0..G_{N-1}
+    CUtensorMap tm_a[kTmaMaxN][kHeights];    // Vrot_n, first 4(h+1) rows
+    CUtensorMap tm_w[kTmaMaxN][kHeights];    // Urot_n, first 4(h+1) columns
+};
+
+struct FusedTmaPlan {
+    FusedTmaMaps maps;
+    FusedArgs base;
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after `limit` polls (each try_wait may suspend briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() {
+    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+
+template <int R>
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, const int* c) {
+    const uint32_t d = smem_u32(dst), b = smem_u32(bar);
+    const uint64_t m = reinterpret_cast<uint64_t>(map);
+    if (R == 1)
+        asm volatile("cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3}], [%2];\n"
+                     ::"r"(d), "l"(m), "r"(b), "r"(c[0]) : "memory");
+    else if (R == 2)
+        asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n"
+                     ::"r"(d), "l"(m), "r"(b), "r"(c[0]), "r"(c[1]) : "memory");
+    else if (R == 3)
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];\n"
+                     ::"r"(d), "l"(m), "r"(b), "r"(c[0]), "r"(c[1]), "r"(c[2]) : "memory");
+    else if (R == 4)
+        asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];\n"
+                     ::"r"(d), "l"(m), "r"(b), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]) : "memory");
+    else
+        asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, %7}], [%2];\n"
+                     ::"r"(d), "l"(m), "r"(b), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]) : "memory");
+}
+
+template <int R>
+__device__ __forceinline__ void tma_store(const CUtensorMap* map, const void* src, const int* c) {
+    const uint32_t s = smem_u32(src);
+    const uint64_t m = reinterpret_cast<uint64_t>(map);
+    if (R == 2)
+        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n"
+                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]) : "memory");
+    else if (R == 3)
+        asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];\n"
+                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]), "r"(c[2]) : "memory");
+    else if (R == 4)
+        asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];\n"
+                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]) : "memory");
+    else
+        asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];\n"
+                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]) : "memory");
+}
+
+constexpr uint32_t kWaitPolls = 1u << 22;   // bounded mbarrier wait (far above any real copy time)
+
+// ---------------------------------------------------------------------------
+// kernel
+// ---------------------------------------------------------------------------
+// Only the kept directions carry Z_n and M_n: with s_n kept singular values,
+// Z_n = Urot[:, :s] Vrot[:s] and M_n = G_n' Vrot[:s]^T, so per element and mode
+// the pass does sp_n = round_up(s_n, 4) multiply-adds for each, and loads only
+// sp_n rows of Vrot and columns of Urot (one tensor map per height).
+template <int N>
+__global__ void __launch_bounds__(FU_THREADS, 1)
+    fused_tma_kernel(const __grid_constant__ FusedTmaMaps tm, const FusedArgs fa, const int output,
+                     float* const Lout) {
+    DevScalars* sc = fa.sc;
+    if (!output && sc->done) return;
+    const FusedGeom& g = fa.g;
+    extern __shared__ __align__(1024) float sm_raw[];
+    // stage buffers aligned to 1024 bytes (the launch adds 1 KB of slack)
+    float* sm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full_bar[2];
+    __shared__ int tile_o[2][N];      // origins of the tiles in the two stages
+    const int t = threadIdx.x;
+    const int nthr = blockDim.x;
+    const int B = g.B;
+
+    int sp[N];                         // kept count rounded up to 4 (0: mode has no low-rank part)
+    uint32_t tx = output ? 0u : (uint32_t)(4 * (N + 2) * B);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        sp[n] = (sc->kept[n] + 3) & ~3;
+        tx += (uint32_t)(4 * (g.C[n] + g.b[n]) * sp[n]);
+    }
+
+    int q[N];
+    {
+        int r = blockIdx.x;
+        for (int n = N - 1; n >= 0; --n) { q[n] = r % g.Q[n]; r /= g.Q[n]; }
+    }
+    int64_t ts[N], te[N];
+    int64_t ntile = 1;
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        ts[n] = (int64_t)q[n] * g.nt[n] / g.Q[n];
+        te[n] = (int64_t)(q[n] + 1) * g.nt[n] / g.Q[n];
+        ntile *= te[n] - ts[n];
+    }
+    // odometer over the region's tiles (C order), advanced by the issuing thread
+    int tc[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) tc[n] = (int)ts[n];
+
+    // micro-box of this thread: 2 along mode N-2, 4 along mode N-1
+    int u0[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) u0[n] = ((t >> g.mbsh[n]) & (g.b[n] / g.mb[n] - 1)) * g.mb[n];
+    int e0 = 0;
+#pragma unroll
+    for (int n = 0; n < N; ++n) e0 += u0[n] << g.esh[n];
+    int cb[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        int c = 0;
+#pragma unroll
+        for (int m = 0; m < N; ++m)
+            if (m != n) c += u0[m] << g.csh[n][m];
+        cb[n] = c;
+    }
+
+    const double mu = sc->mu;
+    double mun = fa.rho * mu;
+    if (mun > fa.mu_max) mun = fa.mu_max;
+    const float cfac = (float)(mu / mun);
+    const float thr = (float)(1.0 / (mu * N));
+    const float invN = 1.0f / N;
+    float resmax = 0.f, l1 = 0.f, chk = 0.f, res2[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) res2[n] = 0.f;
+
+    float* macc = sm + g.macc_base;
+    float* red = sm + g.red_off;
+    if (!output)
+        for (int i = t; i < g.macc_floats; i += nthr) macc[i] = 0.f;
+    if (t == 0) {
+        mbar_init(&full_bar[0], 1);
+        mbar_init(&full_bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int st) {
+        int o[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) { o[n] = tc[n] * g.b[n]; tile_o[st][n] = o[n]; }
+#pragma unroll
+        for (int n = N - 1; n >= 0; --n) {
+            if (++tc[n] < te[n]) break;
+            tc[n] = (int)ts[n];
+        }
+        float* stg = sm + st * g.stage_floats;
+        uint64_t* bar = &full_bar[st];
+        mbar_expect_tx(bar, tx);
+        int cx[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) cx[k] = o[N - 1 - k];
+        if (!output)
+#pragma unroll
+            for (int a = 0; a < N + 2; ++a) tma_load<N>(stg + g.xs_off + a * B, &tm.tm_x[a], bar, cx);
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            if (sp[n] == 0) continue;
+            const int h = sp[n] / 4 - 1;
+            int ca[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) ca[k] = (N - 1 - k == n) ? 0 : o[N - 1 - k];
+            tma_load<N>(stg + g.as_off[n], &tm.tm_a[n][h], bar, ca);
+            int cw[2] = {0, o[n]};
+            tma_load<2>(stg + g.ws_off[n], &tm.tm_w[n][h], bar, cw);
+        }
+    };
+
+    bool failed = false;
+    if (t == 0 && ntile > 0) issue(0);
+    for (int64_t it = 0; it < ntile; ++it) {
+        const int st = (int)(it & 1);
+        const uint32_t par = (uint32_t)((it >> 1) & 1);
+        if (t == 0 && it + 1 < ntile) {
+            bulk_wait_read0();          // stores issued from the other stage have read their data
+            issue(st ^ 1);
+        }
+        bool ok = mbar_wait_bounded(&full_bar[st], par, kWaitPolls);
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        float* stg = sm + st * g.stage_floats;
+        float* Xs = stg + g.xs_off;
+        int o[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) o[n] = tile_o[st][n];
+
+        // ---- Z_n for the thread's 8 elements (j = d2 * 4 + d1), rank sp_n ----
+        float z[N][8];
+#pragma unroll
+        for (int n = 0; n < N; ++n)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) z[n][j] = 0.f;
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            const int h = sp[n];
+            if (h == 0) continue;
+            const float* As = stg + g.as_off[n];     // Vrot slice, row stride per block = h
+            const float* Ws = stg + g.ws_off[n];     // Urot rows [l][h]
+            if (n == N - 1) {
+                const float* Wt = Ws + u0[n] * h;
+                const float* At = As + cb[n] * h;
+                for (int r = 0; r < h; r += 4) {
+                    float4 w[4];
+#pragma unroll
+                    for (int d1 = 0; d1 < 4; ++d1) w[d1] = *reinterpret_cast<const float4*>(Wt + d1 * h + r);
+#pragma unroll
+                    for (int d2 = 0; d2 < 2; ++d2) {
+                        const float4 a = *reinterpret_cast<const float4*>(At + d2 * h + r);
+#pragma unroll
+                        for (int d1 = 0; d1 < 4; ++d1) {
+                            float acc = z[n][d2 * 4 + d1];
+                            acc = fmaf(w[d1].x, a.x, acc);
+                            acc = fmaf(w[d1].y, a.y, acc);
+                            acc = fmaf(w[d1].z, a.z, acc);
+                            z[n][d2 * 4 + d1] = fmaf(w[d1].w, a.w, acc);
+                        }
+                    }
+                }
+            } else {
+                const int H = g.esh[n];
+                const int chi = cb[n] >> H, clo = cb[n] & ((1 << H) - 1);
+                const int rs = 1 << H;
+                const float* Ab = As + ((chi * h) << H) + clo;
+                const float* Wt = Ws + u0[n] * h;
+                if (n == N - 2) {
+                    for (int r = 0; r < h; r += 4) {
+                        const float4 w0 = *reinterpret_cast<const float4*>(Wt + r);
+                        const float4 w1 = *reinterpret_cast<const float4*>(Wt + h + r);
+                        const float w0s[4] = {w0.x, w0.y, w0.z, w0.w}, w1s[4] = {w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const float4 a = *reinterpret_cast<const float4*>(Ab + (r + kk) * rs);
+                            z[n][0] = fmaf(w0s[kk], a.x, z[n][0]);
+                            z[n][1] = fmaf(w0s[kk], a.y, z[n][1]);
+                            z[n][2] = fmaf(w0s[kk], a.z, z[n][2]);
+                            z[n][3] = fmaf(w0s[kk], a.w, z[n][3]);
+                            z[n][4] = fmaf(w1s[kk], a.x, z[n][4]);
+                            z[n][5] = fmaf(w1s[kk], a.y, z[n][5]);
+                            z[n][6] = fmaf(w1s[kk], a.z, z[n][6]);
+                            z[n][7] = fmaf(w1s[kk], a.w, z[n][7]);
+                        }
+                    }
+                } else {
+                    const int s2 = 1 << g.csh[n][N - 2];
+                    for (int r = 0; r < h; r += 4) {
+                        const float4 w = *reinterpret_cast<const float4*>(Wt + r);
+                        const float ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+                            for (int d2 = 0; d2 < 2; ++d2) {
+                                const float4 a = *reinterpret_cast<const float4*>(Ab + (r + kk) * rs + d2 * s2);
+                                z[n][d2 * 4 + 0] = fmaf(ws[kk], a.x, z[n][d2 * 4 + 0]);
+                                z[n][d2 * 4 + 1] = fmaf(ws[kk], a.y, z[n][d2 * 4 + 1]);
+                                z[n][d2 * 4 + 2] = fmaf(ws[kk], a.z, z[n][d2 * 4 + 2]);
+                                z[n][d2 * 4 + 3] = fmaf(ws[kk], a.w, z[n][d2 * 4 + 3]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+
+        if (output) {
+            // L = sum_n alpha_n Z_n / sum alpha_n, stored directly (once per solve)
+            int64_t tbase = 0;
+            bool vbase = true;
+#pragma unroll
+            for (int n = 0; n < N; ++n) tbase += (int64_t)(o[n] + u0[n]) * g.stride[n];
+#pragma unroll
+            for (int n = 0; n < N - 2; ++n) vbase = vbase && (o[n] + u0[n] < g.I[n]);
+#pragma unroll
+            for (int d2 = 0; d2 < 2; ++d2) {
+                const bool v2 = vbase && (o[N - 2] + u0[N - 2] + d2 < g.I[N - 2]);
+                const int64_t rowoff = tbase + (int64_t)d2 * g.stride[N - 2];
+#pragma unroll
+                for (int d1 = 0; d1 < 4; ++d1) {
+                    if (v2 && (o[N - 1] + u0[N - 1] + d1 < g.I[N - 1])) {
+                        float s = 0.f;
+#pragma unroll
+                        for (int n = 0; n < N; ++n) s = fmaf(fa.alpha_w[n], z[n][d2 * 4 + d1], s);
+                        Lout[rowoff + d1] = s;
+                    }
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // ---- elementwise update, in place in the stage ----
+        //   gz_n = G_n - Z_n,  Ebar = mean_n(G_n + E - Z_n) = E + mean(gz),
+        //   E' = prox(Ebar),  d = T - E',  r_n = d - Z_n,
+        //   G_n' = d + (mu/mu') (gz_n + E - E')
+#pragma unroll
+        for (int d2 = 0; d2 < 2; ++d2) {
+            const int eb = e0 + (d2 << g.esh[N - 2]);
+            float4 x = *reinterpret_cast<const float4*>(Xs + eb);
+            const float tv[4] = {x.x, x.y, x.z, x.w};
+            x = *reinterpret_cast<const float4*>(Xs + B + eb);
+            const float ev[4] = {x.x, x.y, x.z, x.w};
+            float gv[N][4];
+#pragma unroll
+            for (int n = 0; n < N; ++n) {
+                x = *reinterpret_cast<const float4*>(Xs + (2 + n) * B + eb);
+                gv[n][0] = x.x; gv[n][1] = x.y; gv[n][2] = x.z; gv[n][3] = x.w;
+            }
+            float en[4];
+#pragma unroll
+            for (int d1 = 0; d1 < 4; ++d1) {
+                float sgz = 0.f;
+#pragma unroll
+                for (int n = 0; n < N; ++n) {
+                    gv[n][d1] -= z[n][d2 * 4 + d1];
+                    sgz += gv[n][d1];
+                }
+                const float ebar = fmaf(sgz, invN, ev[d1]);
+                const float mag = fabsf(ebar) - thr;
+                const float e = mag > 0.f ? copysignf(mag, ebar) : 0.f;
+                en[d1] = e;
+                const float d = tv[d1] - e;
+                const float qd = ev[d1] - e;
+#pragma unroll
+                for (int n = 0; n < N; ++n) {
+                    const float r = d - z[n][d2 * 4 + d1];
+                    resmax = fmaxf(resmax, fabsf(r));
+                    res2[n] = fmaf(r, r, res2[n]);
+                    const float gnew = fmaf(cfac, gv[n][d1] + qd, d);
+                    gv[n][d1] = gnew;
+                    chk += gnew;
+                }
+                l1 += fabsf(e);
+                chk += e;
+            }
+            *reinterpret_cast<float4*>(Xs + B + eb) = make_float4(en[0], en[1], en[2], en[3]);
+#pragma unroll
+            for (int n = 0; n < N; ++n)
+                *reinterpret_cast<float4*>(Xs + (2 + n) * B + eb) = make_float4(gv[n][0], gv[n][1], gv[n][2], gv[n][3]);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            int cx[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) cx[k] = o[N - 1 - k];
+#pragma unroll
+            for (int a = 1; a < N + 2; ++a) tma_store<N>(&tm.tm_x[a], Xs + a * B, cx);
+            bulk_commit();
+        }
+
+        // ---- M_n (W basis) += G_n' Vrot^T over this tile, kept rows only ----
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            const int h = sp[n];
+            if (h == 0) continue;
+            const int R4 = h / 4, Rp = g.Rp[n];
+            const int bn = g.b[n], Cn = g.C[n], H = g.esh[n], shn = g.sh[n];
+            const float* As = stg + g.as_off[n];
+            const float* Gn = Xs + (2 + n) * B;
+            const int MR = (n == N - 1) ? 4 : (bn >= 2 ? 2 : 1);
+            const int nmt = (bn / MR) * R4;
+            int lns = 0;                                   // slices: a power of two
+            while ((nmt << (lns + 1)) <= nthr) ++lns;
+            const int ns = 1 << lns;
+            for (int w = t; w < nmt * ns; w += nthr) {
+                const int sl = w & (ns - 1), mt = w >> lns;
+                const int rb = mt / R4, r4 = mt % R4;
+                const int l0 = rb * MR;
+                float acc[4][4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+                if (n == N - 1) {
+                    for (int c = sl; c < Cn; c += ns) {
+                        const float4 gg = *reinterpret_cast<const float4*>(Gn + (c << shn) + l0);
+                        const float4 a = *reinterpret_cast<const float4*>(As + c * h + 4 * r4);
+                        const float gs4[4] = {gg.x, gg.y, gg.z, gg.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            acc[i][0] = fmaf(gs4[i], a.x, acc[i][0]);
+                            acc[i][1] = fmaf(gs4[i], a.y, acc[i][1]);
+                            acc[i][2] = fmaf(gs4[i], a.z, acc[i][2]);
+                            acc[i][3] = fmaf(gs4[i], a.w, acc[i][3]);
+                        }
+                    }
+                } else {
+                    const int mask = (1 << H) - 1;
+                    for (int c4 = sl; c4 < Cn / 4; c4 += ns) {
+                        const int c = 4 * c4;
+                        const int chi = c >> H, clo = c & mask;
+                        float4 a[4];
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            a[kk] = *reinterpret_cast<const float4*>(As + ((chi * h + 4 * r4 + kk) << H) + clo);
+                        for (int i = 0; i < MR; ++i) {
+                            const float4 gg = *reinterpret_cast<const float4*>(Gn + (chi << (H + shn)) + ((l0 + i) << H) + clo);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                float s = acc[i][kk];
+                                s = fmaf(gg.x, a[kk].x, s);
+                                s = fmaf(gg.y, a[kk].y, s);
+                                s = fmaf(gg.z, a[kk].z, s);
+                                acc[i][kk] = fmaf(gg.w, a[kk].w, s);
+                            }
+                        }
+                    }
+                }
+                float* dst = red + (size_t)(sl * nmt + mt) * 16;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    *reinterpret_cast<float4*>(dst + 4 * i) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            }
+            __syncthreads();
+            float* mac = macc + g.macc_off[n];
+            const int64_t rowbase = ts[n] * bn;
+            for (int w = t; w < nmt * MR * 4; w += nthr) {
+                const int mt = w / (MR * 4), qq = w % (MR * 4);
+                const int i = qq / 4, k = qq % 4;
+                float s = 0.f;
+                for (int sl = 0; sl < ns; ++sl) s += red[(size_t)(sl * nmt + mt) * 16 + 4 * i + k];
+                const int rb = mt / R4, r4 = mt % R4;
+                const int64_t row = o[n] + rb * MR + i - rowbase;
+                mac[row * Rp + 4 * r4 + k] += s;
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+    if (t == 0) bulk_wait_read0();
+    if (failed) {
+        // a copy never arrived: record it and leave (the stage may still be written
+        // by a straggling copy, so wait on both barriers once more, bounded)
+        if (t == 0) {
+            mbar_wait_bounded(&full_bar[0], 0, kWaitPolls);
+            mbar_wait_bounded(&full_bar[1], 0, kWaitPolls);
+            sc->status = -5;   // PASD_ERR_TIMEOUT
+            sc->done = 1;
+            __threadfence();
+        }
+        return;
+    }
+    if (output) return;
+
+    // ---- flush this region's M_n sums ----
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        int64_t combo = 0;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            if (m == n) continue;
+            combo = combo * g.Q[m] + q[m];
+        }
+        const int Rp = g.Rp[n];
+        const int64_t rowbase = ts[n] * g.b[n];
+        int64_t rows = (te[n] - ts[n]) * g.b[n];
+        if (rowbase + rows > g.I[n]) rows = g.I[n] - rowbase;
+        float* dst = fa.mp_part[n] + combo * g.mp_combo_stride[n] + rowbase * Rp;
+        const float* mac = macc + g.macc_off[n];
+        for (int64_t idx = t; idx < rows * Rp; idx += nthr) dst[idx] = mac[idx];
+    }
+
+    // ---- block reductions of the residual statistics ----
+    __shared__ float wred[FU_THREADS / 32][PASD_MAXN + 3];
+    const int nonfin = !isfinite(chk);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        resmax = fmaxf(resmax, __shfl_down_sync(0xffffffffu, resmax, off));
+        l1 += __shfl_down_sync(0xffffffffu, l1, off);
+#pragma unroll
+        for (int n = 0; n < N; ++n) res2[n] += __shfl_down_sync(0xffffffffu, res2[n], off);
+    }
+    int nf = nonfin;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) nf |= __shfl_down_sync(0xffffffffu, nf, off);
+    const int wid = t >> 5, lane = t & 31;
+    if (lane == 0) {
+        wred[wid][0] = resmax;
+        wred[wid][1] = l1;
+        wred[wid][2] = (float)nf;
+#pragma unroll
+        for (int n = 0; n < N; ++n) wred[wid][3 + n] = res2[n];
+    }
+    __syncthreads();
+    if (t == 0) {
+        float mx = 0.f, s1 = 0.f, nfs = 0.f, s2[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) s2[n] = 0.f;
+        for (int w = 0; w < (nthr + 31) / 32; ++w) {
+            mx = fmaxf(mx, wred[w][0]);
+            s1 += wred[w][1];
+            nfs = fmaxf(nfs, wred[w][2]);
+#pragma unroll
+            for (int n = 0; n < N; ++n) s2[n] += wred[w][3 + n];
+        }
+        float* p = fa.part + (size_t)blockIdx.x * fa.part_stride;
+        p[0] = mx;
+        p[1] = s1;
+        p[2] = nfs;
+#pragma unroll
+        for (int n = 0; n < N; ++n) p[3 + n] = s2[n];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host: planning, tensor maps, launch
+// ---------------------------------------------------------------------------
+bool plan_fused_tma(FusedGeom& g, int N, const int64_t* I, const int* Rp, int num_sms,
+                    size_t smem_limit) {
+    if (N < 2 || N > kTmaMaxN) return false;
+    if (I[N - 1] % 4 != 0) return false;
+    for (int n = 0; n < N; ++n)
+        if (I[n] >= (int64_t)1 << 31) return false;
+    return plan_geom_impl(g, N, I, Rp, num_sms, smem_limit, true);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// dims / box innermost first
+static bool encode(CUtensorMap* m, const float* base, int rank, const uint64_t* dims, const uint32_t* box,
+                   char* err, size_t errlen, const char* what) {
+    EncodeTiledFn fn = get_encode();
+    if (!fn) {
+        snprintf(err, errlen, "cuTensorMapEncodeTiled unavailable");
+        return false;
+    }
+    cuuint64_t gd[5], gs[4];
+    cuuint32_t bd[5], es[5];
+    uint64_t stride = 4;
+    for (int k = 0; k < rank; ++k) {
+        gd[k] = dims[k];
+        bd[k] = box[k];
+        es[k] = 1;
+        if (k > 0) gs[k - 1] = stride;
+        stride *= dims[k];
+    }
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<float*>(base), gd, gs, bd, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(err, errlen, "cuTensorMapEncodeTiled(%s) failed with %d", what, (int)r);
+        return false;
+    }
+    return true;
+}
+
+FusedTmaPlan* make_fused_tma(const FusedArgs& a, const float* T_copy, char* err, size_t errlen) {
+    const FusedGeom& g = a.g;
+    const int N = g.N;
+    FusedTmaPlan* p = new FusedTmaPlan();
+    std::memset(&p->maps, 0, sizeof(p->maps));
+    p->base = a;
+    uint64_t dims[5];
+    uint32_t box[5];
+    for (int k = 0; k < N; ++k) { dims[k] = g.I[N - 1 - k]; box[k] = g.b[N - 1 - k]; }
+    const float* xs[PASD_MAXN + 2];
+    xs[0] = T_copy;
+    xs[1] = a.E;
+    for (int n = 0; n < N; ++n) xs[2 + n] = a.G[n];
+    for (int i = 0; i < N + 2; ++i)
+        if (!encode(&p->maps.tm_x[i], xs[i], N, dims, box, err, errlen, "element tile")) { delete p; return nullptr; }
+    for (int n = 0; n < N; ++n) {
+        for (int hh = 4; hh <= g.Rp[n]; hh += 4) {
+            uint64_t ad[5];
+            uint32_t ab[5];
+            for (int k = 0; k < N; ++k) {
+                int m = N - 1 - k;
+                if (m == n) { ad[k] = g.Rp[n]; ab[k] = hh; }
+                else { ad[k] = g.I[m]; ab[k] = g.b[m]; }
+            }
+            if (!encode(&p->maps.tm_a[n][hh / 4 - 1], a.A[n], N, ad, ab, err, errlen, "Vrot_n rows")) { delete p; return nullptr; }
+            uint64_t wd[2] = {(uint64_t)g.Rp[n], (uint64_t)g.I[n]};
+            uint32_t wb[2] = {(uint32_t)hh, (uint32_t)g.b[n]};
+            if (!encode(&p->maps.tm_w[n][hh / 4 - 1], a.Wz[n], 2, wd, wb, err, errlen, "Urot_n rows")) { delete p; return nullptr; }
+        }
+    }
+    return p;
+}
+
+void destroy_fused_tma(FusedTmaPlan* p) { delete p; }
+
+template <int N>
+static void launch_tma_n(FusedTmaPlan* p, int output, float* L, cudaStream_t s) {
+    const FusedGeom& g = p->base.g;
+    size_t smem = (size_t)g.smem_floats * 4 + 1024;
+    cudaFuncSetAttribute(fused_tma_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fused_tma_kernel<N><<<g.nregions, g.nthreads, smem, s>>>(p->maps, p->base, output, L);
+}
+
+void launch_fused_tma(FusedTmaPlan* p, int output, float* L, cudaStream_t s) {
+    switch (p->base.g.N) {
+        case 2: launch_tma_n<2>(p, output, L, s); break;
+        case 3: launch_tma_n<3>(p, output, L, s); break;
+        case 4: launch_tma_n<4>(p, output, L, s); break;
+        default: break;
+    }
+}
+
+}  // namespace pasd

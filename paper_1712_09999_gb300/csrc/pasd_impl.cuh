@@ -65,6 +65,9 @@ struct ApassArgs {
 };
 
 void launch_apass(const ApassArgs& a, cudaStream_t s);
+// All modes in as few launches as possible (one per distinct padded rank);
+// returns the number of launches.
+int launch_apass_modes(const ApassArgs* a, int N, cudaStream_t s);
 size_t apass_smem_bytes(int Rp, bool rowmajor);
 int apass_ncta(int64_t P);
 
@@ -76,14 +79,15 @@ struct SmallModeArgs {
     int R, Rp;
     double lambda;         // lambda_n
     float* U;              // I x Rp
-    float* Wz;             // I x Rp
+    float* Urot;           // I x Rp: U W, the subspace in the SVT eigenbasis
     float* W;              // Rp x Rp (columns = eigenvectors, by descending eigenvalue)
     float* F;              // Rp
     float* sigma;          // Rp
     const float* gram_part; int n_gram;     // [n_gram][Rp][Rp]
-    const float* mp_part; int n_mp;         // [n_mp][I][Rp]  (G A^T partials)
-    float* scratch;        // 4 * I * Rp floats
+    const float* Mred;     // I x Rp: G Vrot^T summed over regions (by finalize)
+    float* scratch;        // 4 * I * Rp floats (U-step matrices when not in smem)
     int32_t* kept;         // device int (per mode)
+    int polar_in_smem;     // 1: the U-step keeps its I x R matrices in shared memory
 };
 
 struct SmallArgs {
@@ -104,11 +108,34 @@ struct FinalizeArgs {
     double rho, mu_max, tol;
     int stop_rule, max_iter;
     double* trace;         // [max_iter][13]
+    // cross-region sums of G_n A_n^T
+    const float* mp_part[PASD_MAXN];   // [n_mp][I][Rp]
+    int n_mp[PASD_MAXN];
+    int64_t I[PASD_MAXN];
+    int R[PASD_MAXN], Rp[PASD_MAXN];
+    float* Mred[PASD_MAXN];            // [I][Rp]
 };
+size_t polar_smem_bytes(int maxRp, int64_t maxI);
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 void launch_init_state(DevScalars* sc, const float* T, double mu0, int N, float** U,
                        const int64_t* I, const int* R, const int* Rp, float** W, float** F,
-                       int32_t* kept, cudaStream_t s);
+                       float** Urot, int32_t* kept, cudaStream_t s);
+
+struct VrotMode {
+    const float* A;        // [pre][Rp][post]
+    float* V;              // [pre][Rp][post]
+    const float* W;        // Rp x Rp
+    const float* F;        // Rp
+    int64_t P, post;
+    int R, Rp;
+};
+struct VrotArgs {
+    int N;
+    const DevScalars* sc;
+    VrotMode m[PASD_MAXN];
+    int cta_start[PASD_MAXN + 1];
+};
+void launch_vrot(const VrotArgs& a, cudaStream_t s);
 void launch_norm_fro(const float* T, int64_t D, float* part, int nparts, DevScalars* sc,
                      cudaStream_t s);
 void launch_export_y(const float* G, const float* T, const float* E, const DevScalars* sc,
@@ -143,6 +170,13 @@ struct FusedGeom {
     int gs_off, red_off, macc_base;
     int smem_floats;
     int64_t mp_combo_stride[PASD_MAXN];  // floats per combo in mp_part[n] (= I_n * Rp_n)
+    // TMA-pipelined variant (two stages of [Xs | As_n | Ws_n], see fused_tma.cu)
+    int tma;                             // 1 when the TMA kernel is used
+    int nthreads;                        // B / 8
+    int stage_floats;                    // floats per stage
+    int xs_off;                          // element tiles (T, E, G_0..G_{N-1}) inside a stage
+    uint32_t stage_tx_bytes;             // bytes one stage's TMA loads deliver
+    uint32_t out_tx_bytes;               // bytes of the A / Wz loads only (output pass)
 };
 
 struct FusedArgs {
@@ -150,8 +184,8 @@ struct FusedArgs {
     DevScalars* sc;
     float* E;
     float* G[PASD_MAXN];
-    const float* A[PASD_MAXN];
-    const float* Wz[PASD_MAXN];
+    const float* A[PASD_MAXN];      // Vrot_n = diag(F) W^T A_n  (rows >= kept are zero)
+    const float* Wz[PASD_MAXN];     // Urot_n = U_n W           (Z_n = Urot Vrot)
     float* mp_part[PASD_MAXN];
     float* part;           // [nregions][stride] reduction partials
     int part_stride;
@@ -165,5 +199,16 @@ struct FusedArgs {
 bool plan_fused_geom(FusedGeom& g, int N, const int64_t* I, const int* Rp, int num_sms,
                      size_t smem_limit);
 void launch_fused(const FusedArgs& a, cudaStream_t s);
+
+// TMA-fed, double-buffered version of the fused pass (N <= 5, I_N % 4 == 0).
+// The element tiles come from plan-owned buffers (T is copied at begin), so the
+// tensor maps are fixed for the life of the plan.
+struct FusedTmaPlan;
+bool plan_fused_tma(FusedGeom& g, int N, const int64_t* I, const int* Rp, int num_sms,
+                    size_t smem_limit);
+// Encodes the tensor maps; returns false if the driver refuses one.
+FusedTmaPlan* make_fused_tma(const FusedArgs& a, const float* T_copy, char* err, size_t errlen);
+void destroy_fused_tma(FusedTmaPlan* p);
+void launch_fused_tma(FusedTmaPlan* p, int output, float* L, cudaStream_t s);
 
 }  // namespace pasd

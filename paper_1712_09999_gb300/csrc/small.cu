@@ -123,22 +123,32 @@ __device__ void sort_desc(const float* A, int n, int ld, int* perm) {
 }
 
 // C (ca x cb, ldc) = X^T Y over `rows` rows; X (rows x ldx), Y (rows x ldy).
-__device__ void block_AtB(const float* X, int ldx, const float* Y, int ldy, int64_t rows, int ca,
-                          int cb, float* C, int ldc) {
-    for (int idx = threadIdx.x; idx < ca * cb; idx += blockDim.x) {
-        int i = idx / cb, j = idx % cb;
+// One warp per output, lanes stride over the rows, shuffle reduction (fixed
+// order, so the result is deterministic). With `sym` (X == Y, ca == cb) only
+// the upper triangle is computed and mirrored.
+__device__ void warp_AtB(const float* X, int ldx, const float* Y, int ldy, int64_t rows, int ca, int cb,
+                         float* C, int ldc, bool sym) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = warp; o < ca * cb; o += nw) {
+        const int a = o / cb, b = o % cb;
+        if (sym && a > b) continue;
         float s = 0.f;
-        for (int64_t r = 0; r < rows; ++r) s = fmaf(X[r * ldx + i], Y[r * ldy + j], s);
-        C[i * ldc + j] = s;
+        for (int64_t r = lane; r < rows; r += 32) s = fmaf(X[r * ldx + a], Y[r * ldy + b], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) {
+            C[a * ldc + b] = s;
+            if (sym) C[b * ldc + a] = s;
+        }
     }
 }
 
-// Y (rows x cols, ldy) = X (rows x inner, ldx) * S (inner x cols, lds).
-__device__ void block_AB(const float* X, int ldx, const float* S, int lds, int64_t rows, int inner,
-                         int cols, float* Y, int ldy) {
+// Y[:, y0 + c] (rows x cols) = X (rows x inner) * S (inner x cols); one thread per output.
+__device__ void block_AB(const float* X, int ldx, const float* S, int lds, int64_t rows, int inner, int cols,
+                         float* Y, int ldy) {
     for (int64_t idx = threadIdx.x; idx < rows * cols; idx += blockDim.x) {
-        int64_t i = idx / cols;
-        int j = (int)(idx % cols);
+        const int64_t i = idx / cols;
+        const int j = (int)(idx % cols);
         float s = 0.f;
         for (int k = 0; k < inner; ++k) s = fmaf(X[i * ldx + k], S[k * lds + j], s);
         Y[i * ldy + j] = s;
@@ -186,21 +196,40 @@ __global__ void __launch_bounds__(SM_THREADS) svt_kernel(SmallArgs sa) {
     if (sc->done) return;
     const SmallModeArgs& m = sa.m[blockIdx.x];
     const int R = m.R, Rp = m.Rp, ld = Rp;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
     extern __shared__ __align__(16) float sm[];
     JacobiBufs jb = carve_jacobi(sm, ld);
-    float* Smat = sm + jacobi_floats(ld);       // ld x ld
+    float* Smat = sm + jacobi_floats(ld);       // ld x ld (sorted eigenvectors)
     float* fsh = Smat + ld * ld;                // ld
     int* perm = reinterpret_cast<int*>(fsh + ld);
+    float* red = reinterpret_cast<float*>(perm + ld);   // nw x 256
 
-    // 1. Gram matrix C = sum over CTA partials (fixed order)
-    for (int idx = t; idx < R * R; idx += blockDim.x) {
-        int i = idx / R, j = idx % R;
-        float s = 0.f;
-        for (int p = 0; p < m.n_gram; ++p) s += m.gram_part[(size_t)p * Rp * Rp + i * Rp + j];
-        jb.A[i * ld + j] = s;
+    // 1. Gram matrix = sum over the A-pass CTA partials: warp w owns partials
+    //    w, w + nw, ...; lanes own outputs; then a fixed-order sum over warps.
+    const int nout = Rp * Rp;
+    for (int obase = 0; obase < nout; obase += 256) {
+        float acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+        for (int p = warp; p < m.n_gram; p += nw) {
+            const float* src = m.gram_part + (size_t)p * nout + obase;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                int o = lane + 32 * k;
+                if (obase + o < nout) acc[k] += src[o];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) red[warp * 256 + lane + 32 * k] = acc[k];
+        __syncthreads();
+        for (int o = t; o < 256 && obase + o < nout; o += blockDim.x) {
+            float s = 0.f;
+            for (int w = 0; w < nw; ++w) s += red[w * 256 + o];
+            int oo = obase + o, i = oo / Rp, j = oo % Rp;
+            if (i < R && j < R) jb.A[i * ld + j] = s;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // 2. eigen-decomposition
     float *Ae, *Ve;
     block_jacobi(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, R, ld, 1e-6f, 30, &Ae, &Ve);
@@ -220,7 +249,6 @@ __global__ void __launch_bounds__(SM_THREADS) svt_kernel(SmallArgs sa) {
         m.sigma[t] = sig;
         m.F[t] = f;
     }
-    // W (sorted columns) -> global, padded
     for (int idx = t; idx < Rp * Rp; idx += blockDim.x) {
         int i = idx / Rp, j = idx % Rp;
         float v = 0.f;
@@ -240,22 +268,21 @@ __global__ void __launch_bounds__(SM_THREADS) svt_kernel(SmallArgs sa) {
         sc->kept[blockIdx.x] = kept;
         sc->nuclear[blockIdx.x] = nuc;
     }
-    // 4. S = W diag(F) W^T
+    // 4. Urot = U W (I x Rp): the active subspace in the eigenbasis of the SVT.
+    //    With Vrot = diag(F) W^T A_n (rows beyond the kept count are zero),
+    //    fold_n(U_n V_n) = Urot[:, :s] Vrot[:s], the refold of rank s.
     for (int idx = t; idx < R * R; idx += blockDim.x) {
         int i = idx / R, j = idx % R;
-        float s = 0.f;
-        for (int k = 0; k < R; ++k) s = fmaf(Ve[i * ld + perm[k]] * fsh[k], Ve[j * ld + perm[k]], s);
-        Smat[i * ld + j] = s;
+        Smat[i * ld + j] = Ve[i * ld + perm[j]];
     }
     __syncthreads();
-    // 5. Wz = U S (I x Rp, zero padding columns)
     for (int64_t idx = t; idx < m.I * Rp; idx += blockDim.x) {
         int64_t i = idx / Rp;
         int j = (int)(idx % Rp);
         float s = 0.f;
         if (j < R)
             for (int k = 0; k < R; ++k) s = fmaf(m.U[i * Rp + k], Smat[k * ld + j], s);
-        m.Wz[idx] = s;
+        m.Urot[idx] = s;
     }
 }
 
@@ -266,7 +293,8 @@ __global__ void __launch_bounds__(SM_THREADS) svt_kernel(SmallArgs sa) {
 //   U = [ P1 , X ],  P1 = polar(M_n[:, :s]),  X = polar((I - P1 P1^T) (U W)[:, s:]),
 // i.e. the unique polar factor on the range of M_n and, on its null space, the
 // isometry closest to the previous iterate (identity at k = 0, where s = 0).
-// A closing Newton-Schulz step re-orthonormalises U.
+// A closing Newton-Schulz step re-orthonormalises U. The I x R matrices live in
+// shared memory (row stride Rp + 1) when they fit, else in the global scratch.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
     DevScalars* sc = sa.sc;
@@ -277,90 +305,66 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
     const int t = threadIdx.x;
     extern __shared__ __align__(16) float sm[];
     JacobiBufs jb = carve_jacobi(sm, ld);
-    float* Wsh = sm + jacobi_floats(ld);   // ld x ld
-    float* Z = Wsh + ld * ld;              // ld x ld
-    float* K = Z + ld * ld;                // ld x ld
-    float* fsh = K + ld * ld;              // ld
+    float* Z = sm + jacobi_floats(ld) + ld * ld;   // ld x ld
+    float* K = Z + ld * ld;                        // ld x ld
+    float* big = K + ld * ld + 2 * ld + 64;        // 3 x I x LD when it fits
+    const bool in_smem = m.polar_in_smem != 0;
+    const int LD = in_smem ? Rp + 1 : Rp;
+    float* Mw = in_smem ? big : m.scratch;                 // [P1 | X]
+    float* Pw = Mw + I * LD;                               // M in the W basis
+    float* Bw = Pw + I * LD;                               // (U W)[:, s:], then B
 
     const int s = *m.kept;
     const int q = R - s;
-    float* Mp = m.scratch;                 // I x Rp : reduced G A^T
-    float* Mr = Mp + I * Rp;               // I x Rp : M in the W basis, then B
-    float* Ur = Mr + I * Rp;               // I x Rp : U W (null columns)
-    float* Un = Ur + I * Rp;               // I x Rp : new U before re-orthonormalisation
-
-    for (int idx = t; idx < Rp * Rp; idx += blockDim.x) Wsh[idx] = m.W[idx];
-    if (t < Rp) fsh[t] = m.F[t];
-    __syncthreads();
 
     if (s > 0) {
-        // M' = sum of partials (fixed order), columns r < R
-        for (int64_t idx = t; idx < I * R; idx += blockDim.x) {
-            int64_t i = idx / R;
-            int r = (int)(idx % R);
-            float acc = 0.f;
-            for (int p = 0; p < m.n_mp; ++p) acc += m.mp_part[(size_t)p * I * Rp + i * Rp + r];
-            Mp[i * Rp + r] = acc;
-        }
-        __syncthreads();
-        // M = M' W[:, :s] diag(F[:s])
+        // M in the W basis: G_n Vrot^T, summed over regions by the finalize kernel
         for (int64_t idx = t; idx < I * s; idx += blockDim.x) {
             int64_t i = idx / s;
             int c = (int)(idx % s);
-            float acc = 0.f;
-            for (int r = 0; r < R; ++r) acc = fmaf(Mp[i * Rp + r], Wsh[r * ld + c], acc);
-            Mr[i * Rp + c] = acc * fsh[c];
+            Pw[i * LD + c] = m.Mred[i * Rp + c];
         }
         __syncthreads();
-        // B1 = M^T M (s x s), eigen -> Z1 = B1^{-1/2}; P1 = M Z1
-        block_AtB(Mr, Rp, Mr, Rp, I, s, s, jb.A, ld);
+        // B1 = M^T M, Z1 = B1^{-1/2}, P1 = M Z1
+        warp_AtB(Pw, LD, Pw, LD, I, s, s, jb.A, ld, true);
         __syncthreads();
         float *Ae, *Ve;
         block_jacobi(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, s, ld, 1e-6f, 30, &Ae, &Ve);
         inv_sqrt_from_eig(Ae, Ve, s, ld, Z);
-        block_AB(Mr, Rp, Z, ld, I, s, s, Un, Rp);
+        block_AB(Pw, LD, Z, ld, I, s, s, Mw, LD);
         __syncthreads();
     }
     if (q > 0) {
-        // Ur = U W[:, s:]
+        // (U W)[:, s:], from the SVT of the previous loop body (eye at k = 0)
         for (int64_t idx = t; idx < I * q; idx += blockDim.x) {
             int64_t i = idx / q;
             int c = (int)(idx % q);
-            float acc = 0.f;
-            for (int r = 0; r < R; ++r) acc = fmaf(m.U[i * Rp + r], Wsh[r * ld + s + c], acc);
-            Ur[i * Rp + c] = acc;
+            Bw[i * LD + c] = m.Urot[i * Rp + s + c];
         }
         __syncthreads();
-        float* Bm = Mr;   // reuse
         if (s > 0) {
             // K = P1^T Ur (s x q);  B = Ur - P1 K
-            block_AtB(Un, Rp, Ur, Rp, I, s, q, K, ld);
+            warp_AtB(Mw, LD, Bw, LD, I, s, q, K, ld, false);
             __syncthreads();
             for (int64_t idx = t; idx < I * q; idx += blockDim.x) {
                 int64_t i = idx / q;
                 int c = (int)(idx % q);
-                float acc = Ur[i * Rp + c];
-                for (int k = 0; k < s; ++k) acc = fmaf(-Un[i * Rp + k], K[k * ld + c], acc);
-                Bm[i * Rp + c] = acc;
+                float acc = Bw[i * LD + c];
+                for (int k = 0; k < s; ++k) acc = fmaf(-Mw[i * LD + k], K[k * ld + c], acc);
+                Bw[i * LD + c] = acc;
             }
-        } else {
-            for (int64_t idx = t; idx < I * q; idx += blockDim.x) {
-                int64_t i = idx / q;
-                int c = (int)(idx % q);
-                Bm[i * Rp + c] = Ur[i * Rp + c];
-            }
+            __syncthreads();
         }
-        __syncthreads();
-        block_AtB(Bm, Rp, Bm, Rp, I, q, q, jb.A, ld);
+        warp_AtB(Bw, LD, Bw, LD, I, q, q, jb.A, ld, true);
         __syncthreads();
         float *Ae, *Ve;
         block_jacobi(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, q, ld, 1e-6f, 30, &Ae, &Ve);
         inv_sqrt_from_eig(Ae, Ve, q, ld, Z);
-        block_AB(Bm, Rp, Z, ld, I, q, q, Un + s, Rp);
+        block_AB(Bw, LD, Z, ld, I, q, q, Mw + s, LD);
         __syncthreads();
     }
     // Newton-Schulz: U = Un (3 I - Un^T Un) / 2
-    block_AtB(Un, Rp, Un, Rp, I, R, R, K, ld);
+    warp_AtB(Mw, LD, Mw, LD, I, R, R, K, ld, true);
     __syncthreads();
     for (int idx = t; idx < R * R; idx += blockDim.x) {
         int i = idx / R, j = idx % R;
@@ -372,90 +376,132 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
         int j = (int)(idx % Rp);
         float acc = 0.f;
         if (j < R)
-            for (int k = 0; k < R; ++k) acc = fmaf(Un[i * Rp + k], Z[k * ld + j], acc);
+            for (int k = 0; k < R; ++k) acc = fmaf(Mw[i * LD + k], Z[k * ld + j], acc);
         m.U[idx] = acc;
     }
 }
 
-static size_t small_smem_bytes(int maxRp) {
+static size_t small_base_floats(int maxRp) {
     int ld = maxRp;
-    return 4 * (size_t)(jacobi_floats(ld) + 3 * ld * ld + 2 * ld + 64);
+    return (size_t)jacobi_floats(ld) + 3 * ld * ld + 2 * ld + 64;
+}
+static size_t svt_smem_bytes(int maxRp) {
+    return 4 * (small_base_floats(maxRp) + (size_t)(SM_THREADS / 32) * 256);
+}
+// Bytes of shared memory the U-step needs with its I x R matrices resident.
+size_t polar_smem_bytes(int maxRp, int64_t maxI) {
+    return 4 * (small_base_floats(maxRp) + 3 * (size_t)maxI * (maxRp + 1));
 }
 
 void launch_svt(const SmallArgs& a, cudaStream_t s) {
     int maxRp = 4;
     for (int n = 0; n < a.N; ++n) maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
-    size_t smem = small_smem_bytes(maxRp);
+    size_t smem = svt_smem_bytes(maxRp);
     cudaFuncSetAttribute(svt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     svt_kernel<<<a.N, SM_THREADS, smem, s>>>(a);
 }
 
 void launch_polar(const SmallArgs& a, cudaStream_t s) {
     int maxRp = 4;
-    for (int n = 0; n < a.N; ++n) maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
-    size_t smem = small_smem_bytes(maxRp);
+    int64_t maxI = 1;
+    bool any_smem = false;
+    for (int n = 0; n < a.N; ++n) {
+        maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
+        if (a.m[n].polar_in_smem) { any_smem = true; maxI = a.m[n].I > maxI ? a.m[n].I : maxI; }
+    }
+    size_t smem = any_smem ? polar_smem_bytes(maxRp, maxI) : 4 * small_base_floats(maxRp);
     cudaFuncSetAttribute(polar_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     polar_kernel<<<a.N, SM_THREADS, smem, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------
-// Finalize one loop body: residual norms of T - Z_n - E (the stop test of
-// Algorithm 1), objective of Eq. 3, mu schedule, iteration record.
-// part layout per CTA: [0] max |T - Z_n - E|, [1] sum |E|, [2] non-finite flag,
-// [3 + n] sum (T - Z_n - E)^2.
+// Finalize one loop body. CTA 0: residual norms of T - Z_n - E (the stop test
+// of Algorithm 1), objective of Eq. 3, mu schedule, iteration record. Other
+// CTAs: the fixed-order sum of the per-region G_n A_n^T partials (one output
+// per thread), which the next U-step reads.
+// part layout per region: [0] max |T - Z_n - E|, [1] sum |E|, [2] non-finite
+// flag, [3 + n] sum (T - Z_n - E)^2.
 // ---------------------------------------------------------------------------
 __global__ void finalize_kernel(FinalizeArgs fa) {
     DevScalars* sc = fa.sc;
     if (sc->done) return;
-    __shared__ double sh[32][PASD_MAXN + 3];
     const int t = threadIdx.x, nt = blockDim.x;
+    if (blockIdx.x > 0) {
+        int64_t o = (int64_t)(blockIdx.x - 1) * nt + t;
+        for (int n = 0; n < fa.N; ++n) {
+            const int64_t cnt = fa.I[n] * fa.R[n];
+            if (o < cnt) {
+                const int64_t i = o / fa.R[n];
+                const int r = (int)(o % fa.R[n]);
+                float acc = 0.f;
+                if (r < sc->kept[n]) {      // only the kept directions carry G V^T
+                    const int64_t stride = fa.I[n] * fa.Rp[n];
+                    const float* src = fa.mp_part[n] + i * fa.Rp[n] + r;
+#pragma unroll 8
+                    for (int p = 0; p < fa.n_mp[n]; ++p) acc += src[(int64_t)p * stride];
+                }
+                fa.Mred[n][i * fa.Rp[n] + r] = acc;
+                return;
+            }
+            o -= cnt;
+        }
+        return;
+    }
+    __shared__ double sh[32][PASD_MAXN + 3];
     double mx = 0.0, l1 = 0.0, nf = 0.0;
     double r2[PASD_MAXN];
+#pragma unroll
     for (int n = 0; n < PASD_MAXN; ++n) r2[n] = 0.0;
-    // deterministic: thread t owns parts t, t + nt, ...; then a fixed tree
     for (int p = t; p < fa.nparts; p += nt) {
         const float* q = fa.part + (size_t)p * fa.stride;
         mx = fmax(mx, (double)q[0]);
         l1 += (double)q[1];
         nf = fmax(nf, (double)q[2]);
-        for (int n = 0; n < fa.N; ++n) r2[n] += (double)q[3 + n];
+#pragma unroll
+        for (int n = 0; n < PASD_MAXN; ++n)
+            if (n < fa.N) r2[n] += (double)q[3 + n];
     }
-    // warp reduce
+#pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
         l1 += __shfl_down_sync(0xffffffffu, l1, off);
         nf = fmax(nf, __shfl_down_sync(0xffffffffu, nf, off));
-        for (int n = 0; n < fa.N; ++n) r2[n] += __shfl_down_sync(0xffffffffu, r2[n], off);
+#pragma unroll
+        for (int n = 0; n < PASD_MAXN; ++n) r2[n] += __shfl_down_sync(0xffffffffu, r2[n], off);
     }
-    int w = t >> 5, lane = t & 31;
+    const int w = t >> 5, lane = t & 31;
     if (lane == 0) {
         sh[w][0] = mx; sh[w][1] = l1; sh[w][2] = nf;
-        for (int n = 0; n < fa.N; ++n) sh[w][3 + n] = r2[n];
+#pragma unroll
+        for (int n = 0; n < PASD_MAXN; ++n) sh[w][3 + n] = r2[n];
     }
     __syncthreads();
     if (t == 0) {
-        int nw = (nt + 31) / 32;
+        const int nw = (nt + 31) / 32;
         for (int i = 1; i < nw; ++i) {
             mx = fmax(mx, sh[i][0]);
             l1 += sh[i][1];
             nf = fmax(nf, sh[i][2]);
-            for (int n = 0; n < fa.N; ++n) r2[n] += sh[i][3 + n];
+#pragma unroll
+            for (int n = 0; n < PASD_MAXN; ++n) r2[n] += sh[i][3 + n];
         }
         double r2max = 0.0;
-        for (int n = 0; n < fa.N; ++n) r2max = fmax(r2max, r2[n]);
-        double tn = sc->t_norm_fro;
-        double fro_rel = tn > 0 ? sqrt(r2max) / tn : 0.0;
+#pragma unroll
+        for (int n = 0; n < PASD_MAXN; ++n)
+            if (n < fa.N) r2max = fmax(r2max, r2[n]);
+        const double tn = sc->t_norm_fro;
+        const double fro_rel = tn > 0 ? sqrt(r2max) / tn : 0.0;
         double obj = l1;
         for (int n = 0; n < fa.N; ++n) obj += fa.lambda[n] * sc->nuclear[n];
-        double mu = sc->mu;
+        const double mu = sc->mu;
         sc->res_inf = mx;
         sc->res_fro_rel = fro_rel;
         sc->objective = obj;
         sc->l1_E = l1;
         sc->mu_used = mu;
-        double mun = fa.rho * mu;
+        const double mun = fa.rho * mu;
         sc->mu = mun < fa.mu_max ? mun : fa.mu_max;
-        int k = sc->k + 1;
+        const int k = sc->k + 1;
         sc->k = k;
         if (fa.trace && k <= fa.max_iter) {
             double* rec = fa.trace + (size_t)(k - 1) * 13;
@@ -477,7 +523,49 @@ __global__ void finalize_kernel(FinalizeArgs fa) {
 }
 
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
-    finalize_kernel<<<1, 256, 0, s>>>(a);
+    int64_t tot = 0;
+    for (int n = 0; n < a.N; ++n) tot += a.I[n] * a.R[n];
+    int grid = 1 + (int)((tot + 255) / 256);
+    finalize_kernel<<<grid, 256, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// Vrot_n = diag(F) W^T A_n: the small factor V_n of Eq. 13 in the eigenbasis of
+// the SVT, stored like A_n ([pre][Rp][post]); rows at and beyond the kept
+// count are zero. One thread per unfolding column, all modes in one launch.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
+    const DevScalars* sc = va.sc;
+    if (sc->done) return;
+    int k = 0;
+    while (k + 1 < va.N && (int)blockIdx.x >= va.cta_start[k + 1]) ++k;
+    const VrotMode& m = va.m[k];
+    const int R = m.R, Rp = m.Rp;
+    const int s = sc->kept[k];
+    __shared__ float Wt[PASD_MAXR * PASD_MAXR];   // Wt[i][r] = F_i W[r][i]
+    for (int idx = threadIdx.x; idx < s * R; idx += blockDim.x) {
+        int i = idx / R, r = idx % R;
+        Wt[i * R + r] = m.F[i] * m.W[r * Rp + i];
+    }
+    __syncthreads();
+    const int64_t j = (int64_t)(blockIdx.x - va.cta_start[k]) * blockDim.x + threadIdx.x;
+    if (j >= m.P) return;
+    const int64_t a = j / m.post, b = j % m.post;
+    const float* src = m.A + a * Rp * m.post + b;
+    float* dst = m.V + a * Rp * m.post + b;
+    float av[PASD_MAXR];
+#pragma unroll 4
+    for (int r = 0; r < R; ++r) av[r] = src[(int64_t)r * m.post];
+    for (int i = 0; i < Rp; ++i) {
+        float acc = 0.f;
+        if (i < s)
+            for (int r = 0; r < R; ++r) acc = fmaf(Wt[i * R + r], av[r], acc);
+        dst[(int64_t)i * m.post] = acc;
+    }
+}
+
+void launch_vrot(const VrotArgs& a, cudaStream_t s) {
+    vrot_kernel<<<a.cta_start[a.N], 256, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -494,6 +582,7 @@ struct InitArgs {
     int Rp[PASD_MAXN];
     float* W[PASD_MAXN];
     float* F[PASD_MAXN];
+    float* Urot[PASD_MAXN];
     int32_t* kept;
 };
 
@@ -506,7 +595,9 @@ __global__ void init_kernel(InitArgs a) {
          idx += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = idx / Rp;
         int r = (int)(idx % Rp);
-        a.U[n][idx] = (i == r && r < a.R[n]) ? 1.f : 0.f;   // eye(I_n, R_n), zero padding
+        const float v = (i == r && r < a.R[n]) ? 1.f : 0.f;   // eye(I_n, R_n), zero padding
+        a.U[n][idx] = v;
+        a.Urot[n][idx] = v;                                     // U W with W = I
     }
     if (blockIdx.x == 0) {
         for (int idx = threadIdx.x; idx < Rp * Rp; idx += blockDim.x)
@@ -530,11 +621,12 @@ __global__ void init_kernel(InitArgs a) {
 
 void launch_init_state(DevScalars* sc, const float* T, double mu0, int N, float** U,
                        const int64_t* I, const int* R, const int* Rp, float** W, float** F,
-                       int32_t* kept, cudaStream_t s) {
+                       float** Urot, int32_t* kept, cudaStream_t s) {
     InitArgs a;
     a.sc = sc; a.T = T; a.mu0 = mu0; a.N = N; a.kept = kept;
     for (int n = 0; n < N; ++n) {
         a.U[n] = U[n]; a.I[n] = I[n]; a.R[n] = R[n]; a.Rp[n] = Rp[n]; a.W[n] = W[n]; a.F[n] = F[n];
+        a.Urot[n] = Urot[n];
     }
     init_kernel<<<dim3(32, N), 256, 0, s>>>(a);
 }
