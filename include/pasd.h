@@ -224,9 +224,10 @@ pasd_status pasd_mode_product_noalloc(const float* X, int64_t pre, int64_t I, in
  * events on that stream, synchronizes, and writes the summed milliseconds per
  * group into kernel_ms[0 .. PASD_PROFILE_SLOTS-1] in this order:
  *   0 polar (U-step), 1 A-pass (all modes), 2 SVT, 3 Vrot (small factor in the
- *   SVT eigenbasis), 4 fused elementwise pass, 5 finalize.
+ *   SVT eigenbasis), 4 fused elementwise pass, 5 M-pass (the next U-step's
+ *   product G_n V_n^T), 6 finalize.
  * The solver state advances exactly as with pasd_iterate. */
-#define PASD_PROFILE_SLOTS 6
+#define PASD_PROFILE_SLOTS 7
 pasd_status pasd_profile_iterations(pasd_plan_t* plan, int32_t iters, double* kernel_ms,
                                     void* stream);
 

@@ -100,6 +100,8 @@ struct pasd_plan {
     FusedArgs fu{};
     FinalizeArgs fin{};
     VrotArgs vr{};
+    MpassArgs mpa{};
+    size_t mp_smem = 0;
     // graph
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -243,9 +245,40 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     pl->want_tma = !(nt && nt[0] == '1') &&
                    plan_fused_tma(pl->fg, N, Is, Rps, c->num_sms, c->smem_optin);
     if (!pl->want_tma) pl->fg = pl->fg_plain;
-    for (int n = 0; n < N; ++n) {
-        pl->ncta_ap[n] = apass_ncta(pl->m[n].P);
-        pl->n_mp[n] = std::max(pl->fg.nregions / pl->fg.Q[n], pl->fg_plain.nregions / pl->fg_plain.Q[n]);
+    for (int n = 0; n < N; ++n) pl->ncta_ap[n] = apass_ncta(pl->m[n].P);
+    // M-pass: row strips x column ranges, as many CTAs as fit on the device at
+    // once (one wave), split over the modes in proportion to their columns
+    {
+        int64_t work[PASD_MAXN], tot = 0;
+        size_t smem = 0;
+        for (int n = 0; n < N; ++n) {
+            const ModeGeom& g = pl->m[n];
+            MpassMode& mm = pl->mpa.m[n];
+            mm.I = g.I; mm.post = g.post; mm.P = g.P; mm.Rp = g.Rp;
+            mm.variant = mpass_variant(g.I, g.post);
+            mm.IS = mpass_strip_rows(g.I, g.Rp);
+            mm.nstrips = (int)((g.I + mm.IS - 1) / mm.IS);
+            work[n] = (int64_t)mm.nstrips * ((g.P + MP_CB - 1) / MP_CB);
+            tot += work[n];
+            smem = std::max(smem, mpass_smem_bytes(mm.IS, g.Rp, mm.variant));
+        }
+        const int slots = c->num_sms * mpass_ctas_per_sm(smem);
+        int start = 0;
+        for (int n = 0; n < N; ++n) {
+            MpassMode& mm = pl->mpa.m[n];
+            int64_t target = (int64_t)((double)slots * (double)work[n] / (double)tot);
+            int64_t ncg = std::max<int64_t>(1, target / mm.nstrips);
+            int64_t cols = (mm.P + ncg - 1) / ncg;
+            cols = (cols + MP_CB - 1) / MP_CB * MP_CB;
+            mm.cols_per_cg = cols;
+            mm.ncg = (int)((mm.P + cols - 1) / cols);
+            pl->n_mp[n] = mm.ncg;
+            pl->mpa.cta_start[n] = start;
+            start += mm.nstrips * mm.ncg;
+        }
+        pl->mpa.cta_start[N] = start;
+        pl->mpa.N = N;
+        pl->mp_smem = smem;
     }
     int nparts = std::max(pl->fg.nregions, pl->fg_plain.nregions);
     // footprint
@@ -291,6 +324,7 @@ static void enqueue_iteration(pasd_plan_t* pl, cudaStream_t s) {
     launch_svt(pl->small, s);
     launch_vrot(pl->vr, s);
     launch_fused_pass(pl, 0, nullptr, s);
+    launch_mpass(pl->mpa, pl->mp_smem, s);
     launch_finalize(pl->fin, s);
 }
 
@@ -356,7 +390,7 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
     double asum = 0;
     for (int n = 0; n < N; ++n) asum += pl->alpha[n];
     for (int n = 0; n < N; ++n) {
-        fu.G[n] = pl->G[n]; fu.A[n] = pl->Vr[n]; fu.Wz[n] = pl->Urot[n]; fu.mp_part[n] = pl->mp[n];
+        fu.G[n] = pl->G[n]; fu.A[n] = pl->Vr[n]; fu.Wz[n] = pl->Urot[n];
         fu.alpha_w[n] = (float)(pl->alpha[n] / asum);
     }
     fu.part = pl->part;
@@ -375,6 +409,11 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
         vm.A = pl->A[n]; vm.V = pl->Vr[n]; vm.W = pl->W[n]; vm.F = pl->F[n];
         vm.P = g.P; vm.post = g.post; vm.R = g.R; vm.Rp = g.Rp;
         va.cta_start[n + 1] = va.cta_start[n] + (int)((g.P + 255) / 256);
+    }
+    pl->mpa.sc = pl->sc;
+    for (int n = 0; n < N; ++n) {
+        MpassMode& mm = pl->mpa.m[n];
+        mm.G = pl->G[n]; mm.V = pl->Vr[n]; mm.part = pl->mp[n];
     }
     FinalizeArgs& fi = pl->fin;
     fi.N = N; fi.sc = pl->sc; fi.part = pl->part; fi.nparts = pl->fg.nregions; fi.stride = 3 + N;
@@ -400,7 +439,7 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
             fi.nparts = pl->fg.nregions;
         }
     }
-    for (int n = 0; n < N; ++n) fi.n_mp[n] = pl->fg.nregions / pl->fg.Q[n];
+    for (int n = 0; n < N; ++n) fi.n_mp[n] = pl->n_mp[n];
 
     if (pl->use_graph) {
         CUDA_TRY(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -447,9 +486,11 @@ extern "C" pasd_status pasd_profile_iterations(pasd_plan_t* pl, int32_t iters, d
         CUDA_TRY(cudaEventRecord(ev[4], s));
         launch_fused_pass(pl, 0, nullptr, s);
         CUDA_TRY(cudaEventRecord(ev[5], s));
-        launch_finalize(pl->fin, s);
+        launch_mpass(pl->mpa, pl->mp_smem, s);
         CUDA_TRY(cudaEventRecord(ev[6], s));
-        CUDA_TRY(cudaEventSynchronize(ev[6]));
+        launch_finalize(pl->fin, s);
+        CUDA_TRY(cudaEventRecord(ev[7], s));
+        CUDA_TRY(cudaEventSynchronize(ev[7]));
         for (int k = 0; k < PASD_PROFILE_SLOTS; ++k) {
             float t = 0.f;
             CUDA_TRY(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
@@ -462,7 +503,7 @@ extern "C" pasd_status pasd_profile_iterations(pasd_plan_t* pl, int32_t iters, d
 }
 
 extern "C" int32_t pasd_launches_per_iter(const pasd_plan_t* pl) {
-    return pl ? pl->ap_launches + 5 : 0;
+    return pl ? pl->ap_launches + 6 : 0;
 }
 
 // ---------------------------------------------------------------------------

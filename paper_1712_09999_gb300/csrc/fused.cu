@@ -7,22 +7,20 @@
 // The multipliers are stored as G_n = T - E + Y_n/mu, the argument of the next
 // U- and V-steps, so H_n = G_n + E - Z_n and
 //   G_n'    = T - E' + (mu/mu') (H_n - E'),  mu' = min(rho mu, mu_max).
-// The same pass also accumulates M'_n = G_n' A_n^T (I_n x R_n), the product
-// the next U-step needs (M_n = G_n V_n^T = M'_n W diag(F)), so G_n' is never
-// read back for it.
+// The next U-step's product G_n' Vrot_n^T is formed by the M-pass that follows.
 //
-// Z_n is rebuilt on the fly as Wz_n A_n with Wz_n = U_n W diag(F) W^T, a rank-R
-// refold of the small factor; nothing of size D besides T, E, G_n is touched.
+// Z_n is rebuilt on the fly as Urot_n Vrot_n (Urot = U W, Vrot = diag(F) W^T A_n
+// in the eigenbasis W of the SVT), a rank-R refold of the small factor; nothing
+// of size D besides T, E, G_n is touched.
 //
 // Work decomposition: the tensor is cut into boxes ("tiles") of power-of-two
 // extents b_n (B = prod b_n elements), tiles are grouped into regions, one CTA
-// per region. Per tile, the CTA stages the A_n columns and Wz_n rows the tile
-// needs in shared memory; each thread owns a micro-box of 8 elements
+// per region. Per tile, the CTA stages the Vrot_n columns and Urot_n rows the
+// tile needs in shared memory; each thread owns a micro-box of 8 elements
 // (2 along mode N-2, 4 along the contiguous mode N-1) and computes its Z_n in
-// FP32 registers, reusing every loaded operand 2-8 times. The M'_n products run
-// as small register-tiled GEMMs from shared memory; their per-region sums are
-// written once per region and reduced in a fixed order by the U-step kernel,
-// so the pass is deterministic (no atomics).
+// FP32 registers, reusing every loaded operand 2-8 times. Residual statistics
+// are written once per region and reduced in a fixed order by the finalize
+// kernel, so the pass is deterministic (no atomics).
 #include "pasd_impl.cuh"
 #include <algorithm>
 #include <cmath>
@@ -132,14 +130,6 @@ bool plan_geom_impl(FusedGeom& g, int N, const int64_t* I, const int* Rp, int nu
         }
         g.nregions = 1;
         for (int n = 0; n < N; ++n) g.nregions *= g.Q[n];
-        int macc = 0;
-        for (int n = 0; n < N; ++n) {
-            g.ext_max[n] = (int)((g.nt[n] + g.Q[n] - 1) / g.Q[n]) * b[n];
-            g.macc_off[n] = macc;
-            macc += g.ext_max[n] * Rp[n];
-            g.mp_combo_stride[n] = I[n] * Rp[n];
-        }
-        g.macc_floats = macc;
         g.nthreads = B / 8;
         if (tma) {
             bool fits = true;
@@ -154,21 +144,7 @@ bool plan_geom_impl(FusedGeom& g, int N, const int64_t* I, const int* Rp, int nu
             for (int n = 0; n < N; ++n) txo += (int64_t)g.C[n] * Rp[n] + (int64_t)b[n] * Rp[n];
             g.stage_tx_bytes = (uint32_t)(4 * (tx + txo));
             g.out_tx_bytes = (uint32_t)(4 * txo);
-            // the kernel runs the M_n product at every kept height h = 4, 8, ..., Rp_n,
-            // and fewer rows mean more split-K slices: size for the largest
-            int red = 16;
-            for (int n = 0; n < N; ++n) {
-                int MR = (n == N - 1) ? 4 : (b[n] >= 2 ? 2 : 1);
-                for (int h = 4; h <= Rp[n]; h += 4) {
-                    int nmt = (b[n] / MR) * (h / 4);
-                    int ns = 1;
-                    while ((nmt * ns * 2) <= g.nthreads) ns *= 2;
-                    red = std::max(red, 16 * ns * nmt);
-                }
-            }
-            g.red_off = 2 * g.stage_floats;
-            g.macc_base = g.red_off + round32(red);
-            g.smem_floats = g.macc_base + round32(macc);
+            g.smem_floats = 2 * g.stage_floats;
             g.tma = 1;
             // +1 KB so the kernel can align its stages to 1024 bytes
             if ((size_t)g.smem_floats * 4 + 1024 <= smem_limit) return true;
@@ -177,16 +153,6 @@ bool plan_geom_impl(FusedGeom& g, int N, const int64_t* I, const int* Rp, int nu
         int o = 0;
         for (int n = 0; n < N; ++n) { g.as_off[n] = o; o += g.C[n] * (Rp[n] + 4); }
         for (int n = 0; n < N; ++n) { g.ws_off[n] = o; o += b[n] * Rp[n]; }
-        g.gs_off = o; o += N * B;
-        int red = 16 * FU_THREADS;
-        for (int n = 0; n < N; ++n) {
-            int MR = (n == N - 1) ? 4 : (b[n] >= 2 ? 2 : 1);
-            int nmt = (b[n] / MR) * (Rp[n] / 4);
-            int ns = nmt >= FU_THREADS ? 1 : FU_THREADS / nmt;
-            red = std::max(red, 16 * ns * nmt);
-        }
-        g.red_off = o; o += red;
-        g.macc_base = o; o += (macc + 3) / 4 * 4;
         g.smem_floats = o;
         if ((size_t)o * 4 <= smem_limit) return true;
     }
@@ -263,10 +229,6 @@ __global__ void __launch_bounds__(FU_THREADS, 1) fused_kernel(FusedArgs fa) {
     int nonfin = 0;
 #pragma unroll
     for (int n = 0; n < N; ++n) res2[n] = 0.f;
-
-    float* macc = sm + g.macc_base;
-    if (!fa.output)
-        for (int i = t; i < g.macc_floats; i += FU_THREADS) macc[i] = 0.f;
 
     // tiles of the region, C order
     int64_t ntile = 1;
@@ -406,7 +368,6 @@ __global__ void __launch_bounds__(FU_THREADS, 1) fused_kernel(FusedArgs fa) {
         int64_t tbase = toff;
 #pragma unroll
         for (int n = 0; n < N; ++n) tbase += o[n] * g.stride[n];
-        float* Gs = sm + g.gs_off;
 #pragma unroll
         for (int d2 = 0; d2 < 2; ++d2) {
             const bool v2 = vbase && (u0[N - 2] + d2 < ext[N - 2]);
@@ -501,109 +462,9 @@ __global__ void __launch_bounds__(FU_THREADS, 1) fused_kernel(FusedArgs fa) {
                         for (int n = 0; n < N; ++n) fa.G[n][rowoff + d1] = gn[n][d1];
                     }
             }
-            if (active) {
-#pragma unroll
-                for (int n = 0; n < N; ++n)
-                    *reinterpret_cast<float4*>(Gs + n * g.B + ebase) =
-                        make_float4(ok[0] ? gn[n][0] : 0.f, ok[1] ? gn[n][1] : 0.f,
-                                    ok[2] ? gn[n][2] : 0.f, ok[3] ? gn[n][3] : 0.f);
-            }
-        }
-        if (fa.output) continue;
-        __syncthreads();
-
-        // ---- M'_n += G_n' A_n^T over this tile (register-tiled, deterministic) ----
-        float* red = sm + g.red_off;
-#pragma unroll
-        for (int n = 0; n < N; ++n) {
-            const int Rp = g.Rp[n], R4 = Rp / 4, ald = Rp + 4;
-            const int bn = g.b[n], Cn = g.C[n], H = g.esh[n], shn = g.sh[n];
-            const float* As = sm + g.as_off[n];
-            const float* Gn = Gs + n * g.B;
-            const int MR = (n == N - 1) ? 4 : (bn >= 2 ? 2 : 1);
-            const int nmt = (bn / MR) * R4;
-            const int ns = nmt >= FU_THREADS ? 1 : FU_THREADS / nmt;
-            for (int w = t; w < nmt * ns; w += FU_THREADS) {
-                int mt = w % nmt, sl = w / nmt;
-                int rb = mt / R4, r4 = mt % R4;
-                int l0 = rb * MR;
-                float acc[4][4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
-                if (n == N - 1) {
-                    for (int c = sl; c < Cn; c += ns) {
-                        float4 gg = *reinterpret_cast<const float4*>(Gn + (c << shn) + l0);
-                        float4 a = *reinterpret_cast<const float4*>(As + c * ald + 4 * r4);
-                        float gs4[4] = {gg.x, gg.y, gg.z, gg.w};
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            acc[i][0] = fmaf(gs4[i], a.x, acc[i][0]);
-                            acc[i][1] = fmaf(gs4[i], a.y, acc[i][1]);
-                            acc[i][2] = fmaf(gs4[i], a.z, acc[i][2]);
-                            acc[i][3] = fmaf(gs4[i], a.w, acc[i][3]);
-                        }
-                    }
-                } else {
-                    const int lowmask = (1 << H) - 1;
-                    for (int c4 = sl; c4 < Cn / 4; c4 += ns) {
-                        int c = 4 * c4;
-                        int eb = ((c >> H) << (H + shn)) | (c & lowmask);
-                        float4 a0 = *reinterpret_cast<const float4*>(As + c * ald + 4 * r4);
-                        float4 a1 = *reinterpret_cast<const float4*>(As + (c + 1) * ald + 4 * r4);
-                        float4 a2 = *reinterpret_cast<const float4*>(As + (c + 2) * ald + 4 * r4);
-                        float4 a3 = *reinterpret_cast<const float4*>(As + (c + 3) * ald + 4 * r4);
-                        for (int i = 0; i < MR; ++i) {
-                            float4 gg = *reinterpret_cast<const float4*>(Gn + eb + ((l0 + i) << H));
-                            acc[i][0] = fmaf(gg.x, a0.x, fmaf(gg.y, a1.x, fmaf(gg.z, a2.x, fmaf(gg.w, a3.x, acc[i][0]))));
-                            acc[i][1] = fmaf(gg.x, a0.y, fmaf(gg.y, a1.y, fmaf(gg.z, a2.y, fmaf(gg.w, a3.y, acc[i][1]))));
-                            acc[i][2] = fmaf(gg.x, a0.z, fmaf(gg.y, a1.z, fmaf(gg.z, a2.z, fmaf(gg.w, a3.z, acc[i][2]))));
-                            acc[i][3] = fmaf(gg.x, a0.w, fmaf(gg.y, a1.w, fmaf(gg.z, a2.w, fmaf(gg.w, a3.w, acc[i][3]))));
-                        }
-                    }
-                }
-                float* dst = red + (size_t)(sl * nmt + mt) * 16;
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<float4*>(dst + 4 * i) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-            }
-            __syncthreads();
-            float* mac = macc + g.macc_off[n];
-            const int64_t rowbase = ts[n] * bn;
-            for (int w = t; w < nmt * MR * 4; w += FU_THREADS) {
-                int mt = w / (MR * 4), qq = w % (MR * 4);
-                int i = qq / 4, k = qq % 4;
-                float s = 0.f;
-                for (int sl = 0; sl < ns; ++sl) s += red[(size_t)(sl * nmt + mt) * 16 + 4 * i + k];
-                int rb = mt / R4, r4 = mt % R4;
-                int l = rb * MR + i;
-                int64_t row = o[n] + l - rowbase;
-                mac[row * Rp + 4 * r4 + k] += s;
-            }
-            __syncthreads();
         }
     }
     if (fa.output) return;
-
-    // ---- flush the region's M'_n sums ----
-    __syncthreads();
-#pragma unroll
-    for (int n = 0; n < N; ++n) {
-        int64_t combo = 0;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            if (m == n) continue;
-            combo = combo * g.Q[m] + q[m];
-        }
-        const int Rp = g.Rp[n];
-        const int64_t rowbase = ts[n] * g.b[n];
-        int64_t rows = (te[n] - ts[n]) * g.b[n];
-        if (rowbase + rows > g.I[n]) rows = g.I[n] - rowbase;
-        float* dst = fa.mp_part[n] + combo * g.mp_combo_stride[n] + rowbase * Rp;
-        const float* mac = macc + g.macc_off[n];
-        for (int64_t idx = t; idx < rows * Rp; idx += FU_THREADS) dst[idx] = mac[idx];
-    }
 
     // ---- block reductions of the residual statistics ----
     __shared__ float wred[FU_THREADS / 32][PASD_MAXN + 3];

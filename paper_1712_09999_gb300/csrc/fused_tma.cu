@@ -1,19 +1,19 @@
 // TMA-fed, double-buffered fused elementwise pass (same arithmetic as
-// fused.cu, which stays as the path for N > 5 or a contiguous mode whose
+// fused.cu, which stays as the path for N > 4 or a contiguous mode whose
 // length is not a multiple of 4).
 //
 // Per tile (a box of extents b_n), one elected thread issues bulk tensor
 // copies (cp.async.bulk.tensor) into the next stage while the CTA computes the
 // current one:
 //   Xs   : T, E, G_0..G_{N-1} boxes, C order of the box (element index e)
-//   As_n : the A_n columns the tile needs, a box of the N-D tensor A_n
-//          ([pre][Rp][post] viewed with I_n replaced by Rp), i.e. smem layout
-//          [c_hi][r][c_lo] (c_lo = the post-mode part of the column index)
-//          for n < N-1 and [c][r] for the contiguous mode
-//   Ws_n : rows o_n .. o_n + b_n of Wz_n ([l][r])
+//   As_n : the Vrot_n columns the tile needs (kept rows), a box of the N-D
+//          tensor Vrot_n ([pre][Rp][post] viewed with I_n replaced by Rp),
+//          i.e. smem layout [c_hi][r][c_lo] (c_lo = the post-mode part of the
+//          column index) for n < N-1 and [c][r] for the contiguous mode
+//   Ws_n : rows o_n .. o_n + b_n of Urot_n ([l][r])
 // Out-of-range parts of a box are zero-filled by the copy engine, so the
 // arithmetic below needs no masks: a zero element stays zero through the
-// update and adds nothing to the residual sums or the G A^T products.
+// update and adds nothing to the residual sums.
 // Results (E', G_n') overwrite E and G_n in the stage and go back to HBM as
 // bulk tensor stores, clipped to the tensor by the copy engine.
 #include "pasd_impl.cuh"
@@ -127,10 +127,11 @@ constexpr uint32_t kWaitPolls = 1u << 22;   // bounded mbarrier wait (far above 
 // ---------------------------------------------------------------------------
 // kernel
 // ---------------------------------------------------------------------------
-// Only the kept directions carry Z_n and M_n: with s_n kept singular values,
-// Z_n = Urot[:, :s] Vrot[:s] and M_n = G_n' Vrot[:s]^T, so per element and mode
-// the pass does sp_n = round_up(s_n, 4) multiply-adds for each, and loads only
-// sp_n rows of Vrot and columns of Urot (one tensor map per height).
+// Only the kept directions carry Z_n: with s_n kept singular values,
+// Z_n = Urot[:, :s] Vrot[:s], so per element and mode the pass does
+// sp_n = round_up(s_n, 4) multiply-adds and loads only sp_n rows of Vrot and
+// columns of Urot (one tensor map per height). The next U-step's product
+// G_n' Vrot^T is formed by the M-pass that follows.
 template <int N>
 __global__ void __launch_bounds__(FU_THREADS, 1)
     fused_tma_kernel(const __grid_constant__ FusedTmaMaps tm, const FusedArgs fa, const int output,
@@ -200,10 +201,6 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
 #pragma unroll
     for (int n = 0; n < N; ++n) res2[n] = 0.f;
 
-    float* macc = sm + g.macc_base;
-    float* red = sm + g.red_off;
-    if (!output)
-        for (int i = t; i < g.macc_floats; i += nthr) macc[i] = 0.f;
     if (t == 0) {
         mbar_init(&full_bar[0], 1);
         mbar_init(&full_bar[1], 1);
@@ -422,83 +419,6 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
             bulk_commit();
         }
 
-        // ---- M_n (W basis) += G_n' Vrot^T over this tile, kept rows only ----
-#pragma unroll
-        for (int n = 0; n < N; ++n) {
-            const int h = sp[n];
-            if (h == 0) continue;
-            const int R4 = h / 4, Rp = g.Rp[n];
-            const int bn = g.b[n], Cn = g.C[n], H = g.esh[n], shn = g.sh[n];
-            const float* As = stg + g.as_off[n];
-            const float* Gn = Xs + (2 + n) * B;
-            const int MR = (n == N - 1) ? 4 : (bn >= 2 ? 2 : 1);
-            const int nmt = (bn / MR) * R4;
-            int lns = 0;                                   // slices: a power of two
-            while ((nmt << (lns + 1)) <= nthr) ++lns;
-            const int ns = 1 << lns;
-            for (int w = t; w < nmt * ns; w += nthr) {
-                const int sl = w & (ns - 1), mt = w >> lns;
-                const int rb = mt / R4, r4 = mt % R4;
-                const int l0 = rb * MR;
-                float acc[4][4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
-                if (n == N - 1) {
-                    for (int c = sl; c < Cn; c += ns) {
-                        const float4 gg = *reinterpret_cast<const float4*>(Gn + (c << shn) + l0);
-                        const float4 a = *reinterpret_cast<const float4*>(As + c * h + 4 * r4);
-                        const float gs4[4] = {gg.x, gg.y, gg.z, gg.w};
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            acc[i][0] = fmaf(gs4[i], a.x, acc[i][0]);
-                            acc[i][1] = fmaf(gs4[i], a.y, acc[i][1]);
-                            acc[i][2] = fmaf(gs4[i], a.z, acc[i][2]);
-                            acc[i][3] = fmaf(gs4[i], a.w, acc[i][3]);
-                        }
-                    }
-                } else {
-                    const int mask = (1 << H) - 1;
-                    for (int c4 = sl; c4 < Cn / 4; c4 += ns) {
-                        const int c = 4 * c4;
-                        const int chi = c >> H, clo = c & mask;
-                        float4 a[4];
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            a[kk] = *reinterpret_cast<const float4*>(As + ((chi * h + 4 * r4 + kk) << H) + clo);
-                        for (int i = 0; i < MR; ++i) {
-                            const float4 gg = *reinterpret_cast<const float4*>(Gn + (chi << (H + shn)) + ((l0 + i) << H) + clo);
-#pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                float s = acc[i][kk];
-                                s = fmaf(gg.x, a[kk].x, s);
-                                s = fmaf(gg.y, a[kk].y, s);
-                                s = fmaf(gg.z, a[kk].z, s);
-                                acc[i][kk] = fmaf(gg.w, a[kk].w, s);
-                            }
-                        }
-                    }
-                }
-                float* dst = red + (size_t)(sl * nmt + mt) * 16;
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<float4*>(dst + 4 * i) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-            }
-            __syncthreads();
-            float* mac = macc + g.macc_off[n];
-            const int64_t rowbase = ts[n] * bn;
-            for (int w = t; w < nmt * MR * 4; w += nthr) {
-                const int mt = w / (MR * 4), qq = w % (MR * 4);
-                const int i = qq / 4, k = qq % 4;
-                float s = 0.f;
-                for (int sl = 0; sl < ns; ++sl) s += red[(size_t)(sl * nmt + mt) * 16 + 4 * i + k];
-                const int rb = mt / R4, r4 = mt % R4;
-                const int64_t row = o[n] + rb * MR + i - rowbase;
-                mac[row * Rp + 4 * r4 + k] += s;
-            }
-            __syncthreads();
-        }
         __syncthreads();
     }
     if (t == 0) bulk_wait_read0();
@@ -515,24 +435,6 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         return;
     }
     if (output) return;
-
-    // ---- flush this region's M_n sums ----
-#pragma unroll
-    for (int n = 0; n < N; ++n) {
-        int64_t combo = 0;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            if (m == n) continue;
-            combo = combo * g.Q[m] + q[m];
-        }
-        const int Rp = g.Rp[n];
-        const int64_t rowbase = ts[n] * g.b[n];
-        int64_t rows = (te[n] - ts[n]) * g.b[n];
-        if (rowbase + rows > g.I[n]) rows = g.I[n] - rowbase;
-        float* dst = fa.mp_part[n] + combo * g.mp_combo_stride[n] + rowbase * Rp;
-        const float* mac = macc + g.macc_off[n];
-        for (int64_t idx = t; idx < rows * Rp; idx += nthr) dst[idx] = mac[idx];
-    }
 
     // ---- block reductions of the residual statistics ----
     __shared__ float wred[FU_THREADS / 32][PASD_MAXN + 3];

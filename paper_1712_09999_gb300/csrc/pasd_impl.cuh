@@ -108,7 +108,7 @@ struct FinalizeArgs {
     double rho, mu_max, tol;
     int stop_rule, max_iter;
     double* trace;         // [max_iter][13]
-    // cross-region sums of G_n A_n^T
+    // column-range partials of G_n Vrot_n^T from the M-pass, summed into Mred
     const float* mp_part[PASD_MAXN];   // [n_mp][I][Rp]
     int n_mp[PASD_MAXN];
     int64_t I[PASD_MAXN];
@@ -142,8 +142,36 @@ void launch_export_y(const float* G, const float* T, const float* E, const DevSc
                      float* Y, int64_t D, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
-// Fused elementwise pass: Z_n, E-step (Eq. 15), multipliers, residuals and the
-// G_n A_n^T partials of the next U-step, over power-of-two tiles ("boxes").
+// M-pass: M_n = G_(n) Vrot_n^T over the kept rows (the next U-step's product),
+// per column range partial sums part[range][I][Rp], summed by the finalize kernel.
+// ----------------------------------------------------------------------------
+constexpr int MP_THREADS = 256;
+constexpr int MP_CB = 32;        // unfolding columns per pipeline stage
+constexpr int MP_STAGES = 3;
+
+struct MpassMode {
+    const float* G;        // G_n (D floats)
+    const float* V;        // Vrot_n, [pre][Rp][post]
+    float* part;           // [ncg][I][Rp]
+    int64_t I, post, P;
+    int64_t cols_per_cg;   // unfolding columns per range (a multiple of MP_CB)
+    int Rp, IS, nstrips, ncg, variant;
+};
+struct MpassArgs {
+    int N;
+    const DevScalars* sc;
+    MpassMode m[PASD_MAXN];
+    int cta_start[PASD_MAXN + 1];   // CTA b works on mode k with cta_start[k] <= b < cta_start[k+1]
+};
+size_t mpass_smem_bytes(int IS, int Rp, int variant);
+int mpass_variant(int64_t I, int64_t post);
+int mpass_strip_rows(int64_t I, int Rp);
+int mpass_ctas_per_sm(size_t smem);
+void launch_mpass(const MpassArgs& a, size_t smem, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Fused elementwise pass: Z_n, E-step (Eq. 15), multipliers and residuals, over
+// power-of-two tiles ("boxes").
 // ----------------------------------------------------------------------------
 constexpr int FU_THREADS = 256;
 
@@ -163,20 +191,15 @@ struct FusedGeom {
     int64_t nt[PASD_MAXN];               // tiles per mode
     int Q[PASD_MAXN];                    // region grid
     int nregions;
-    int ext_max[PASD_MAXN];              // max rows of mode n a region spans
-    int macc_off[PASD_MAXN];             // offsets (floats) into the region accumulator
-    int macc_floats;
     int as_off[PASD_MAXN], ws_off[PASD_MAXN];   // smem layout (floats)
-    int gs_off, red_off, macc_base;
     int smem_floats;
-    int64_t mp_combo_stride[PASD_MAXN];  // floats per combo in mp_part[n] (= I_n * Rp_n)
     // TMA-pipelined variant (two stages of [Xs | As_n | Ws_n], see fused_tma.cu)
     int tma;                             // 1 when the TMA kernel is used
     int nthreads;                        // B / 8
     int stage_floats;                    // floats per stage
     int xs_off;                          // element tiles (T, E, G_0..G_{N-1}) inside a stage
     uint32_t stage_tx_bytes;             // bytes one stage's TMA loads deliver
-    uint32_t out_tx_bytes;               // bytes of the A / Wz loads only (output pass)
+    uint32_t out_tx_bytes;               // bytes of the Vrot / Urot loads only (output pass)
 };
 
 struct FusedArgs {
@@ -186,7 +209,6 @@ struct FusedArgs {
     float* G[PASD_MAXN];
     const float* A[PASD_MAXN];      // Vrot_n = diag(F) W^T A_n  (rows >= kept are zero)
     const float* Wz[PASD_MAXN];     // Urot_n = U_n W           (Z_n = Urot Vrot)
-    float* mp_part[PASD_MAXN];
     float* part;           // [nregions][stride] reduction partials
     int part_stride;
     double rho, mu_max;
@@ -200,7 +222,7 @@ bool plan_fused_geom(FusedGeom& g, int N, const int64_t* I, const int* Rp, int n
                      size_t smem_limit);
 void launch_fused(const FusedArgs& a, cudaStream_t s);
 
-// TMA-fed, double-buffered version of the fused pass (N <= 5, I_N % 4 == 0).
+// TMA-fed, double-buffered version of the fused pass (N <= 4, I_N % 4 == 0).
 // The element tiles come from plan-owned buffers (T is copied at begin), so the
 // tensor maps are fixed for the life of the plan.
 struct FusedTmaPlan;

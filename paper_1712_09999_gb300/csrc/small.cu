@@ -17,88 +17,116 @@
 // Precision. GB300 issues FP64 at about 1/74 of the FP32 rate (1.0 vs 74
 // TFLOP/s measured), so these kernels work in FP32; only scalar bookkeeping
 // (objective, residual sums, mu) uses FP64.
+//
+// Latency. Each CTA works alone on an SM, so its time is the length of its
+// dependency chain, not its arithmetic: matrices stay in shared memory, the
+// products run as 4 x 4 register tiles over split row ranges (summed in a fixed
+// order, so results do not depend on timing), global reads keep many loads in
+// flight, and a Jacobi round costs one barrier.
 #include "pasd_impl.cuh"
 #include <cfloat>
 
 namespace pasd {
 
 constexpr int SM_THREADS = 512;
+constexpr int TILE_SCRATCH = 4096;   // floats of split partial sums for tile_AtB
 
 // ---------------------------------------------------------------------------
 // Block-wide cyclic Jacobi eigen-solver for a symmetric n x n matrix.
 //   A  (ld x ld, n x n used) is overwritten; eigenvalues end on the diagonal.
 //   V  receives the eigenvectors (columns). A2, V2 are work buffers of the same
-//   shape; pc (2 * ld ints) and cs (2 * ld floats) hold the per-round rotations.
-// Pairs follow the round-robin (circle) ordering so that every round applies
-// n/2 disjoint rotations at once. A rotation is skipped when
-// |a_pq| <= tol * sqrt(|a_pp a_qq|), the relative criterion that preserves the
-// relative accuracy of small eigenvalues of graded matrices. Sweeps stop when
-// a sweep applies no rotation. Returns the pointer (A or A2, V or V2) holding
-// the result through *Aout / *Vout.
+//   shape. Returns the buffers holding the result through *Aout / *Vout.
+// Pairs follow the round-robin (circle) ordering, so every round applies m/2
+// disjoint rotations at once (m = n rounded up to even; an odd n gets a zero
+// dummy index). A rotation is skipped when |a_pq| <= tol * sqrt(|a_pp a_qq|),
+// the relative criterion that keeps the relative accuracy of the small
+// eigenvalues of graded matrices. A sweep starts only if some off-diagonal
+// entry fails that test.
+//
+// Each thread owns elements (i, j) of the rotated matrix and derives the two
+// rotations it needs (those of the pairs holding i and j) from the previous
+// matrix itself, so a round needs a single barrier. The rotation of a pair is
+// computed from its smaller index p and larger index q, identically by every
+// thread that needs it, and the element update is evaluated in an order that
+// is symmetric in (i, j) with explicit rounding, so A stays exactly symmetric.
 // ---------------------------------------------------------------------------
-__device__ void block_jacobi(float* A, float* V, float* A2, float* V2, int* pc, float* cs,
-                             int n, int ld, float tol, int max_sweeps, float** Aout,
-                             float** Vout) {
+__device__ __forceinline__ int rr_partner(int i, int round, int m) {
+    // index 0 stays fixed and meets 1 + round; index 1 + x (x != round) meets
+    // 1 + y with x + y = 2 round (mod m - 1)
+    if (i == 0) return 1 + round;
+    const int x = i - 1, mm = m - 1;
+    if (x == round) return 0;
+    int y = 2 * round - x;
+    if (y >= mm) y -= mm;
+    if (y < 0) y += mm;
+    return 1 + y;
+}
+
+// J restricted to the pair {i, pi}: J[i][i] = ci, J[pi][i] = si.
+__device__ __forceinline__ int pair_rotation(const float* A, int ld, int i, int pi, float tol, float& ci,
+                                             float& si) {
+    const int p = min(i, pi), q = max(i, pi);
+    const float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
+    float c = 1.f, s = 0.f;
+    int rot = 0;
+    if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq))) {
+        const float theta = (aqq - app) / (2.f * apq);
+        float tt;
+        if (fabsf(theta) > 1e18f) tt = 0.5f / theta;
+        else tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(1.f + theta * theta));
+        c = rsqrtf(1.f + tt * tt);
+        s = tt * c;
+        rot = 1;
+    }
+    ci = c;
+    si = (i == p) ? -s : s;      // J[q][p] = -s, J[p][q] = s
+    return rot;
+}
+
+__device__ void block_jacobi(float* A, float* V, float* A2, float* V2, int n, int ld, float tol,
+                             int max_sweeps, float** Aout, float** Vout) {
     const int t = threadIdx.x, nt = blockDim.x;
-    int m = n + (n & 1);      // even size; index n (if odd) is a zero dummy
+    const int m = n + (n & 1);
     for (int idx = t; idx < ld * ld; idx += nt) {
-        int i = idx / ld, j = idx % ld;
+        const int i = idx / ld, j = idx % ld;
         V[idx] = (i == j) ? 1.f : 0.f;
         if (i >= n || j >= n) A[idx] = 0.f;
     }
     __syncthreads();
-    if (m < 2) { *Aout = A; *Vout = V; return; }
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        int rotated_any = 0;
-        for (int round = 0; round < m - 1; ++round) {
-            // rotation parameters, one thread per pair
-            int rot = 0;
-            if (t < m / 2) {
-                int k = t;
-                int p, q;
-                if (k == 0) { p = 0; q = 1 + round; }
-                else {
-                    p = 1 + (round + k) % (m - 1);
-                    q = 1 + (round - k + (m - 1)) % (m - 1);
+    if (m >= 2) {
+        for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+            int need = 0;
+            for (int idx = t; idx < n * n; idx += nt) {
+                const int i = idx / n, j = idx % n;
+                if (i < j) {
+                    const float apq = A[i * ld + j];
+                    need |= (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(A[i * ld + i] * A[j * ld + j])));
                 }
-                float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
-                float c = 1.f, s = 0.f;
-                if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq))) {
-                    float theta = (aqq - app) / (2.f * apq);
-                    float tt;
-                    if (fabsf(theta) > 1e18f) tt = 0.5f / theta;
-                    else tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(1.f + theta * theta));
-                    c = rsqrtf(1.f + tt * tt);
-                    s = tt * c;
-                    rot = 1;
+            }
+            if (!__syncthreads_or(need)) break;
+            for (int round = 0; round < m - 1; ++round) {
+                int rot = 0;
+                for (int idx = t; idx < m * m; idx += nt) {
+                    const int i = idx / m, j = idx % m;
+                    const int pi = rr_partner(i, round, m), pj = rr_partner(j, round, m);
+                    float ci, si, cj, sj;
+                    rot |= pair_rotation(A, ld, i, pi, tol, ci, si);
+                    rot |= pair_rotation(A, ld, j, pj, tol, cj, sj);
+                    const float t1 = __fmul_rn(__fmul_rn(ci, cj), A[i * ld + j]);
+                    const float t2 = __fmul_rn(__fmul_rn(ci, sj), A[i * ld + pj]);
+                    const float t3 = __fmul_rn(__fmul_rn(si, cj), A[pi * ld + j]);
+                    const float t4 = __fmul_rn(__fmul_rn(si, sj), A[pi * ld + pj]);
+                    float v = __fadd_rn(__fadd_rn(t1, __fadd_rn(t2, t3)), t4);
+                    if (pi == j && si != 0.f) v = 0.f;      // the annihilated pair
+                    A2[i * ld + j] = v;
+                    if (i < n) V2[i * ld + j] = fmaf(V[i * ld + pj], sj, V[i * ld + j] * cj);
                 }
-                pc[p] = q; pc[q] = p;
-                cs[2 * p] = c; cs[2 * p + 1] = -s;   // J[p][p] = c, J[q][p] = -s
-                cs[2 * q] = c; cs[2 * q + 1] = s;    // J[q][q] = c, J[p][q] =  s
+                if (__syncthreads_or(rot)) {
+                    float* tA = A; A = A2; A2 = tA;
+                    float* tV = V; V = V2; V2 = tV;
+                }
             }
-            int any = __syncthreads_or(rot);
-            if (!any) continue;
-            rotated_any = 1;
-            // A2 = J^T A J, V2 = V J
-            for (int idx = t; idx < m * m; idx += nt) {
-                int i = idx / m, j = idx % m;
-                int pi = pc[i], pj = pc[j];
-                float ci = cs[2 * i], si = cs[2 * i + 1], cj = cs[2 * j], sj = cs[2 * j + 1];
-                float v = ci * cj * A[i * ld + j] + ci * sj * A[i * ld + pj] +
-                          si * cj * A[pi * ld + j] + si * sj * A[pi * ld + pj];
-                if ((pi == j) && (si != 0.f)) v = 0.f;   // annihilated pair
-                A2[i * ld + j] = v;
-            }
-            for (int idx = t; idx < n * m; idx += nt) {
-                int i = idx / m, j = idx % m;
-                int pj = pc[j];
-                V2[i * ld + j] = V[i * ld + j] * cs[2 * j] + V[i * ld + pj] * cs[2 * j + 1];
-            }
-            __syncthreads();
-            float* tA = A; A = A2; A2 = tA;
-            float* tV = V; V = V2; V2 = tV;
         }
-        if (!rotated_any) break;
     }
     *Aout = A;
     *Vout = V;
@@ -122,58 +150,144 @@ __device__ void sort_desc(const float* A, int n, int ld, int* perm) {
     __syncthreads();
 }
 
-// C (ca x cb, ldc) = X^T Y over `rows` rows; X (rows x ldx), Y (rows x ldy).
-// One warp per output, lanes stride over the rows, shuffle reduction (fixed
-// order, so the result is deterministic). With `sym` (X == Y, ca == cb) only
-// the upper triangle is computed and mirrored.
-__device__ void warp_AtB(const float* X, int ldx, const float* Y, int ldy, int64_t rows, int ca, int cb,
-                         float* C, int ldc, bool sym) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = warp; o < ca * cb; o += nw) {
-        const int a = o / cb, b = o % cb;
-        if (sym && a > b) continue;
-        float s = 0.f;
-        for (int64_t r = lane; r < rows; r += 32) s = fmaf(X[r * ldx + a], Y[r * ldy + b], s);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) {
-            C[a * ldc + b] = s;
-            if (sym) C[b * ldc + a] = s;
+// C (na x nb, ldc) = X[:, :na]^T Y[:, :nb] over `rows` rows (row strides ldx,
+// ldy, multiples of 4; 16-byte aligned bases). The entries of C up to the next
+// multiples of 4 are written as zeros. 4 x 4 register tiles, rows split S ways,
+// split sums added in a fixed order. With `sym` (X == Y, na == nb) only tiles
+// on and above the diagonal are formed and mirrored. Ends with a barrier.
+__device__ void tile_AtB(const float* X, int ldx, int na, const float* Y, int ldy, int nb, int64_t rows,
+                         float* C, int ldc, bool sym, float* scratch) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int ta = (na + 3) / 4, tb = (nb + 3) / 4;
+    const int ntile = sym ? ta * (ta + 1) / 2 : ta * tb;
+    int S = 1;
+    while (ntile * S * 2 <= TILE_SCRATCH / 16 && ntile * S * 2 <= nt && S * 2 <= rows) S *= 2;
+    for (int w = t; w < ntile * S; w += nt) {
+        const int tile = w / S, sp = w % S;
+        int a4, b4;
+        if (sym) {
+            a4 = 0;
+            int rem = tile;
+            while (rem >= ta - a4) { rem -= ta - a4; ++a4; }
+            b4 = a4 + rem;
+        } else {
+            a4 = tile / tb;
+            b4 = tile % tb;
         }
+        const int64_t r0 = rows * sp / S, r1 = rows * (sp + 1) / S;
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        const float* xp = X + r0 * ldx + 4 * a4;
+        const float* yp = Y + r0 * ldy + 4 * b4;
+#pragma unroll 2
+        for (int64_t r = r0; r < r1; ++r, xp += ldx, yp += ldy) {
+            const float4 x = *reinterpret_cast<const float4*>(xp);
+            const float4 y = *reinterpret_cast<const float4*>(yp);
+            const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xs[i], ys[j], acc[i][j]);
+        }
+        float4* dst = reinterpret_cast<float4*>(scratch + (size_t)w * 16);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dst[i] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
     }
+    __syncthreads();
+    const int na4 = 4 * ta, nb4 = 4 * tb;
+    for (int o = t; o < na4 * nb4; o += nt) {
+        const int a = o / nb4, b = o % nb4;
+        if (a >= na || b >= nb) {
+            if (!sym || a <= b) C[a * ldc + b] = 0.f;
+            if (sym && a <= b) C[b * ldc + a] = 0.f;
+            continue;
+        }
+        if (sym && a > b) continue;
+        const int a4 = a >> 2, b4 = b >> 2;
+        const int tile = sym ? a4 * ta - a4 * (a4 - 1) / 2 + (b4 - a4) : a4 * tb + b4;
+        const float* src = scratch + (size_t)tile * S * 16 + (a & 3) * 4 + (b & 3);
+        float s = 0.f;
+        for (int sp = 0; sp < S; ++sp) s += src[sp * 16];
+        C[a * ldc + b] = s;
+        if (sym) C[b * ldc + a] = s;
+    }
+    __syncthreads();
 }
 
-// Y[:, y0 + c] (rows x cols) = X (rows x inner) * S (inner x cols); one thread per output.
-__device__ void block_AB(const float* X, int ldx, const float* S, int lds, int64_t rows, int inner, int cols,
-                         float* Y, int ldy) {
-    for (int64_t idx = threadIdx.x; idx < rows * cols; idx += blockDim.x) {
-        const int64_t i = idx / cols;
-        const int j = (int)(idx % cols);
-        float s = 0.f;
-        for (int k = 0; k < inner; ++k) s = fmaf(X[i * ldx + k], S[k * lds + j], s);
-        Y[i * ldy + j] = s;
+// Y[:, :cols] = X[:, :inner] S  (or Y -= X S with `sub`), rows x cols, cols a
+// multiple of 4; S is inner x cols (row stride lds, a multiple of 4). One
+// thread per row and group of 4 columns. No barrier.
+__device__ void tile_AB(const float* X, int ldx, int inner, const float* S, int lds, int cols, int64_t rows,
+                        float* Y, int ldy, bool sub) {
+    const int c4n = cols / 4;
+    for (int64_t w = threadIdx.x; w < rows * c4n; w += blockDim.x) {
+        const int64_t i = w / c4n;
+        const int c4 = (int)(w % c4n);
+        float4* yp = reinterpret_cast<float4*>(Y + i * ldy + 4 * c4);
+        float4 acc = sub ? *yp : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float sg = sub ? -1.f : 1.f;
+        const float* xr = X + i * ldx;
+        const float* sc = S + 4 * c4;
+        int k = 0;
+#pragma unroll 2
+        for (; k + 4 <= inner; k += 4) {
+            const float4 x4 = *reinterpret_cast<const float4*>(xr + k);
+            const float xs[4] = {sg * x4.x, sg * x4.y, sg * x4.z, sg * x4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 sv = *reinterpret_cast<const float4*>(sc + (k + u) * lds);
+                acc.x = fmaf(xs[u], sv.x, acc.x);
+                acc.y = fmaf(xs[u], sv.y, acc.y);
+                acc.z = fmaf(xs[u], sv.z, acc.z);
+                acc.w = fmaf(xs[u], sv.w, acc.w);
+            }
+        }
+        for (; k < inner; ++k) {
+            const float xv = sg * xr[k];
+            const float4 sv = *reinterpret_cast<const float4*>(sc + k * lds);
+            acc.x = fmaf(xv, sv.x, acc.x);
+            acc.y = fmaf(xv, sv.y, acc.y);
+            acc.z = fmaf(xv, sv.z, acc.z);
+            acc.w = fmaf(xv, sv.w, acc.w);
+        }
+        *yp = acc;
     }
 }
 
 // Z = Q diag(w^{-1/2}) Q^T for the n x n eigen-system (Q columns, eigenvalues w
-// on the diagonal of D). Nonpositive eigenvalues (rank loss) map to 0.
+// on the diagonal of D); entries up to the next multiple of 4 are zero.
+// Nonpositive eigenvalues (rank loss) map to 0. Ends with a barrier.
 __device__ void inv_sqrt_from_eig(const float* D, const float* Q, int n, int ld, float* Z) {
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        int i = idx / n, j = idx % n;
+    const int n4 = (n + 3) & ~3;
+    for (int idx = threadIdx.x; idx < n4 * n4; idx += blockDim.x) {
+        const int i = idx / n4, j = idx % n4;
         float s = 0.f;
-        for (int k = 0; k < n; ++k) {
-            float w = D[k * ld + k];
-            float f = w > 0.f ? rsqrtf(w) : 0.f;
-            s = fmaf(Q[i * ld + k] * f, Q[j * ld + k], s);
-        }
+        if (i < n && j < n)
+            for (int k = 0; k < n; ++k) {
+                const float w = D[k * ld + k];
+                const float f = w > 0.f ? rsqrtf(w) : 0.f;
+                s = fmaf(Q[i * ld + k] * f, Q[j * ld + k], s);
+            }
         Z[i * ld + j] = s;
     }
     __syncthreads();
 }
 
+// dst[i][c] = src[i][c0 + c] for c < w, 0 for w <= c < round4(w); rows x ...
+__device__ void copy_cols(const float* src, int lds, int c0, int w, int64_t rows, float* dst, int ldd) {
+    const int w4 = (w + 3) & ~3;
+    for (int64_t idx = threadIdx.x; idx < rows * w4; idx += blockDim.x) {
+        const int64_t i = idx / w4;
+        const int c = (int)(idx % w4);
+        dst[i * ldd + c] = c < w ? src[i * lds + c0 + c] : 0.f;
+    }
+}
+
 struct JacobiBufs {
-    float *A, *V, *A2, *V2, *cs;
-    int* pc;
+    float *A, *V, *A2, *V2;
 };
 
 __device__ JacobiBufs carve_jacobi(float* base, int ld) {
@@ -182,108 +296,120 @@ __device__ JacobiBufs carve_jacobi(float* base, int ld) {
     b.V = b.A + ld * ld;
     b.A2 = b.V + ld * ld;
     b.V2 = b.A2 + ld * ld;
-    b.cs = b.V2 + ld * ld;
-    b.pc = reinterpret_cast<int*>(b.cs + 2 * ld);
     return b;
 }
-__host__ __device__ constexpr int jacobi_floats(int ld) { return 4 * ld * ld + 4 * ld; }
+__host__ __device__ constexpr int jacobi_floats(int ld) { return 4 * ld * ld; }
+
+// Row stride of the I x R matrices of the U-step in shared memory: a multiple of
+// 4 with (stride / 4) odd, so float4 rows of consecutive rows hit distinct banks.
+__host__ __device__ inline int polar_ld(int Rp) { return ((Rp / 4) & 1) ? Rp : Rp + 4; }
 
 // ---------------------------------------------------------------------------
 // SVT (Eq. 13 and the SVT definition after it), one CTA per mode.
 // ---------------------------------------------------------------------------
+__host__ __device__ inline int svt_red_floats(int Rp) { return Rp * Rp > 2048 ? Rp * Rp : 2048; }
+
 __global__ void __launch_bounds__(SM_THREADS) svt_kernel(SmallArgs sa) {
     DevScalars* sc = sa.sc;
     if (sc->done) return;
+    const double mu = sc->mu;
     const SmallModeArgs& m = sa.m[blockIdx.x];
     const int R = m.R, Rp = m.Rp, ld = Rp;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+    const int t = threadIdx.x;
     extern __shared__ __align__(16) float sm[];
     JacobiBufs jb = carve_jacobi(sm, ld);
-    float* Smat = sm + jacobi_floats(ld);       // ld x ld (sorted eigenvectors)
-    float* fsh = Smat + ld * ld;                // ld
-    int* perm = reinterpret_cast<int*>(fsh + ld);
-    float* red = reinterpret_cast<float*>(perm + ld);   // nw x 256
+    float* Smat = sm + jacobi_floats(ld);       // ld x ld (sorted eigenvectors, zero padded)
+    float* sigsh = Smat + ld * ld;              // ld
+    int* perm = reinterpret_cast<int*>(sigsh + ld);
+    float* red = reinterpret_cast<float*>(perm + ld);   // svt_red_floats(Rp)
 
-    // 1. Gram matrix = sum over the A-pass CTA partials: warp w owns partials
-    //    w, w + nw, ...; lanes own outputs; then a fixed-order sum over warps.
-    const int nout = Rp * Rp;
-    for (int obase = 0; obase < nout; obase += 256) {
-        float acc[8];
+    // 1. Gram matrix = sum over the A-pass CTA partials. Thread (f, g) adds
+    //    float4 f of partials g, g + G, ... (eight loads in flight), then the G
+    //    group sums are added in order; the upper triangle is mirrored, so the
+    //    matrix is exactly symmetric.
+    {
+        const int nf4 = Rp * Rp / 4;
+        const int G = max(1, (int)blockDim.x / nf4);
+        const float4* part = reinterpret_cast<const float4*>(m.gram_part);
+        float4* red4 = reinterpret_cast<float4*>(red);
+        for (int w = t; w < nf4 * G; w += blockDim.x) {
+            const int f = w % nf4, g = w / nf4;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            int p = g;
+            for (; p + 7 * G < m.n_gram; p += 8 * G) {
+                float4 v[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = 0.f;
-        for (int p = warp; p < m.n_gram; p += nw) {
-            const float* src = m.gram_part + (size_t)p * nout + obase;
+                for (int u = 0; u < 8; ++u) v[u] = part[(size_t)(p + u * G) * nf4 + f];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                int o = lane + 32 * k;
-                if (obase + o < nout) acc[k] += src[o];
+                for (int u = 0; u < 8; ++u) {
+                    acc.x += v[u].x; acc.y += v[u].y; acc.z += v[u].z; acc.w += v[u].w;
+                }
             }
+            for (; p < m.n_gram; p += G) {
+                const float4 v = part[(size_t)p * nf4 + f];
+                acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+            }
+            red4[g * nf4 + f] = acc;
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) red[warp * 256 + lane + 32 * k] = acc[k];
         __syncthreads();
-        for (int o = t; o < 256 && obase + o < nout; o += blockDim.x) {
+        for (int o = t; o < Rp * Rp; o += blockDim.x) {
+            const int i = o / Rp, j = o % Rp;
+            if (i > j || j >= R) continue;
             float s = 0.f;
-            for (int w = 0; w < nw; ++w) s += red[w * 256 + o];
-            int oo = obase + o, i = oo / Rp, j = oo % Rp;
-            if (i < R && j < R) jb.A[i * ld + j] = s;
+            for (int g = 0; g < G; ++g) s += red[g * Rp * Rp + o];
+            jb.A[i * ld + j] = s;
+            jb.A[j * ld + i] = s;
         }
         __syncthreads();
     }
     // 2. eigen-decomposition
     float *Ae, *Ve;
-    block_jacobi(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, R, ld, 1e-6f, 30, &Ae, &Ve);
+    block_jacobi(jb.A, jb.V, jb.A2, jb.V2, R, ld, 1e-6f, 30, &Ae, &Ve);
     sort_desc(Ae, R, ld, perm);
-    // 3. thresholds
-    const double mu = sc->mu;
+    // 3. thresholds, sorted eigenvectors (W), kept count and nuclear norm
     const float tau = (float)(m.lambda / mu);
     if (t < Rp) {
         float sig = 0.f, f = 0.f;
         if (t < R) {
-            int src = perm[t];
-            float lam = Ae[src * ld + src];
+            const float lam = Ae[perm[t] * ld + perm[t]];
             sig = sqrtf(fmaxf(lam, 0.f));
             f = sig > tau ? 1.f - tau / sig : 0.f;
         }
-        fsh[t] = f;
+        sigsh[t] = sig;
         m.sigma[t] = sig;
         m.F[t] = f;
     }
     for (int idx = t; idx < Rp * Rp; idx += blockDim.x) {
-        int i = idx / Rp, j = idx % Rp;
-        float v = 0.f;
-        if (i < R && j < R) v = Ve[i * ld + perm[j]];
-        else if (i == j) v = 1.f;
+        const int i = idx / Rp, j = idx % Rp;
+        const bool in = i < R && j < R;
+        const float v = in ? Ve[i * ld + perm[j]] : (i == j ? 1.f : 0.f);
         m.W[idx] = v;
+        Smat[i * ld + j] = in ? v : 0.f;
     }
     __syncthreads();
-    if (t == 0) {
-        int kept = 0;
+    if (t < 32) {
         double nuc = 0.0;
-        for (int i = 0; i < R; ++i) {
-            float sig = m.sigma[i];
+        int kept = 0;
+        for (int i = t; i < R; i += 32) {
+            const float sig = sigsh[i];
             if (sig > tau) { ++kept; nuc += (double)sig - (double)tau; }
         }
-        *m.kept = kept;
-        sc->kept[blockIdx.x] = kept;
-        sc->nuclear[blockIdx.x] = nuc;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            nuc += __shfl_xor_sync(0xffffffffu, nuc, off);
+            kept += __shfl_xor_sync(0xffffffffu, kept, off);
+        }
+        if (t == 0) {
+            *m.kept = kept;
+            sc->kept[blockIdx.x] = kept;
+            sc->nuclear[blockIdx.x] = nuc;
+        }
     }
     // 4. Urot = U W (I x Rp): the active subspace in the eigenbasis of the SVT.
     //    With Vrot = diag(F) W^T A_n (rows beyond the kept count are zero),
     //    fold_n(U_n V_n) = Urot[:, :s] Vrot[:s], the refold of rank s.
-    for (int idx = t; idx < R * R; idx += blockDim.x) {
-        int i = idx / R, j = idx % R;
-        Smat[i * ld + j] = Ve[i * ld + perm[j]];
-    }
-    __syncthreads();
-    for (int64_t idx = t; idx < m.I * Rp; idx += blockDim.x) {
-        int64_t i = idx / Rp;
-        int j = (int)(idx % Rp);
-        float s = 0.f;
-        if (j < R)
-            for (int k = 0; k < R; ++k) s = fmaf(m.U[i * Rp + k], Smat[k * ld + j], s);
-        m.Urot[idx] = s;
-    }
+    //    U's padding columns are zero, so the product runs over Rp.
+    tile_AB(m.U, Rp, Rp, Smat, ld, Rp, m.I, m.Urot, Rp, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -294,7 +420,7 @@ __global__ void __launch_bounds__(SM_THREADS) svt_kernel(SmallArgs sa) {
 // i.e. the unique polar factor on the range of M_n and, on its null space, the
 // isometry closest to the previous iterate (identity at k = 0, where s = 0).
 // A closing Newton-Schulz step re-orthonormalises U. The I x R matrices live in
-// shared memory (row stride Rp + 1) when they fit, else in the global scratch.
+// shared memory when they fit, else in the global scratch.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
     DevScalars* sc = sa.sc;
@@ -302,95 +428,79 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
     const SmallModeArgs& m = sa.m[blockIdx.x];
     const int R = m.R, Rp = m.Rp, ld = Rp;
     const int64_t I = m.I;
-    const int t = threadIdx.x;
     extern __shared__ __align__(16) float sm[];
     JacobiBufs jb = carve_jacobi(sm, ld);
-    float* Z = sm + jacobi_floats(ld) + ld * ld;   // ld x ld
-    float* K = Z + ld * ld;                        // ld x ld
-    float* big = K + ld * ld + 2 * ld + 64;        // 3 x I x LD when it fits
+    float* Z = sm + jacobi_floats(ld);          // ld x ld
+    float* K = Z + ld * ld;                     // ld x ld
+    float* tsc = K + ld * ld;                   // TILE_SCRATCH
+    float* big = tsc + TILE_SCRATCH;            // 4 x I x LD when it fits
     const bool in_smem = m.polar_in_smem != 0;
-    const int LD = in_smem ? Rp + 1 : Rp;
-    float* Mw = in_smem ? big : m.scratch;                 // [P1 | X]
-    float* Pw = Mw + I * LD;                               // M in the W basis
-    float* Bw = Pw + I * LD;                               // (U W)[:, s:], then B
+    const int LD = in_smem ? polar_ld(Rp) : Rp;
+    float* Mw = in_smem ? big : m.scratch;      // [P1 | X]
+    float* Pw = Mw + I * LD;                    // M in the W basis
+    float* Bw = Pw + I * LD;                    // (U W)[:, s:], then (I - P1 P1^T) of it
+    float* Xb = Bw + I * LD;                    // X
 
     const int s = *m.kept;
     const int q = R - s;
+    const int s4 = (s + 3) & ~3, q4 = (q + 3) & ~3;
 
     if (s > 0) {
         // M in the W basis: G_n Vrot^T, summed over regions by the finalize kernel
-        for (int64_t idx = t; idx < I * s; idx += blockDim.x) {
-            int64_t i = idx / s;
-            int c = (int)(idx % s);
-            Pw[i * LD + c] = m.Mred[i * Rp + c];
-        }
+        copy_cols(m.Mred, Rp, 0, s, I, Pw, LD);
         __syncthreads();
         // B1 = M^T M, Z1 = B1^{-1/2}, P1 = M Z1
-        warp_AtB(Pw, LD, Pw, LD, I, s, s, jb.A, ld, true);
-        __syncthreads();
+        tile_AtB(Pw, LD, s, Pw, LD, s, I, jb.A, ld, true, tsc);
         float *Ae, *Ve;
-        block_jacobi(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, s, ld, 1e-6f, 30, &Ae, &Ve);
+        block_jacobi(jb.A, jb.V, jb.A2, jb.V2, s, ld, 1e-6f, 30, &Ae, &Ve);
         inv_sqrt_from_eig(Ae, Ve, s, ld, Z);
-        block_AB(Pw, LD, Z, ld, I, s, s, Mw, LD);
+        tile_AB(Pw, LD, s, Z, ld, s4, I, Mw, LD, false);
         __syncthreads();
     }
     if (q > 0) {
         // (U W)[:, s:], from the SVT of the previous loop body (eye at k = 0)
-        for (int64_t idx = t; idx < I * q; idx += blockDim.x) {
-            int64_t i = idx / q;
-            int c = (int)(idx % q);
-            Bw[i * LD + c] = m.Urot[i * Rp + s + c];
-        }
+        copy_cols(m.Urot, Rp, s, q, I, Bw, LD);
         __syncthreads();
         if (s > 0) {
             // K = P1^T Ur (s x q);  B = Ur - P1 K
-            warp_AtB(Mw, LD, Bw, LD, I, s, q, K, ld, false);
-            __syncthreads();
-            for (int64_t idx = t; idx < I * q; idx += blockDim.x) {
-                int64_t i = idx / q;
-                int c = (int)(idx % q);
-                float acc = Bw[i * LD + c];
-                for (int k = 0; k < s; ++k) acc = fmaf(-Mw[i * LD + k], K[k * ld + c], acc);
-                Bw[i * LD + c] = acc;
-            }
+            tile_AtB(Mw, LD, s, Bw, LD, q, I, K, ld, false, tsc);
+            tile_AB(Mw, LD, s, K, ld, q4, I, Bw, LD, true);
             __syncthreads();
         }
-        warp_AtB(Bw, LD, Bw, LD, I, q, q, jb.A, ld, true);
-        __syncthreads();
+        tile_AtB(Bw, LD, q, Bw, LD, q, I, jb.A, ld, true, tsc);
         float *Ae, *Ve;
-        block_jacobi(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, q, ld, 1e-6f, 30, &Ae, &Ve);
+        block_jacobi(jb.A, jb.V, jb.A2, jb.V2, q, ld, 1e-6f, 30, &Ae, &Ve);
         inv_sqrt_from_eig(Ae, Ve, q, ld, Z);
-        block_AB(Bw, LD, Z, ld, I, q, q, Mw + s, LD);
+        tile_AB(Bw, LD, q, Z, ld, q4, I, Xb, LD, false);
+        __syncthreads();
+        for (int64_t idx = threadIdx.x; idx < I * q; idx += blockDim.x) {
+            const int64_t i = idx / q;
+            const int c = (int)(idx % q);
+            Mw[i * LD + s + c] = Xb[i * LD + c];
+        }
         __syncthreads();
     }
-    // Newton-Schulz: U = Un (3 I - Un^T Un) / 2
-    warp_AtB(Mw, LD, Mw, LD, I, R, R, K, ld, true);
-    __syncthreads();
-    for (int idx = t; idx < R * R; idx += blockDim.x) {
-        int i = idx / R, j = idx % R;
-        Z[i * ld + j] = ((i == j) ? 1.5f : 0.f) - 0.5f * K[i * ld + j];
+    // Newton-Schulz: U = Un (3 I - Un^T Un) / 2, written with zero padding columns
+    tile_AtB(Mw, LD, R, Mw, LD, R, I, K, ld, true, tsc);
+    for (int idx = threadIdx.x; idx < Rp * Rp; idx += blockDim.x) {
+        const int i = idx / Rp, j = idx % Rp;
+        Z[i * ld + j] = (i < R && j < R) ? ((i == j) ? 1.5f : 0.f) - 0.5f * K[i * ld + j] : 0.f;
     }
     __syncthreads();
-    for (int64_t idx = t; idx < I * Rp; idx += blockDim.x) {
-        int64_t i = idx / Rp;
-        int j = (int)(idx % Rp);
-        float acc = 0.f;
-        if (j < R)
-            for (int k = 0; k < R; ++k) acc = fmaf(Mw[i * LD + k], Z[k * ld + j], acc);
-        m.U[idx] = acc;
-    }
+    tile_AB(Mw, LD, R, Z, ld, Rp, I, m.U, Rp, false);
 }
 
 static size_t small_base_floats(int maxRp) {
-    int ld = maxRp;
-    return (size_t)jacobi_floats(ld) + 3 * ld * ld + 2 * ld + 64;
+    const int ld = maxRp;
+    return (size_t)jacobi_floats(ld) + 2 * (size_t)ld * ld + TILE_SCRATCH;
 }
 static size_t svt_smem_bytes(int maxRp) {
-    return 4 * (small_base_floats(maxRp) + (size_t)(SM_THREADS / 32) * 256);
+    const int ld = maxRp;
+    return 4 * ((size_t)jacobi_floats(ld) + (size_t)ld * ld + 2 * (size_t)ld + svt_red_floats(maxRp));
 }
 // Bytes of shared memory the U-step needs with its I x R matrices resident.
 size_t polar_smem_bytes(int maxRp, int64_t maxI) {
-    return 4 * (small_base_floats(maxRp) + 3 * (size_t)maxI * (maxRp + 1));
+    return 4 * (small_base_floats(maxRp) + 4 * (size_t)maxI * polar_ld(maxRp));
 }
 
 void launch_svt(const SmallArgs& a, cudaStream_t s) {
@@ -417,58 +527,88 @@ void launch_polar(const SmallArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Finalize one loop body. CTA 0: residual norms of T - Z_n - E (the stop test
 // of Algorithm 1), objective of Eq. 3, mu schedule, iteration record. Other
-// CTAs: the fixed-order sum of the per-region G_n A_n^T partials (one output
-// per thread), which the next U-step reads.
+// CTAs: the fixed-order sum of the M-pass partials of G_n Vrot_n^T (64 outputs
+// per CTA, four threads per output), which the next U-step reads.
 // part layout per region: [0] max |T - Z_n - E|, [1] sum |E|, [2] non-finite
 // flag, [3 + n] sum (T - Z_n - E)^2.
 // ---------------------------------------------------------------------------
-__global__ void finalize_kernel(FinalizeArgs fa) {
+constexpr int FIN_THREADS = 256;
+constexpr int FIN_OUT = FIN_THREADS / 4;
+
+__global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(FinalizeArgs fa) {
     DevScalars* sc = fa.sc;
     if (sc->done) return;
     const int t = threadIdx.x, nt = blockDim.x;
     if (blockIdx.x > 0) {
-        int64_t o = (int64_t)(blockIdx.x - 1) * nt + t;
+        __shared__ float sub[4][FIN_OUT];
+        const int ol = t % FIN_OUT, h = t / FIN_OUT;
+        int64_t o = (int64_t)(blockIdx.x - 1) * FIN_OUT + ol;
+        int mode = -1;
+        int64_t i = 0;
+        int r = 0;
         for (int n = 0; n < fa.N; ++n) {
             const int64_t cnt = fa.I[n] * fa.R[n];
-            if (o < cnt) {
-                const int64_t i = o / fa.R[n];
-                const int r = (int)(o % fa.R[n]);
-                float acc = 0.f;
-                if (r < sc->kept[n]) {      // only the kept directions carry G V^T
-                    const int64_t stride = fa.I[n] * fa.Rp[n];
-                    const float* src = fa.mp_part[n] + i * fa.Rp[n] + r;
-#pragma unroll 8
-                    for (int p = 0; p < fa.n_mp[n]; ++p) acc += src[(int64_t)p * stride];
-                }
-                fa.Mred[n][i * fa.Rp[n] + r] = acc;
-                return;
-            }
+            if (o < cnt) { mode = n; i = o / fa.R[n]; r = (int)(o % fa.R[n]); break; }
             o -= cnt;
         }
+        float acc = 0.f;
+        if (mode >= 0 && r < sc->kept[mode]) {      // only the kept directions carry G V^T
+            const int64_t stride = fa.I[mode] * fa.Rp[mode];
+            const float* src = fa.mp_part[mode] + i * fa.Rp[mode] + r;
+            const int np = fa.n_mp[mode];
+            int p = h;
+            for (; p + 60 < np; p += 64) {          // 16 loads in flight, added in order
+                float v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) v[u] = src[(int64_t)(p + 4 * u) * stride];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) acc += v[u];
+            }
+            for (; p < np; p += 4) acc += src[(int64_t)p * stride];
+        }
+        sub[h][ol] = acc;
+        __syncthreads();
+        if (h == 0 && mode >= 0)
+            fa.Mred[mode][i * fa.Rp[mode] + r] = ((sub[0][ol] + sub[1][ol]) + sub[2][ol]) + sub[3][ol];
         return;
     }
-    __shared__ double sh[32][PASD_MAXN + 3];
-    double mx = 0.0, l1 = 0.0, nf = 0.0;
-    double r2[PASD_MAXN];
+    // scalars the tail needs, loaded first so that their latency overlaps the reduction
+    double mu = 0.0, tn = 0.0, nuc[PASD_MAXN];
+    int k0 = 0, kp[PASD_MAXN];
+    if (t == 0) {
+        mu = sc->mu;
+        tn = sc->t_norm_fro;
+        k0 = sc->k;
 #pragma unroll
-    for (int n = 0; n < PASD_MAXN; ++n) r2[n] = 0.0;
+        for (int n = 0; n < PASD_MAXN; ++n) {
+            nuc[n] = n < fa.N ? sc->nuclear[n] : 0.0;
+            kp[n] = n < fa.N ? sc->kept[n] : 0;
+        }
+    }
+    // FP32 tree reductions over the region partials (fixed order)
+    float mx = 0.f, l1 = 0.f, nf = 0.f;
+    float r2[PASD_MAXN];
+#pragma unroll
+    for (int n = 0; n < PASD_MAXN; ++n) r2[n] = 0.f;
     for (int p = t; p < fa.nparts; p += nt) {
         const float* q = fa.part + (size_t)p * fa.stride;
-        mx = fmax(mx, (double)q[0]);
-        l1 += (double)q[1];
-        nf = fmax(nf, (double)q[2]);
+        mx = fmaxf(mx, q[0]);
+        l1 += q[1];
+        nf = fmaxf(nf, q[2]);
 #pragma unroll
         for (int n = 0; n < PASD_MAXN; ++n)
-            if (n < fa.N) r2[n] += (double)q[3 + n];
+            if (n < fa.N) r2[n] += q[3 + n];
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
-        l1 += __shfl_down_sync(0xffffffffu, l1, off);
-        nf = fmax(nf, __shfl_down_sync(0xffffffffu, nf, off));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+        nf = fmaxf(nf, __shfl_xor_sync(0xffffffffu, nf, off));
 #pragma unroll
-        for (int n = 0; n < PASD_MAXN; ++n) r2[n] += __shfl_down_sync(0xffffffffu, r2[n], off);
+        for (int n = 0; n < PASD_MAXN; ++n)
+            if (n < fa.N) r2[n] += __shfl_xor_sync(0xffffffffu, r2[n], off);
     }
+    __shared__ float sh[FIN_THREADS / 32][PASD_MAXN + 3];
     const int w = t >> 5, lane = t & 31;
     if (lane == 0) {
         sh[w][0] = mx; sh[w][1] = l1; sh[w][2] = nf;
@@ -479,40 +619,43 @@ __global__ void finalize_kernel(FinalizeArgs fa) {
     if (t == 0) {
         const int nw = (nt + 31) / 32;
         for (int i = 1; i < nw; ++i) {
-            mx = fmax(mx, sh[i][0]);
+            mx = fmaxf(mx, sh[i][0]);
             l1 += sh[i][1];
-            nf = fmax(nf, sh[i][2]);
+            nf = fmaxf(nf, sh[i][2]);
 #pragma unroll
-            for (int n = 0; n < PASD_MAXN; ++n) r2[n] += sh[i][3 + n];
+            for (int n = 0; n < PASD_MAXN; ++n)
+                if (n < fa.N) r2[n] += sh[i][3 + n];
         }
-        double r2max = 0.0;
+        float r2max = 0.f;
 #pragma unroll
         for (int n = 0; n < PASD_MAXN; ++n)
-            if (n < fa.N) r2max = fmax(r2max, r2[n]);
-        const double tn = sc->t_norm_fro;
-        const double fro_rel = tn > 0 ? sqrt(r2max) / tn : 0.0;
+            if (n < fa.N) r2max = fmaxf(r2max, r2[n]);
+        const double fro_rel = tn > 0 ? sqrt((double)r2max) / tn : 0.0;
         double obj = l1;
-        for (int n = 0; n < fa.N; ++n) obj += fa.lambda[n] * sc->nuclear[n];
-        const double mu = sc->mu;
-        sc->res_inf = mx;
+#pragma unroll
+        for (int n = 0; n < PASD_MAXN; ++n)
+            if (n < fa.N) obj += fa.lambda[n] * nuc[n];
+        const double mxd = mx;
+        sc->res_inf = mxd;
         sc->res_fro_rel = fro_rel;
         sc->objective = obj;
         sc->l1_E = l1;
         sc->mu_used = mu;
         const double mun = fa.rho * mu;
         sc->mu = mun < fa.mu_max ? mun : fa.mu_max;
-        const int k = sc->k + 1;
+        const int k = k0 + 1;
         sc->k = k;
         if (fa.trace && k <= fa.max_iter) {
             double* rec = fa.trace + (size_t)(k - 1) * 13;
-            rec[0] = k; rec[1] = mx; rec[2] = fro_rel; rec[3] = obj; rec[4] = mu;
-            for (int n = 0; n < 8; ++n) rec[5 + n] = n < fa.N ? sc->kept[n] : 0;
+            rec[0] = k; rec[1] = mxd; rec[2] = fro_rel; rec[3] = obj; rec[4] = mu;
+#pragma unroll
+            for (int n = 0; n < 8; ++n) rec[5 + n] = kp[n];
         }
-        if (nf > 0.0 || !isfinite(mx)) {
+        if (nf > 0.f || !isfinite(mx)) {
             sc->nonfinite = 1;
             sc->status = -4;   // PASD_ERR_NONFINITE
             sc->done = 1;
-        } else if ((fa.stop_rule == 0 && mx < fa.tol) || (fa.stop_rule == 1 && fro_rel < fa.tol)) {
+        } else if ((fa.stop_rule == 0 && mxd < fa.tol) || (fa.stop_rule == 1 && fro_rel < fa.tol)) {
             sc->status = 0;    // PASD_OK
             sc->done = 1;
         } else if (k >= fa.max_iter) {
@@ -525,8 +668,8 @@ __global__ void finalize_kernel(FinalizeArgs fa) {
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
     int64_t tot = 0;
     for (int n = 0; n < a.N; ++n) tot += a.I[n] * a.R[n];
-    int grid = 1 + (int)((tot + 255) / 256);
-    finalize_kernel<<<grid, 256, 0, s>>>(a);
+    int grid = 1 + (int)((tot + FIN_OUT - 1) / FIN_OUT);
+    finalize_kernel<<<grid, FIN_THREADS, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -534,6 +677,7 @@ void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
 // the SVT, stored like A_n ([pre][Rp][post]); rows at and beyond the kept
 // count are zero. One thread per unfolding column, all modes in one launch.
 // ---------------------------------------------------------------------------
+template <int RB>
 __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     const DevScalars* sc = va.sc;
     if (sc->done) return;
@@ -553,19 +697,31 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     const int64_t a = j / m.post, b = j % m.post;
     const float* src = m.A + a * Rp * m.post + b;
     float* dst = m.V + a * Rp * m.post + b;
-    float av[PASD_MAXR];
-#pragma unroll 4
-    for (int r = 0; r < R; ++r) av[r] = src[(int64_t)r * m.post];
+    // the column of A_n in registers (RB >= R, fully unrolled), all loads in flight
+    float av[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) av[r] = r < R ? src[(int64_t)r * m.post] : 0.f;
     for (int i = 0; i < Rp; ++i) {
         float acc = 0.f;
-        if (i < s)
-            for (int r = 0; r < R; ++r) acc = fmaf(Wt[i * R + r], av[r], acc);
+        if (i < s) {
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+                if (r < R) acc = fmaf(Wt[i * R + r], av[r], acc);
+        }
         dst[(int64_t)i * m.post] = acc;
     }
 }
 
 void launch_vrot(const VrotArgs& a, cudaStream_t s) {
-    vrot_kernel<<<a.cta_start[a.N], 256, 0, s>>>(a);
+    int maxRp = 4;
+    for (int n = 0; n < a.N; ++n) maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
+    const int grid = a.cta_start[a.N];
+    if (maxRp <= 8) vrot_kernel<8><<<grid, 256, 0, s>>>(a);
+    else if (maxRp <= 16) vrot_kernel<16><<<grid, 256, 0, s>>>(a);
+    else if (maxRp <= 24) vrot_kernel<24><<<grid, 256, 0, s>>>(a);
+    else if (maxRp <= 32) vrot_kernel<32><<<grid, 256, 0, s>>>(a);
+    else if (maxRp <= 48) vrot_kernel<48><<<grid, 256, 0, s>>>(a);
+    else vrot_kernel<64><<<grid, 256, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------

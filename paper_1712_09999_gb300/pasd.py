@@ -253,7 +253,7 @@ def pasd_mode_product_noalloc(X, pre: int, I: int, post: int, U, R: int, A, gram
                                            _stream(stream)), "pasd_mode_product_noalloc")
 
 
-PROFILE_SLOTS = ("polar", "apass", "svt", "vrot", "fused", "finalize")
+PROFILE_SLOTS = ("polar", "apass", "svt", "vrot", "fused", "mpass", "finalize")
 
 
 def pasd_profile_iterations(plan: int, iters: int, stream=None) -> dict:
