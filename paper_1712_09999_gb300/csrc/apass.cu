@@ -12,8 +12,10 @@
 // is broadcast from shared memory. Columns past P and rows past I are zero-filled
 // by the copy, so they contribute nothing to A or to the Gram sums.
 #include "pasd_impl.cuh"
+#include "tma.cuh"
 
 #include <algorithm>
+#include <cstring>
 
 namespace pasd {
 
@@ -40,15 +42,76 @@ struct ApLayout {
     static constexpr int gs_stage = rowmajor ? AP_BN * gs_ld : AP_BK * gs_ld;
 };
 
+// Shared memory of the Gram partial reduction (after the A tile [AP_BN][RP + 4]).
+static inline __host__ __device__ int gram_red_floats(int RP) {
+    const int nb = RP / 4, nbt = nb * (nb + 1) / 2;
+    const int nsl = nbt >= AP_THREADS ? 1 : AP_THREADS / nbt;
+    return nsl * nbt * 16;
+}
+
+// Per-CTA Gram partial: the sum over this CTA's columns of A[:, j] A[:, j]^T,
+// columns t and t + 128 of the thread in acc0 / acc1 (zero for absent columns).
+// 4 x 4 blocks on and above the diagonal, each summed over NSL column slices
+// and then over the slices in order (deterministic); written with its mirror.
+// `smem` must be free (no copy in flight) and hold AP_BN (RP + 4) +
+// gram_red_floats(RP) floats.
+template <int RP>
+__device__ __forceinline__ void gram_epilogue(const float* acc0, const float* acc1, float* smem, float* gp) {
+    const int t = threadIdx.x;
+    constexpr int ALD = RP + 4;
+    float* As = smem;   // [AP_BN][ALD]
+#pragma unroll
+    for (int r4 = 0; r4 < RP / 4; ++r4) {
+        *reinterpret_cast<float4*>(As + t * ALD + 4 * r4) =
+            make_float4(acc0[4 * r4], acc0[4 * r4 + 1], acc0[4 * r4 + 2], acc0[4 * r4 + 3]);
+        *reinterpret_cast<float4*>(As + (t + 128) * ALD + 4 * r4) =
+            make_float4(acc1[4 * r4], acc1[4 * r4 + 1], acc1[4 * r4 + 2], acc1[4 * r4 + 3]);
+    }
+    constexpr int NB = RP / 4;
+    constexpr int NBT = NB * (NB + 1) / 2;
+    constexpr int NSL = NBT >= AP_THREADS ? 1 : AP_THREADS / NBT;
+    float* red = smem + AP_BN * ALD;
+    __syncthreads();
+    for (int w = t; w < NBT * NSL; w += AP_THREADS) {
+        int blk = w % NBT, sl = w / NBT;
+        int bi = 0, rem = blk;
+        while (rem >= NB - bi) { rem -= NB - bi; ++bi; }
+        int bj = bi + rem;
+        float g[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) g[q] = 0.f;
+        for (int c = sl; c < AP_BN; c += NSL) {
+            float4 x = *reinterpret_cast<const float4*>(As + c * ALD + 4 * bi);
+            float4 y = *reinterpret_cast<const float4*>(As + c * ALD + 4 * bj);
+            float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) g[p * 4 + q] = fmaf(xs[p], ys[q], g[p * 4 + q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) red[(sl * NBT + blk) * 16 + q] = g[q];
+    }
+    __syncthreads();
+    for (int o = t; o < NBT * 16; o += AP_THREADS) {
+        int blk = o / 16, q = o % 16;
+        float sum = 0.f;
+        for (int sl = 0; sl < NSL; ++sl) sum += red[(sl * NBT + blk) * 16 + q];
+        int bi = 0, rem = blk;
+        while (rem >= NB - bi) { rem -= NB - bi; ++bi; }
+        int bj = bi + rem;
+        int r = 4 * bi + q / 4, c = 4 * bj + q % 4;
+        gp[r * RP + c] = sum;
+        gp[c * RP + r] = sum;
+    }
+}
+
 size_t apass_smem_bytes(int Rp, bool rowmajor) {
     size_t gs = (size_t)AP_STAGES * (rowmajor ? AP_BN * (AP_BK + 4) : AP_BK * (AP_BN + 4));
     size_t us = (size_t)AP_STAGES * AP_BK * Rp;
     size_t pipe = gs + us;
-    size_t epi = (size_t)AP_BN * (Rp + 4);
-    int nb = Rp / 4, nbt = nb * (nb + 1) / 2;
-    int nsl = nbt >= AP_THREADS ? 1 : AP_THREADS / nbt;
-    size_t red = (size_t)nsl * nbt * 16;
-    return 4 * ((pipe > epi ? pipe : epi) + red);
+    size_t epi = (size_t)AP_BN * (Rp + 4) + gram_red_floats(Rp);
+    return 4 * (pipe > epi ? pipe : epi);
 }
 
 int apass_ncta(int64_t P) { return (int)((P + AP_BN - 1) / AP_BN); }
@@ -227,56 +290,7 @@ __device__ __forceinline__ void apass_body(const ApassArgs& a, int cta, float* s
         }
     }
 
-    // ---- Gram partial: sum over this CTA's columns of A[:, j] A[:, j]^T ----
-    constexpr int ALD = RP + 4;
-    float* As = smem;   // [AP_BN][ALD] (reuses the pipeline buffers)
-#pragma unroll
-    for (int r4 = 0; r4 < RP / 4; ++r4) {
-        *reinterpret_cast<float4*>(As + t * ALD + 4 * r4) =
-            make_float4(acc0[4 * r4], acc0[4 * r4 + 1], acc0[4 * r4 + 2], acc0[4 * r4 + 3]);
-        *reinterpret_cast<float4*>(As + (t + 128) * ALD + 4 * r4) =
-            make_float4(acc1[4 * r4], acc1[4 * r4 + 1], acc1[4 * r4 + 2], acc1[4 * r4 + 3]);
-    }
-    constexpr int NB = RP / 4;
-    constexpr int NBT = NB * (NB + 1) / 2;
-    constexpr int NSL = NBT >= AP_THREADS ? 1 : AP_THREADS / NBT;
-    size_t pipe = (size_t)AP_STAGES * (L::gs_stage + AP_BK * RP);
-    size_t epi = (size_t)AP_BN * ALD;
-    float* red = smem + (pipe > epi ? pipe : epi);
-    __syncthreads();
-    for (int w = t; w < NBT * NSL; w += AP_THREADS) {
-        int blk = w % NBT, sl = w / NBT;
-        int bi = 0, rem = blk;
-        while (rem >= NB - bi) { rem -= NB - bi; ++bi; }
-        int bj = bi + rem;
-        float g[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) g[q] = 0.f;
-        for (int c = sl; c < AP_BN; c += NSL) {
-            float4 x = *reinterpret_cast<const float4*>(As + c * ALD + 4 * bi);
-            float4 y = *reinterpret_cast<const float4*>(As + c * ALD + 4 * bj);
-            float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) g[p * 4 + q] = fmaf(xs[p], ys[q], g[p * 4 + q]);
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) red[(sl * NBT + blk) * 16 + q] = g[q];
-    }
-    __syncthreads();
-    float* gp = a.gram_part + (size_t)cta * RP * RP;
-    for (int o = t; o < NBT * 16; o += AP_THREADS) {
-        int blk = o / 16, q = o % 16;
-        float s = 0.f;
-        for (int sl = 0; sl < NSL; ++sl) s += red[(sl * NBT + blk) * 16 + q];
-        int bi = 0, rem = blk;
-        while (rem >= NB - bi) { rem -= NB - bi; ++bi; }
-        int bj = bi + rem;
-        int r = 4 * bi + q / 4, c = 4 * bj + q % 4;
-        gp[r * RP + c] = s;
-        gp[c * RP + r] = s;
-    }
+    gram_epilogue<RP>(acc0, acc1, smem, a.gram_part + (size_t)cta * RP * RP);
 }
 
 static int apass_variant(const ApassArgs& a) {
@@ -357,5 +371,278 @@ int launch_apass_modes(const ApassArgs* a, int N, cudaStream_t s) {
 }
 
 void launch_apass(const ApassArgs& a, cudaStream_t s) { launch_apass_modes(&a, 1, s); }
+
+// ---------------------------------------------------------------------------
+// TMA-fed A-pass. The G tile of each pipeline stage arrives by one bulk tensor
+// copy (and the U rows by another), so a stage costs one issuing thread instead
+// of a copy instruction per 16 bytes per thread, and the copies stay out of the
+// load/store pipe the FMA loop reads shared memory through.
+//   post > 1 : a task is BN consecutive columns inside one a-row of the
+//              unfolding (BN = min(256, post)); the tile is [k][col], dense.
+//   post == 1: a task is 256 consecutive columns (rows of G); the tile is
+//              [col][k] with the 64-byte swizzle (16-byte group g of row c sits
+//              at g ^ ((c >> 1) & 3)), so the float4 reads below are conflict-free.
+// The arithmetic is the cp.async kernel's (same per-thread column pairs and the
+// same order of accumulation), so both give identical results.
+// ---------------------------------------------------------------------------
+struct ApassTmaMaps {
+    CUtensorMap g[PASD_MAXN];
+    CUtensorMap u[PASD_MAXN];
+};
+
+struct ApassTmaPlan {
+    ApassTmaMaps maps;
+    ApassTmaArgs args;
+    size_t smem;
+};
+
+// Stage stride in floats: 512-byte multiples, the period of the 64-byte swizzle,
+// so every stage's G tile starts on a swizzle boundary.
+static inline __host__ __device__ int at_stage_floats(int BN, int RP) {
+    return (AP_BK * BN + AP_BK * RP + 127) / 128 * 128;
+}
+
+template <int RP>
+__global__ void __launch_bounds__(AP_THREADS) apass_tma_kernel(const __grid_constant__ ApassTmaMaps maps,
+                                                               const ApassTmaArgs aa) {
+    extern __shared__ __align__(16) float sm_raw[];
+    float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 511) & ~uintptr_t(511));
+    __shared__ __align__(8) uint64_t full[AT_STAGES];
+    int k = 0;
+    while (k + 1 < aa.count && (int)blockIdx.x >= aa.cta_start[k + 1]) ++k;
+    const ApassTmaMode& m = aa.m[k];
+    DevScalars* sc = aa.sc;
+    if (sc->done) return;
+    const int task = blockIdx.x - aa.cta_start[k];
+    const int t = threadIdx.x;
+    const int64_t I = m.I, post = m.post;
+    const int BN = m.BN;
+    int64_t a0, b0;
+    int ncol;
+    if (!m.rowmajor) {
+        a0 = task / m.nbb;
+        b0 = (int64_t)(task % m.nbb) * BN;
+        ncol = (int)((post - b0) < BN ? (post - b0) : BN);
+    } else {
+        a0 = (int64_t)task * BN;
+        b0 = 0;
+        ncol = (int)((m.pre - a0) < BN ? (m.pre - a0) : BN);
+    }
+    const int nk = (int)((I + AP_BK - 1) / AP_BK);
+    const int sst = at_stage_floats(BN, RP);
+    const int gfl = AP_BK * BN;
+    const uint32_t tx = (uint32_t)(4 * (AP_BK * BN + AP_BK * RP));
+
+    if (t == 0) {
+        for (int s2 = 0; s2 < AT_STAGES; ++s2) mbar_init(&full[s2], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int kc) {
+        const int st = kc % AT_STAGES;
+        float* gs = smem + st * sst;
+        mbar_expect_tx(&full[st], tx);
+        if (!m.rowmajor) {
+            const int c[3] = {(int)b0, kc * AP_BK, (int)a0};
+            tma_load<3>(gs, &maps.g[k], &full[st], c);
+        } else {
+            const int c[2] = {kc * AP_BK, (int)a0};
+            tma_load<2>(gs, &maps.g[k], &full[st], c);
+        }
+        const int cu[2] = {0, kc * AP_BK};
+        tma_load<2>(gs + gfl, &maps.u[k], &full[st], cu);
+    };
+    if (t == 0)
+        for (int s2 = 0; s2 < AT_STAGES - 1 && s2 < nk; ++s2) issue(s2);
+
+    float acc0[RP], acc1[RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) { acc0[r] = 0.f; acc1[r] = 0.f; }
+    bool failed = false;
+    for (int kc = 0; kc < nk; ++kc) {
+        const int st = kc % AT_STAGES;
+        const uint32_t par = (uint32_t)((kc / AT_STAGES) & 1);
+        const bool ok = mbar_wait_bounded(&full[st], par, kWaitPolls);
+        // also orders every thread's reads of the stage refilled below
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        if (t == 0 && kc + AT_STAGES - 1 < nk) issue(kc + AT_STAGES - 1);
+        const float* gs = smem + st * sst;
+        const float* us = gs + gfl;
+        if (!m.rowmajor) {
+            const int c1 = t + 128 < BN ? t + 128 : t;    // a column past the task is never stored
+#pragma unroll 4
+            for (int kk = 0; kk < AP_BK; ++kk) {
+                const float g0 = gs[kk * BN + t];
+                const float g1 = gs[kk * BN + c1];
+                const float4* u4 = reinterpret_cast<const float4*>(us + kk * RP);
+#pragma unroll
+                for (int r4 = 0; r4 < RP / 4; ++r4) {
+                    const float4 u = u4[r4];
+                    acc0[4 * r4 + 0] = fmaf(g0, u.x, acc0[4 * r4 + 0]);
+                    acc0[4 * r4 + 1] = fmaf(g0, u.y, acc0[4 * r4 + 1]);
+                    acc0[4 * r4 + 2] = fmaf(g0, u.z, acc0[4 * r4 + 2]);
+                    acc0[4 * r4 + 3] = fmaf(g0, u.w, acc0[4 * r4 + 3]);
+                    acc1[4 * r4 + 0] = fmaf(g1, u.x, acc1[4 * r4 + 0]);
+                    acc1[4 * r4 + 1] = fmaf(g1, u.y, acc1[4 * r4 + 1]);
+                    acc1[4 * r4 + 2] = fmaf(g1, u.z, acc1[4 * r4 + 2]);
+                    acc1[4 * r4 + 3] = fmaf(g1, u.w, acc1[4 * r4 + 3]);
+                }
+            }
+        } else {
+            const int sw = (t >> 1) & 3;    // the same for columns t and t + 128
+            const float* r0 = gs + t * AP_BK;
+            const float* r1 = gs + (t + 128) * AP_BK;
+#pragma unroll
+            for (int k4 = 0; k4 < AP_BK / 4; ++k4) {
+                const float4 g0v = *reinterpret_cast<const float4*>(r0 + 4 * (k4 ^ sw));
+                const float4 g1v = *reinterpret_cast<const float4*>(r1 + 4 * (k4 ^ sw));
+                const float g0s[4] = {g0v.x, g0v.y, g0v.z, g0v.w};
+                const float g1s[4] = {g1v.x, g1v.y, g1v.z, g1v.w};
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const float4* u4 = reinterpret_cast<const float4*>(us + (4 * k4 + kk) * RP);
+                    const float g0 = g0s[kk], g1 = g1s[kk];
+#pragma unroll
+                    for (int r4 = 0; r4 < RP / 4; ++r4) {
+                        const float4 u = u4[r4];
+                        acc0[4 * r4 + 0] = fmaf(g0, u.x, acc0[4 * r4 + 0]);
+                        acc0[4 * r4 + 1] = fmaf(g0, u.y, acc0[4 * r4 + 1]);
+                        acc0[4 * r4 + 2] = fmaf(g0, u.z, acc0[4 * r4 + 2]);
+                        acc0[4 * r4 + 3] = fmaf(g0, u.w, acc0[4 * r4 + 3]);
+                        acc1[4 * r4 + 0] = fmaf(g1, u.x, acc1[4 * r4 + 0]);
+                        acc1[4 * r4 + 1] = fmaf(g1, u.y, acc1[4 * r4 + 1]);
+                        acc1[4 * r4 + 2] = fmaf(g1, u.z, acc1[4 * r4 + 2]);
+                        acc1[4 * r4 + 3] = fmaf(g1, u.w, acc1[4 * r4 + 3]);
+                    }
+                }
+            }
+        }
+    }
+    if (failed) {
+        // a copy never landed: record it and leave once the copies in flight are
+        // accounted for (bounded), so no copy writes into a reassigned CTA's memory
+        if (t == 0) {
+            for (int s2 = 0; s2 < AT_STAGES; ++s2) mbar_wait_bounded(&full[s2], 0, kWaitPolls);
+            sc->status = -5;   // PASD_ERR_TIMEOUT
+            sc->done = 1;
+            __threadfence();
+        }
+        return;
+    }
+    __syncthreads();   // every stage consumed and no copy in flight: smem is free for the epilogue
+
+    // columns past the task carry no data: zero them for the Gram sums
+    const bool v0 = t < ncol, v1 = t + 128 < ncol;
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+        if (!v0) acc0[r] = 0.f;
+        if (!v1) acc1[r] = 0.f;
+    }
+    // ---- store A (layout [pre][Rp][post]) ----
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float* acc = h ? acc1 : acc0;
+        const int c = t + 128 * h;
+        if (c < ncol) {
+            if (m.rowmajor) {
+                float4* dst = reinterpret_cast<float4*>(m.A + (a0 + c) * RP);
+#pragma unroll
+                for (int r4 = 0; r4 < RP / 4; ++r4)
+                    dst[r4] = make_float4(acc[4 * r4], acc[4 * r4 + 1], acc[4 * r4 + 2], acc[4 * r4 + 3]);
+            } else {
+                float* dst = m.A + a0 * RP * post + b0 + c;
+#pragma unroll
+                for (int r = 0; r < RP; ++r) dst[(int64_t)r * post] = acc[r];
+            }
+        }
+    }
+    gram_epilogue<RP>(acc0, acc1, smem, m.gram_part + (size_t)task * RP * RP);
+}
+
+template <int RP>
+static void launch_tma_rp(const ApassTmaPlan& p, cudaStream_t s) {
+    cudaFuncSetAttribute(apass_tma_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    apass_tma_kernel<RP><<<p.args.cta_start[p.args.count], AP_THREADS, p.smem, s>>>(p.maps, p.args);
+}
+
+void launch_apass_tma(const ApassTmaPlan* p, cudaStream_t s) {
+    switch (p->args.Rp) {
+        case 4: launch_tma_rp<4>(*p, s); break;
+        case 8: launch_tma_rp<8>(*p, s); break;
+        case 12: launch_tma_rp<12>(*p, s); break;
+        case 16: launch_tma_rp<16>(*p, s); break;
+        case 20: launch_tma_rp<20>(*p, s); break;
+        case 24: launch_tma_rp<24>(*p, s); break;
+        case 28: launch_tma_rp<28>(*p, s); break;
+        case 32: launch_tma_rp<32>(*p, s); break;
+        case 40: launch_tma_rp<40>(*p, s); break;
+        case 48: launch_tma_rp<48>(*p, s); break;
+        case 56: launch_tma_rp<56>(*p, s); break;
+        case 64: launch_tma_rp<64>(*p, s); break;
+        default: break;
+    }
+}
+
+bool apass_tma_supported(int64_t I, int64_t post) {
+    if (post == 1) return I % 4 == 0;
+    return post % 4 == 0;
+}
+
+int apass_tma_tasks(int64_t I, int64_t pre, int64_t post) {
+    (void)I;
+    if (post == 1) return (int)((pre + 255) / 256);
+    const int64_t BN = post < 256 ? post : 256;
+    return (int)(pre * ((post + BN - 1) / BN));
+}
+
+ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, char* err, size_t errlen) {
+    ApassTmaPlan* p = new ApassTmaPlan();
+    std::memset(&p->maps, 0, sizeof(p->maps));
+    p->args = ApassTmaArgs{};
+    p->args.count = count;
+    p->args.sc = const_cast<DevScalars*>(a[modes[0]].sc);
+    p->args.Rp = a[modes[0]].Rp;
+    int start = 0;
+    size_t smem = 0;
+    for (int q = 0; q < count; ++q) {
+        const ApassArgs& x = a[modes[q]];
+        ApassTmaMode& mm = p->args.m[q];
+        mm.I = x.I; mm.pre = x.pre; mm.post = x.post; mm.P = x.P;
+        mm.rowmajor = x.post == 1;
+        mm.BN = mm.rowmajor ? 256 : (int)(x.post < 256 ? x.post : 256);
+        mm.nbb = mm.rowmajor ? 1 : (int)((x.post + mm.BN - 1) / mm.BN);
+        mm.A = x.A;
+        mm.gram_part = x.gram_part;
+        const int ntask = apass_tma_tasks(x.I, x.pre, x.post);
+        p->args.cta_start[q] = start;
+        start += ntask;
+        const int Rp = x.Rp;
+        bool ok;
+        if (!mm.rowmajor) {
+            uint64_t d[3] = {(uint64_t)x.post, (uint64_t)x.I, (uint64_t)x.pre};
+            uint32_t b[3] = {(uint32_t)mm.BN, (uint32_t)AP_BK, 1u};
+            ok = encode_tiled_f32(&p->maps.g[q], x.G, 3, d, b, CU_TENSOR_MAP_SWIZZLE_NONE, err, errlen, "A-pass G");
+        } else {
+            uint64_t d[2] = {(uint64_t)x.I, (uint64_t)x.pre};
+            uint32_t b[2] = {(uint32_t)AP_BK, 256u};
+            ok = encode_tiled_f32(&p->maps.g[q], x.G, 2, d, b, CU_TENSOR_MAP_SWIZZLE_64B, err, errlen, "A-pass G");
+        }
+        if (ok) {
+            uint64_t d[2] = {(uint64_t)Rp, (uint64_t)x.I};
+            uint32_t b[2] = {(uint32_t)Rp, (uint32_t)AP_BK};
+            ok = encode_tiled_f32(&p->maps.u[q], x.U, 2, d, b, CU_TENSOR_MAP_SWIZZLE_NONE, err, errlen, "A-pass U");
+        }
+        if (!ok) { delete p; return nullptr; }
+        const size_t pipe = (size_t)AT_STAGES * at_stage_floats(mm.BN, Rp);
+        const size_t epi = (size_t)AP_BN * (Rp + 4) + gram_red_floats(Rp);
+        smem = std::max(smem, 4 * std::max(pipe, epi) + 512);
+    }
+    p->args.cta_start[count] = start;
+    p->smem = smem;
+    return p;
+}
+
+void destroy_apass_tma(ApassTmaPlan* p) { delete p; }
+
 
 }  // namespace pasd

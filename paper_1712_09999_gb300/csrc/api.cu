@@ -53,6 +53,7 @@ struct pasd_ctx {
     int device = 0;
     int num_sms = 0;
     size_t smem_optin = 0;
+    size_t smem_per_sm = 0;
     size_t hbm_budget = 0;
     // served path
     std::mutex mu;
@@ -102,6 +103,16 @@ struct pasd_plan {
     VrotArgs vr{};
     MpassArgs mpa{};
     size_t mp_smem = 0;
+    bool mp_use_tma = false;
+    MpassTmaArgs mpt{};
+    size_t mpt_smem = 0;
+    MpassTmaPlan* mp_tma = nullptr;
+    // A-pass: TMA plans (one per padded rank) and the modes on the cp.async kernel
+    bool ap_use_tma[PASD_MAXN];
+    ApassTmaPlan* ap_tma[PASD_MAXN];
+    int n_ap_tma = 0;
+    ApassArgs ap_plain[PASD_MAXN];
+    int n_ap_plain = 0;
     // graph
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -130,6 +141,7 @@ extern "C" pasd_status pasd_ctx_create(int device, size_t hbm_budget_bytes, pasd
     if (e != cudaSuccess) { delete c; return fail(PASD_ERR_CUDA, cudaGetErrorString(e)); }
     c->num_sms = prop.multiProcessorCount;
     c->smem_optin = prop.sharedMemPerBlockOptin;
+    c->smem_per_sm = prop.sharedMemPerMultiprocessor;
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     c->hbm_budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
@@ -242,10 +254,25 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
         return fail(PASD_ERR_UNSUPPORTED, "no tile shape fits shared memory for these ranks");
     }
     const char* nt = std::getenv("PASD_NO_TMA");
-    pl->want_tma = !(nt && nt[0] == '1') &&
-                   plan_fused_tma(pl->fg, N, Is, Rps, c->num_sms, c->smem_optin);
+    // one CTA per SM with the largest tile that fits, or two resident CTAs per SM
+    // (more copies in flight) with tiles that fit half the SM's shared memory:
+    // whichever keeps more threads resident, two CTAs on a tie
+    if (!(nt && nt[0] == '1')) {
+        FusedGeom one{}, two{};
+        const size_t half = c->smem_per_sm / 2 > 2048 ? c->smem_per_sm / 2 - 1024 : 0;
+        const bool ok1 = plan_fused_tma(one, N, Is, Rps, c->num_sms, c->smem_optin);
+        const bool ok2 = plan_fused_tma(two, N, Is, Rps, 2 * c->num_sms, std::min(half, c->smem_optin));
+        if (ok2 && (!ok1 || 2 * two.nthreads >= one.nthreads)) { pl->fg = two; pl->want_tma = true; }
+        else if (ok1) { pl->fg = one; pl->want_tma = true; }
+    }
     if (!pl->want_tma) pl->fg = pl->fg_plain;
-    for (int n = 0; n < N; ++n) pl->ncta_ap[n] = apass_ncta(pl->m[n].P);
+    const bool tma_ok = !(nt && nt[0] == '1');
+    for (int n = 0; n < N; ++n) {
+        const ModeGeom& g = pl->m[n];
+        pl->ap_use_tma[n] = tma_ok && apass_tma_supported(g.I, g.post);
+        // Gram partials: room for either kernel's CTA count (the TMA plan may be refused later)
+        pl->ncta_ap[n] = std::max(apass_ncta(g.P), apass_tma_tasks(g.I, g.pre, g.post));
+    }
     // M-pass: row strips x column ranges, as many CTAs as fit on the device at
     // once (one wave), split over the modes in proportion to their columns
     {
@@ -279,6 +306,42 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
         pl->mpa.cta_start[N] = start;
         pl->mpa.N = N;
         pl->mp_smem = smem;
+    }
+    // TMA-fed M-pass when every mode's layout allows it: CTAs = row strips x
+    // ranges of whole chunks, one wave, split over the modes by work
+    pl->mp_use_tma = tma_ok;
+    for (int n = 0; n < N; ++n) pl->mp_use_tma = pl->mp_use_tma && mpass_tma_supported(pl->m[n].I, pl->m[n].post);
+    if (pl->mp_use_tma) {
+        int64_t work[PASD_MAXN], tot = 0;
+        size_t smem = 0;
+        for (int n = 0; n < N; ++n) {
+            const ModeGeom& g = pl->m[n];
+            MpassTmaMode& mm = pl->mpt.m[n];
+            mm.I = g.I; mm.pre = g.pre; mm.post = g.post; mm.P = g.P; mm.Rp = g.Rp;
+            mm.rowmajor = g.post == 1;
+            mm.IS = mpass_strip_rows(g.I, g.Rp);
+            mm.nstrips = (int)((g.I + mm.IS - 1) / mm.IS);
+            mm.nch = mpass_tma_chunks(g.pre, g.post);
+            mm.nbb = mm.rowmajor ? 1 : (int)((g.post + MP_CB - 1) / MP_CB);
+            work[n] = (int64_t)mm.nstrips * mm.nch;
+            tot += work[n];
+            smem = std::max(smem, mpass_tma_smem_bytes(mm.IS, g.Rp));
+        }
+        const int slots = c->num_sms * mpass_tma_ctas_per_sm(smem);
+        int start = 0;
+        for (int n = 0; n < N; ++n) {
+            MpassTmaMode& mm = pl->mpt.m[n];
+            int64_t target = (int64_t)((double)slots * (double)work[n] / (double)tot);
+            int64_t ncg = std::max<int64_t>(1, target / mm.nstrips);
+            mm.cpr = (int)((mm.nch + ncg - 1) / ncg);
+            mm.ncg = (mm.nch + mm.cpr - 1) / mm.cpr;
+            pl->n_mp[n] = std::max(pl->n_mp[n], mm.ncg);
+            pl->mpt.cta_start[n] = start;
+            start += mm.nstrips * mm.ncg;
+        }
+        pl->mpt.cta_start[N] = start;
+        pl->mpt.N = N;
+        pl->mpt_smem = smem;
     }
     int nparts = std::max(pl->fg.nregions, pl->fg_plain.nregions);
     // footprint
@@ -318,13 +381,25 @@ static void launch_fused_pass(pasd_plan_t* pl, int output, float* L, cudaStream_
     }
 }
 
+static int launch_apass_all(pasd_plan_t* pl, cudaStream_t s) {
+    int launches = 0;
+    for (int q = 0; q < pl->n_ap_tma; ++q) { launch_apass_tma(pl->ap_tma[q], s); ++launches; }
+    if (pl->n_ap_plain > 0) launches += launch_apass_modes(pl->ap_plain, pl->n_ap_plain, s);
+    return launches;
+}
+
+static void launch_mpass_any(pasd_plan_t* pl, cudaStream_t s) {
+    if (pl->mp_use_tma) launch_mpass_tma(pl->mp_tma, s);
+    else launch_mpass(pl->mpa, pl->mp_smem, s);
+}
+
 static void enqueue_iteration(pasd_plan_t* pl, cudaStream_t s) {
     launch_polar(pl->small, s);
-    pl->ap_launches = launch_apass_modes(pl->ap, pl->N, s);
+    pl->ap_launches = launch_apass_all(pl, s);
     launch_svt(pl->small, s);
     launch_vrot(pl->vr, s);
     launch_fused_pass(pl, 0, nullptr, s);
-    launch_mpass(pl->mpa, pl->mp_smem, s);
+    launch_mpass_any(pl, s);
     launch_finalize(pl->fin, s);
 }
 
@@ -381,7 +456,7 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
         ApassArgs& a = pl->ap[n];
         a.G = pl->G[n]; a.U = pl->U[n]; a.A = pl->A[n]; a.gram_part = pl->gram[n]; a.sc = pl->sc;
         a.I = g.I; a.pre = g.pre; a.post = g.post; a.P = g.P; a.R = g.R; a.Rp = g.Rp;
-        a.ncta = pl->ncta_ap[n];
+        a.ncta = apass_ncta(g.P);      // CTAs of the cp.async kernel
     }
     FusedArgs& fu = pl->fu;
     fu.g = pl->fg;
@@ -439,7 +514,45 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
             fi.nparts = pl->fg.nregions;
         }
     }
-    for (int n = 0; n < N; ++n) fi.n_mp[n] = pl->n_mp[n];
+    // M-pass: the TMA kernel when every mode allows it and its maps are accepted;
+    // the finalize sums exactly the partials the kernel in use writes
+    if (pl->mp_use_tma) {
+        pl->mpt.sc = pl->sc;
+        const float* gp[PASD_MAXN];
+        const float* vp[PASD_MAXN];
+        for (int n = 0; n < N; ++n) {
+            pl->mpt.m[n].part = pl->mp[n];
+            gp[n] = pl->G[n];
+            vp[n] = pl->Vr[n];
+        }
+        char err[256] = {0};
+        pl->mp_tma = make_mpass_tma(pl->mpt, gp, vp, pl->mpt_smem, err, sizeof(err));
+        if (!pl->mp_tma) pl->mp_use_tma = false;
+    }
+    for (int n = 0; n < N; ++n) fi.n_mp[n] = pl->mp_use_tma ? pl->mpt.m[n].ncg : pl->mpa.m[n].ncg;
+
+    // A-pass: TMA plans for the modes whose layout allows them (grouped by padded
+    // rank), the cp.async kernel for the rest or when a tensor map is refused
+    {
+        pl->n_ap_tma = 0;
+        pl->n_ap_plain = 0;
+        bool grouped[PASD_MAXN] = {false};
+        for (int n = 0; n < N; ++n) {
+            if (!pl->ap_use_tma[n] || grouped[n]) continue;
+            int modes[PASD_MAXN], cnt = 0;
+            for (int k = n; k < N; ++k)
+                if (pl->ap_use_tma[k] && !grouped[k] && pl->m[k].Rp == pl->m[n].Rp) { modes[cnt++] = k; grouped[k] = true; }
+            char err[256] = {0};
+            ApassTmaPlan* tp = make_apass_tma(pl->ap, modes, cnt, err, sizeof(err));
+            if (tp) pl->ap_tma[pl->n_ap_tma++] = tp;
+            else for (int q = 0; q < cnt; ++q) pl->ap_use_tma[modes[q]] = false;
+        }
+        for (int n = 0; n < N; ++n) {
+            const ModeGeom& g = pl->m[n];
+            if (!pl->ap_use_tma[n]) pl->ap_plain[pl->n_ap_plain++] = pl->ap[n];
+            sa.m[n].n_gram = pl->ap_use_tma[n] ? apass_tma_tasks(g.I, g.pre, g.post) : apass_ncta(g.P);
+        }
+    }
 
     if (pl->use_graph) {
         CUDA_TRY(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -453,6 +566,8 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
 extern "C" pasd_status pasd_plan_destroy(pasd_plan_t* pl) {
     if (!pl) return fail(PASD_ERR_INVALID_ARG, "plan is NULL");
     if (pl->tma) destroy_fused_tma(pl->tma);
+    for (int q = 0; q < pl->n_ap_tma; ++q) destroy_apass_tma(pl->ap_tma[q]);
+    if (pl->mp_tma) destroy_mpass_tma(pl->mp_tma);
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
@@ -478,7 +593,7 @@ extern "C" pasd_status pasd_profile_iterations(pasd_plan_t* pl, int32_t iters, d
         CUDA_TRY(cudaEventRecord(ev[0], s));
         launch_polar(pl->small, s);
         CUDA_TRY(cudaEventRecord(ev[1], s));
-        launch_apass_modes(pl->ap, pl->N, s);
+        launch_apass_all(pl, s);
         CUDA_TRY(cudaEventRecord(ev[2], s));
         launch_svt(pl->small, s);
         CUDA_TRY(cudaEventRecord(ev[3], s));
@@ -486,7 +601,7 @@ extern "C" pasd_status pasd_profile_iterations(pasd_plan_t* pl, int32_t iters, d
         CUDA_TRY(cudaEventRecord(ev[4], s));
         launch_fused_pass(pl, 0, nullptr, s);
         CUDA_TRY(cudaEventRecord(ev[5], s));
-        launch_mpass(pl->mpa, pl->mp_smem, s);
+        launch_mpass_any(pl, s);
         CUDA_TRY(cudaEventRecord(ev[6], s));
         launch_finalize(pl->fin, s);
         CUDA_TRY(cudaEventRecord(ev[7], s));

@@ -17,6 +17,7 @@
 // Results (E', G_n') overwrite E and G_n in the stage and go back to HBM as
 // bulk tensor stores, clipped to the tensor by the copy engine.
 #include "pasd_impl.cuh"
+#include "tma.cuh"
 
 #include <cuda.h>
 #include <algorithm>
@@ -44,85 +45,6 @@ struct FusedTmaPlan {
     FusedArgs base;
 };
 
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: gives up after `limit` polls (each try_wait may suspend briefly).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
-    for (uint32_t i = 0; i < limit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() {
-    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-}
-
-template <int R>
-__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, const int* c) {
-    const uint32_t d = smem_u32(dst), b = smem_u32(bar);
-    const uint64_t m = reinterpret_cast<uint64_t>(map);
-    if (R == 1)
-        asm volatile("cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3}], [%2];\n"
-                     ::"r"(d), "l"(m), "r"(b), "r"(c[0]) : "memory");
-    else if (R == 2)
-        asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n"
-                     ::"r"(d), "l"(m), "r"(b), "r"(c[0]), "r"(c[1]) : "memory");
-    else if (R == 3)
-        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];\n"
-                     ::"r"(d), "l"(m), "r"(b), "r"(c[0]), "r"(c[1]), "r"(c[2]) : "memory");
-    else if (R == 4)
-        asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];\n"
-                     ::"r"(d), "l"(m), "r"(b), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]) : "memory");
-    else
-        asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, %7}], [%2];\n"
-                     ::"r"(d), "l"(m), "r"(b), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]) : "memory");
-}
-
-template <int R>
-__device__ __forceinline__ void tma_store(const CUtensorMap* map, const void* src, const int* c) {
-    const uint32_t s = smem_u32(src);
-    const uint64_t m = reinterpret_cast<uint64_t>(map);
-    if (R == 2)
-        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n"
-                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]) : "memory");
-    else if (R == 3)
-        asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];\n"
-                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]), "r"(c[2]) : "memory");
-    else if (R == 4)
-        asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];\n"
-                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]) : "memory");
-    else
-        asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];\n"
-                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]) : "memory");
-}
-
-constexpr uint32_t kWaitPolls = 1u << 22;   // bounded mbarrier wait (far above any real copy time)
 
 // ---------------------------------------------------------------------------
 // kernel
@@ -507,9 +429,9 @@ static EncodeTiledFn get_encode() {
     return fn;
 }
 
-// dims / box innermost first
-static bool encode(CUtensorMap* m, const float* base, int rank, const uint64_t* dims, const uint32_t* box,
-                   char* err, size_t errlen, const char* what) {
+// dims / box innermost first (dense C-order array)
+bool encode_tiled_f32(CUtensorMap* m, const float* base, int rank, const uint64_t* dims, const uint32_t* box,
+                      CUtensorMapSwizzle swizzle, char* err, size_t errlen, const char* what) {
     EncodeTiledFn fn = get_encode();
     if (!fn) {
         snprintf(err, errlen, "cuTensorMapEncodeTiled unavailable");
@@ -526,13 +448,18 @@ static bool encode(CUtensorMap* m, const float* base, int rank, const uint64_t* 
         stride *= dims[k];
     }
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<float*>(base), gd, gs, bd, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         snprintf(err, errlen, "cuTensorMapEncodeTiled(%s) failed with %d", what, (int)r);
         return false;
     }
     return true;
+}
+
+static bool encode(CUtensorMap* m, const float* base, int rank, const uint64_t* dims, const uint32_t* box,
+                   char* err, size_t errlen, const char* what) {
+    return encode_tiled_f32(m, base, rank, dims, box, CU_TENSOR_MAP_SWIZZLE_NONE, err, errlen, what);
 }
 
 FusedTmaPlan* make_fused_tma(const FusedArgs& a, const float* T_copy, char* err, size_t errlen) {

@@ -65,6 +65,31 @@ struct ApassArgs {
 };
 
 void launch_apass(const ApassArgs& a, cudaStream_t s);
+
+// TMA-fed A-pass (post % 4 == 0, or post == 1 with I % 4 == 0): one launch per
+// group of modes with the same padded rank; one CTA per task (column block).
+constexpr int AT_STAGES = 3;
+struct ApassTmaMode {
+    int64_t I, pre, post, P;
+    int BN;                // columns per task
+    int nbb;               // tasks per a-row (post > 1)
+    int rowmajor;          // post == 1
+    float* A;              // [pre][Rp][post]
+    float* gram_part;      // [tasks][Rp][Rp]
+};
+struct ApassTmaArgs {
+    int count, Rp;
+    DevScalars* sc;
+    ApassTmaMode m[PASD_MAXN];
+    int cta_start[PASD_MAXN + 1];
+};
+struct ApassTmaPlan;
+bool apass_tma_supported(int64_t I, int64_t post);
+int apass_tma_tasks(int64_t I, int64_t pre, int64_t post);
+// modes[0..count) index `a`; all share a[modes[0]].Rp. nullptr (with err) if a map is refused.
+ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, char* err, size_t errlen);
+void launch_apass_tma(const ApassTmaPlan* p, cudaStream_t s);
+void destroy_apass_tma(ApassTmaPlan* p);
 // All modes in as few launches as possible (one per distinct padded rank);
 // returns the number of launches.
 int launch_apass_modes(const ApassArgs* a, int N, cudaStream_t s);
@@ -167,6 +192,35 @@ size_t mpass_smem_bytes(int IS, int Rp, int variant);
 int mpass_variant(int64_t I, int64_t post);
 int mpass_strip_rows(int64_t I, int Rp);
 int mpass_ctas_per_sm(size_t smem);
+
+// TMA-fed M-pass (post == 1 with I % 4 == 0, or post % 4 == 0 and post >= MP_CB):
+// one launch for all modes; CTA = (row strip, range of cpr chunks of MP_CB columns).
+constexpr int MT_STAGES = 3;
+struct MpassTmaMode {
+    int64_t I, pre, post, P;
+    int Rp, IS, nstrips;
+    int nch;               // chunks (post > 1: pre * nbb; post == 1: ceil(pre / MP_CB))
+    int nbb;               // chunks per a-row (post > 1)
+    int cpr;               // chunks per column range
+    int ncg;               // column ranges
+    int rowmajor;          // post == 1
+    float* part;           // [ncg][I][Rp]
+};
+struct MpassTmaArgs {
+    int N;
+    DevScalars* sc;
+    MpassTmaMode m[PASD_MAXN];
+    int cta_start[PASD_MAXN + 1];
+};
+struct MpassTmaPlan;
+bool mpass_tma_supported(int64_t I, int64_t post);
+int mpass_tma_chunks(int64_t pre, int64_t post);
+size_t mpass_tma_smem_bytes(int IS, int Rp);
+int mpass_tma_ctas_per_sm(size_t smem);
+MpassTmaPlan* make_mpass_tma(const MpassTmaArgs& a, const float* const* G, const float* const* V, size_t smem,
+                             char* err, size_t errlen);
+void launch_mpass_tma(const MpassTmaPlan* p, cudaStream_t s);
+void destroy_mpass_tma(MpassTmaPlan* p);
 void launch_mpass(const MpassArgs& a, size_t smem, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
