@@ -35,7 +35,7 @@ constexpr int TILE_SCRATCH = 4096;   // floats of split partial sums for tile_At
 // Block-wide cyclic Jacobi eigen-solver for a symmetric n x n matrix.
 //   A  (ld x ld, n x n used) is overwritten; eigenvalues end on the diagonal.
 //   V  receives the eigenvectors (columns). A2, V2 are work buffers of the same
-//   shape. Returns the buffers holding the result through *Aout / *Vout.
+//   shape. Returns the buffers holding the result.
 // Pairs follow the round-robin (circle) ordering, so every round applies m/2
 // disjoint rotations at once (m = n rounded up to even; an odd n gets a zero
 // dummy index). A rotation is skipped when |a_pq| <= tol * sqrt(|a_pp a_qq|),
@@ -43,13 +43,19 @@ constexpr int TILE_SCRATCH = 4096;   // floats of split partial sums for tile_At
 // eigenvalues of graded matrices. A sweep starts only if some off-diagonal
 // entry fails that test.
 //
-// Each thread owns elements (i, j) of the rotated matrix and derives the two
-// rotations it needs (those of the pairs holding i and j) from the previous
-// matrix itself, so a round needs a single barrier. The rotation of a pair is
-// computed from its smaller index p and larger index q, identically by every
-// thread that needs it, and the element update is evaluated in an order that
-// is symmetric in (i, j) with explicit rounding, so A stays exactly symmetric.
+// A round computes the rotation of every index once (thread i < m, for the pair
+// holding i; both members of a pair evaluate it identically from the smaller
+// index p and the larger index q), then every thread updates its elements of
+// A and V from the two rotations it needs; two barriers per round. The element
+// update is evaluated in an order that is symmetric in (i, j) with explicit
+// rounding, so A stays exactly symmetric.
 // ---------------------------------------------------------------------------
+// Buffers holding the eigenvalues (diagonal) and eigenvectors (columns) on return.
+struct EigBufs {
+    float* A;
+    float* V;
+};
+
 __device__ __forceinline__ int rr_partner(int i, int round, int m) {
     // index 0 stays fixed and meets 1 + round; index 1 + x (x != round) meets
     // 1 + y with x + y = 2 round (mod m - 1)
@@ -62,7 +68,11 @@ __device__ __forceinline__ int rr_partner(int i, int round, int m) {
     return 1 + y;
 }
 
-// J restricted to the pair {i, pi}: J[i][i] = ci, J[pi][i] = si.
+// J restricted to the pair {i, pi}: J[i][i] = ci, J[pi][i] = si. The tangent is
+// formed with the hardware's approximate reciprocal and reciprocal square root
+// (a Jacobi round is a chain of dependent steps; the correctly rounded forms
+// made it about a quarter slower); c and s come from the same t, so the
+// rotation is orthogonal to rounding whatever t's last bits are.
 __device__ __forceinline__ int pair_rotation(const float* A, int ld, int i, int pi, float tol, float& ci,
                                              float& si) {
     const int p = min(i, pi), q = max(i, pi);
@@ -70,11 +80,15 @@ __device__ __forceinline__ int pair_rotation(const float* A, int ld, int i, int 
     float c = 1.f, s = 0.f;
     int rot = 0;
     if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq))) {
-        const float theta = (aqq - app) / (2.f * apq);
+        const float theta = __fdividef(aqq - app, 2.f * apq);
         float tt;
-        if (fabsf(theta) > 1e18f) tt = 0.5f / theta;
-        else tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(1.f + theta * theta));
-        c = rsqrtf(1.f + tt * tt);
+        if (fabsf(theta) > 1e18f) {
+            tt = __fdividef(0.5f, theta);
+        } else {
+            const float r = fmaf(theta, theta, 1.f);
+            tt = copysignf(__fdividef(1.f, fabsf(theta) + r * rsqrtf(r)), theta);
+        }
+        c = rsqrtf(fmaf(tt, tt, 1.f));
         s = tt * c;
         rot = 1;
     }
@@ -83,8 +97,9 @@ __device__ __forceinline__ int pair_rotation(const float* A, int ld, int i, int 
     return rot;
 }
 
-__device__ void block_jacobi(float* A, float* V, float* A2, float* V2, int n, int ld, float tol,
-                             int max_sweeps, float** Aout, float** Vout) {
+// pc: m ints, cs: 2 m floats of shared scratch for the round's rotations.
+__device__ EigBufs block_jacobi(float* A, float* V, float* A2, float* V2, int* pc, float* cs, int n, int ld,
+                                float tol, int max_sweeps) {
     const int t = threadIdx.x, nt = blockDim.x;
     const int m = n + (n & 1);
     for (int idx = t; idx < ld * ld; idx += nt) {
@@ -106,12 +121,19 @@ __device__ void block_jacobi(float* A, float* V, float* A2, float* V2, int n, in
             if (!__syncthreads_or(need)) break;
             for (int round = 0; round < m - 1; ++round) {
                 int rot = 0;
+                if (t < m) {
+                    const int pi = rr_partner(t, round, m);
+                    float ci, si;
+                    rot = pair_rotation(A, ld, t, pi, tol, ci, si);
+                    pc[t] = pi;
+                    cs[2 * t] = ci;
+                    cs[2 * t + 1] = si;
+                }
+                if (!__syncthreads_or(rot)) continue;
                 for (int idx = t; idx < m * m; idx += nt) {
                     const int i = idx / m, j = idx % m;
-                    const int pi = rr_partner(i, round, m), pj = rr_partner(j, round, m);
-                    float ci, si, cj, sj;
-                    rot |= pair_rotation(A, ld, i, pi, tol, ci, si);
-                    rot |= pair_rotation(A, ld, j, pj, tol, cj, sj);
+                    const int pi = pc[i], pj = pc[j];
+                    const float ci = cs[2 * i], si = cs[2 * i + 1], cj = cs[2 * j], sj = cs[2 * j + 1];
                     const float t1 = __fmul_rn(__fmul_rn(ci, cj), A[i * ld + j]);
                     const float t2 = __fmul_rn(__fmul_rn(ci, sj), A[i * ld + pj]);
                     const float t3 = __fmul_rn(__fmul_rn(si, cj), A[pi * ld + j]);
@@ -121,15 +143,20 @@ __device__ void block_jacobi(float* A, float* V, float* A2, float* V2, int n, in
                     A2[i * ld + j] = v;
                     if (i < n) V2[i * ld + j] = fmaf(V[i * ld + pj], sj, V[i * ld + j] * cj);
                 }
-                if (__syncthreads_or(rot)) {
-                    float* tA = A; A = A2; A2 = tA;
-                    float* tV = V; V = V2; V2 = tV;
-                }
+                __syncthreads();
+                float* tA = A; A = A2; A2 = tA;
+                float* tV = V; V = V2; V2 = tV;
             }
         }
     }
-    *Aout = A;
-    *Vout = V;
+    return EigBufs{A, V};
+}
+
+// Symmetric eigen-solve of the n x n matrix in A (block-wide Jacobi; a single
+// warp running the same rounds measured about twice as slow on 20 x 20 here).
+__device__ __forceinline__ EigBufs sym_eig(float* A, float* V, float* A2, float* V2, int* pc, float* cs,
+                                           int n, int ld, float tol, int max_sweeps) {
+    return block_jacobi(A, V, A2, V2, pc, cs, n, ld, tol, max_sweeps);
 }
 
 // Descending order of the diagonal of A (n x n, ld): perm[rank] = index.
@@ -277,17 +304,35 @@ __device__ void inv_sqrt_from_eig(const float* D, const float* Q, int n, int ld,
 }
 
 // dst[i][c] = src[i][c0 + c] for c < w, 0 for w <= c < round4(w); rows x ...
+// (eight elements per thread per pass, loaded before any is stored, so the
+// global reads overlap instead of forming a chain)
 __device__ void copy_cols(const float* src, int lds, int c0, int w, int64_t rows, float* dst, int ldd) {
     const int w4 = (w + 3) & ~3;
-    for (int64_t idx = threadIdx.x; idx < rows * w4; idx += blockDim.x) {
-        const int64_t i = idx / w4;
-        const int c = (int)(idx % w4);
-        dst[i * ldd + c] = c < w ? src[i * lds + c0 + c] : 0.f;
+    const int64_t tot = rows * w4;
+    const int64_t step = (int64_t)blockDim.x;
+    for (int64_t base = threadIdx.x; base < tot; base += 8 * step) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t idx = base + u * step;
+            v[u] = 0.f;
+            if (idx < tot) {
+                const int64_t i = idx / w4;
+                const int c = (int)(idx % w4);
+                if (c < w) v[u] = src[i * lds + c0 + c];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t idx = base + u * step;
+            if (idx < tot) dst[(idx / w4) * ldd + (idx % w4)] = v[u];
+        }
     }
 }
 
 struct JacobiBufs {
-    float *A, *V, *A2, *V2;
+    float *A, *V, *A2, *V2, *cs;
+    int* pc;
 };
 
 __device__ JacobiBufs carve_jacobi(float* base, int ld) {
@@ -296,9 +341,12 @@ __device__ JacobiBufs carve_jacobi(float* base, int ld) {
     b.V = b.A + ld * ld;
     b.A2 = b.V + ld * ld;
     b.V2 = b.A2 + ld * ld;
+    b.cs = b.V2 + ld * ld;
+    b.pc = reinterpret_cast<int*>(b.cs + 2 * ld);
     return b;
 }
-__host__ __device__ constexpr int jacobi_floats(int ld) { return 4 * ld * ld; }
+// (a multiple of 4 floats, so what follows stays 16-byte aligned)
+__host__ __device__ constexpr int jacobi_floats(int ld) { return 4 * ld * ld + 4 * ld; }
 
 // Row stride of the I x R matrices of the U-step in shared memory: a multiple of
 // 4 with (stride / 4) odd, so float4 rows of consecutive rows hit distinct banks.
@@ -363,8 +411,9 @@ __global__ void __launch_bounds__(SM_THREADS) svt_kernel(SmallArgs sa) {
         __syncthreads();
     }
     // 2. eigen-decomposition
-    float *Ae, *Ve;
-    block_jacobi(jb.A, jb.V, jb.A2, jb.V2, R, ld, 1e-6f, 30, &Ae, &Ve);
+    const EigBufs eb = sym_eig(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, R, ld, 1e-6f, 30);
+    const float* Ae = eb.A;
+    const float* Ve = eb.V;
     sort_desc(Ae, R, ld, perm);
     // 3. thresholds, sorted eigenvectors (W), kept count and nuclear norm
     const float tau = (float)(m.lambda / mu);
@@ -451,8 +500,9 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
         __syncthreads();
         // B1 = M^T M, Z1 = B1^{-1/2}, P1 = M Z1
         tile_AtB(Pw, LD, s, Pw, LD, s, I, jb.A, ld, true, tsc);
-        float *Ae, *Ve;
-        block_jacobi(jb.A, jb.V, jb.A2, jb.V2, s, ld, 1e-6f, 30, &Ae, &Ve);
+        const EigBufs eb = sym_eig(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, s, ld, 1e-6f, 30);
+        const float* Ae = eb.A;
+        const float* Ve = eb.V;
         inv_sqrt_from_eig(Ae, Ve, s, ld, Z);
         tile_AB(Pw, LD, s, Z, ld, s4, I, Mw, LD, false);
         __syncthreads();
@@ -468,8 +518,9 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
             __syncthreads();
         }
         tile_AtB(Bw, LD, q, Bw, LD, q, I, jb.A, ld, true, tsc);
-        float *Ae, *Ve;
-        block_jacobi(jb.A, jb.V, jb.A2, jb.V2, q, ld, 1e-6f, 30, &Ae, &Ve);
+        const EigBufs eb = sym_eig(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, q, ld, 1e-6f, 30);
+        const float* Ae = eb.A;
+        const float* Ve = eb.V;
         inv_sqrt_from_eig(Ae, Ve, q, ld, Z);
         tile_AB(Bw, LD, q, Z, ld, q4, I, Xb, LD, false);
         __syncthreads();
@@ -697,18 +748,40 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     const int64_t a = j / m.post, b = j % m.post;
     const float* src = m.A + a * Rp * m.post + b;
     float* dst = m.V + a * Rp * m.post + b;
-    // the column of A_n in registers (RB >= R, fully unrolled), all loads in flight
+    // the column of A_n in registers (RB >= Rp, fully unrolled), all loads in
+    // flight; with post == 1 the column is Rp contiguous floats (float4 moves)
     float av[RB];
+    if (m.post == 1) {
 #pragma unroll
-    for (int r = 0; r < RB; ++r) av[r] = r < R ? src[(int64_t)r * m.post] : 0.f;
-    for (int i = 0; i < Rp; ++i) {
+        for (int r4 = 0; r4 < RB / 4; ++r4) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (4 * r4 < Rp) v = reinterpret_cast<const float4*>(src)[r4];
+            av[4 * r4] = v.x; av[4 * r4 + 1] = v.y; av[4 * r4 + 2] = v.z; av[4 * r4 + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < RB; ++r) av[r] = r < R ? src[(int64_t)r * m.post] : 0.f;
+    }
+    float out[RB];
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
         float acc = 0.f;
         if (i < s) {
 #pragma unroll
             for (int r = 0; r < RB; ++r)
                 if (r < R) acc = fmaf(Wt[i * R + r], av[r], acc);
         }
-        dst[(int64_t)i * m.post] = acc;
+        out[i] = acc;
+    }
+    if (m.post == 1) {
+#pragma unroll
+        for (int i4 = 0; i4 < RB / 4; ++i4)
+            if (4 * i4 < Rp)
+                reinterpret_cast<float4*>(dst)[i4] = make_float4(out[4 * i4], out[4 * i4 + 1], out[4 * i4 + 2], out[4 * i4 + 3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+            if (i < Rp) dst[(int64_t)i * m.post] = out[i];
     }
 }
 
