@@ -56,7 +56,7 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-FUSED_SOURCES = ("fused_tma.cu", "fused.cu")   # the kernel and its tile planner
+FUSED_SOURCES = ("fused_tma.cu", "fused.cu", "tma.cuh")   # the kernel, its tile planner, its copy wrappers
 
 
 def _fused_src_hash():
@@ -258,7 +258,7 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (fused_ms / 1000.0) / 1e9
     traffic = _fused_traffic()
-    roofline = {"bound": "hbm", "kernel": "fused elementwise pass (refold, E-shrink, multipliers, G A^T)",
+    roofline = {"bound": "hbm", "kernel": "fused elementwise pass (refold Z_n, E-step, multipliers, residuals)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
                 "profiled_bodies": [k0 + 1, k0 + 30], "kept_mean": kept_mean.tolist(),
