@@ -16,7 +16,10 @@ added between steps.
 Extra keys: roofline of the dominant kernel (CUDA-event duration of the fused
 elementwise pass vs its algorithmic bytes), clocks sampled during the timed
 region, e2e (whole solves through pasd_solve_host with pinned host buffers),
-and cpu_baseline (the FP64 oracle on the host cores, a bounded sample).
+serving (Poisson arrivals of planted cubes of sides 32-256 through
+pasd_submit / pasd_poll: solves/s, p50 / p99 latency, and the same requests
+solved one at a time), video (loop bodies/s on the 144x176x3x300 colour-video
+shape) and cpu_baseline (the FP64 oracle on the host cores, a bounded sample).
 
 --impl reference times the FP64 oracle (the method as the paper defines it),
 each step one loop body on the same 200^3 workload.
@@ -169,6 +172,115 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def _serving(P, torch, ctx, args):
+    """Continuous-batching service: Poisson arrivals of planted cubes through
+    pasd_submit / pasd_poll, against the same requests solved one at a time."""
+    import numpy as np
+    from paper_1712_09999_gb300 import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    specs = synth.serving_mix(args.serve_problems, seed=4)
+    tg = time.perf_counter()
+    probs = [synth.serving_problem(sp) for sp in specs]
+    gen_s = time.perf_counter() - tg
+    Ts = [torch.from_numpy(pr.T).to(dev) for pr in probs]
+    slots = []
+    serial_ms = []
+    iters = []
+    for q, sp in enumerate(specs):
+        prm = P.make_params(sp.dims, sp.rank_bounds, max_iter=1000)
+        row = []
+        for _ in range(args.serve_slots):
+            plan, _ = P.pasd_plan(ctx, prm)
+            L = torch.empty_like(Ts[q])
+            E = torch.empty_like(Ts[q])
+            P.pasd_solve(plan, Ts[q], L, E)          # allocation, graph capture, warm-up
+            row.append((plan, L, E))
+        slots.append(row)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = P.pasd_solve(row[0][0], Ts[q], row[0][1], row[0][2])
+        e1.record()
+        torch.cuda.synchronize()
+        serial_ms.append(e0.elapsed_time(e1))
+        iters.append(int(r.iters))
+    n_req = int(args.serve_rate * args.serve_seconds)
+    arrivals = synth.poisson_arrivals(args.serve_rate, n_req, seed=5)
+    which = np.random.Generator(np.random.PCG64(6)).integers(0, len(specs), size=n_req)
+    nxt = [0] * len(specs)
+    pending = {}
+    lat, finish, bad = [], [], 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    i = 0
+    while i < n_req or pending:
+        now = time.perf_counter() - t0
+        while i < n_req and arrivals[i] <= now:
+            q = int(which[i])
+            plan, L, E = slots[q][nxt[q]]
+            nxt[q] = (nxt[q] + 1) % len(slots[q])
+            pending[P.pasd_submit(ctx, plan, Ts[q], L, E)] = float(arrivals[i])
+            i += 1
+        for tk in list(pending):
+            st, _ = P.pasd_poll(ctx, tk)
+            if st != P.PENDING:
+                f = time.perf_counter() - t0
+                lat.append(f - pending.pop(tk))
+                finish.append(f)
+                bad += st not in (P.OK, P.NOT_CONVERGED)
+        time.sleep(0.0002)
+    span = max(finish) - float(arrivals[0])
+    serial_s = sum(serial_ms[int(q)] for q in which) / 1000.0
+    for row in slots:
+        for plan, _, _ in row:
+            P.pasd_plan_destroy(plan)
+    return {"offered_rate": args.serve_rate, "requests": n_req, "solves_per_s": n_req / span,
+            "p50_ms": 1000 * _percentile(lat, 50), "p99_ms": 1000 * _percentile(lat, 99),
+            "serial_solves_per_s": n_req / serial_s, "failed": bad, "precision": "fp32",
+            "mix": f"{len(specs)} planted cubes, side log-uniform 32-256, Tucker 3-20, R=floor(1.2 r), "
+                   f"5-30% corruption (seed 4); {args.serve_slots} plans per problem; Poisson arrivals "
+                   f"(seed 5) for {args.serve_seconds} s",
+            "sides": [sp.dims[0] for sp in specs], "iters_per_solve": iters,
+            "serial_ms_per_solve": [round(x, 2) for x in serial_ms], "generation_s": round(gen_s, 1)}
+
+
+def _video(P, torch, ctx, args):
+    """Loop bodies per second on the colour-video shape 144x176x3x300, R = (20, 20, 3, 5),
+    the paper's default lambda_n, timed over a fixed number of bodies past the activation."""
+    from paper_1712_09999_gb300 import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pr = synth.video()
+    T = torch.from_numpy(pr.T).to(dev)
+    plan, footprint = P.pasd_plan(ctx, P.make_params(pr.T.shape, (20, 20, 3, 5), stop=P.STOP_FIXED_ITERS,
+                                                     max_iter=10 ** 6))
+    stream = torch.cuda.current_stream()
+    P.pasd_begin(plan, T, stream)
+    P.pasd_iterate(plan, args.video_pre, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    P.pasd_iterate(plan, args.video_iters, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    tr = __import__("numpy").zeros((args.video_pre + args.video_iters, P.TRACE_STRIDE))
+    P.pasd_state_get(plan, P.STATE_TRACE, 0, tr)
+    P.pasd_plan_destroy(plan)
+    return {"workload": "video 144x176x3x300 (rank-1 background, 16 moving rectangles, 5% voxels, seed 2), "
+                        "R=(20,20,3,5), paper-default lambda_n", "iters_per_s": args.video_iters / (ms / 1000.0),
+            "bodies_timed": [args.video_pre + 1, args.video_pre + args.video_iters],
+            "kept_at_end": tr[-1, 5:9].astype(int).tolist(), "footprint_bytes": footprint}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -288,6 +400,10 @@ def run_ours(args):
             "clocks": clocks, "roofline": roofline, "e2e": e2e,
             "gpu_launches": args.steps * P.pasd_launches_per_iter(plan) +
                             3 * sum(1 for q in range(args.warmup, args.warmup + args.steps) if q % k_conv == 0)}
+    if rank == 0 and not args.no_serving:
+        line["serving"] = _serving(P, torch, ctx, args)
+    if rank == 0 and not args.no_video:
+        line["video"] = _video(P, torch, ctx, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, el = _oracle_iters_per_s(pr.T, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -341,6 +457,14 @@ def main():
     ap.add_argument("--e2e-solves", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served-throughput measurement")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window (s)")
+    ap.add_argument("--serve-problems", type=int, default=8)
+    ap.add_argument("--serve-slots", type=int, default=3, help="plans per problem")
+    ap.add_argument("--no-video", action="store_true", help="skip the video-shape measurement")
+    ap.add_argument("--video-pre", type=int, default=150)
+    ap.add_argument("--video-iters", type=int, default=200)
     args = ap.parse_args()
     if args.profile_workload:
         run_profile_workload(args)

@@ -103,3 +103,91 @@ def random_tensor(dims, seed: int, dtype=np.float32) -> np.ndarray:
     """Unstructured N(0,1) tensor (kernel-level tests)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal(tuple(dims)).astype(dtype)
+
+
+@dataclass
+class RequestSpec:
+    """One served solve: a planted cube with its solver rank bounds."""
+
+    dims: tuple
+    tucker: tuple
+    rank_bounds: tuple
+    rho: float
+    seed: int
+
+
+def serving_mix(n: int, seed: int = 4, side_lo: int = 32, side_hi: int = 256) -> list:
+    """Request shapes of the serving workload.
+
+    Cube side log-uniform on [side_lo, side_hi]; Tucker rank r_n uniform on
+    {3, ..., 20} per mode; rank bound floor(1.2 r_n), at most the side;
+    corruption fraction uniform on [0.05, 0.30] (values U[-1,1] max|L0|).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for q in range(n):
+        side = int(round(float(np.exp(rng.uniform(np.log(side_lo), np.log(side_hi))))))
+        tucker = tuple(int(rng.integers(3, 21)) for _ in range(3))
+        bounds = tuple(min(side, int(np.floor(1.2 * r))) for r in tucker)
+        rho = float(rng.uniform(0.05, 0.30))
+        out.append(RequestSpec((side,) * 3, tucker, bounds, rho, 1000 + seed * 100 + q))
+    return out
+
+
+def serving_problem(spec: RequestSpec) -> Problem:
+    return planted(spec.dims, spec.tucker, spec.rho, spec.seed, scale="max", amp=1.0)
+
+
+def poisson_arrivals(rate: float, count: int, seed: int = 5) -> np.ndarray:
+    """Arrival times (seconds from 0) of `count` requests at Poisson rate `rate`."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))
+
+
+def video(height: int = 144, width: int = 176, frames: int = 300, seed: int = 2,
+          n_rect: int = 16, coverage: float = 0.05) -> Problem:
+    """Colour-video-shaped tensor, modes (height, width, channel, frame).
+
+    Background: one frame of U[0,1] noise smoothed by a Gaussian of 4 pixels per
+    channel and scaled to [0,1], times a per-frame gain 1 + 0.05 U[-1,1], so it is
+    rank 1 along the frame mode. Foreground: n_rect rectangles with sides in
+    {8, ..., 24}, a random colour in [0,1]^3 and a constant velocity of up to 2
+    pixels per frame (reflecting at the borders), each visible over one
+    contiguous window of frames sized so that the expected fraction of covered
+    voxels is `coverage`. Covered pixels are replaced: E0 = T - L0.
+    """
+    from scipy.ndimage import gaussian_filter
+    rng = np.random.Generator(np.random.PCG64(seed))
+    bg = rng.uniform(0.0, 1.0, size=(height, width, 3))
+    for c in range(3):
+        bg[:, :, c] = gaussian_filter(bg[:, :, c], sigma=4.0, mode="reflect")
+    bg = (bg - bg.min()) / max(bg.max() - bg.min(), 1e-12)
+    gain = 1.0 + 0.05 * rng.uniform(-1.0, 1.0, size=frames)
+    l0 = bg[:, :, :, None] * gain[None, None, None, :]
+    t = l0.copy()
+    sides = rng.integers(8, 25, size=(n_rect, 2))
+    mean_area = float(np.mean(sides[:, 0] * sides[:, 1]))
+    always_on = n_rect * mean_area / (height * width)
+    win = max(1, min(frames, int(round(frames * coverage / max(always_on, 1e-12)))))
+    for q in range(n_rect):
+        h, w = int(sides[q, 0]), int(sides[q, 1])
+        colour = rng.uniform(0.0, 1.0, size=3)
+        y, x = rng.uniform(0, height - h), rng.uniform(0, width - w)
+        vy, vx = rng.uniform(-2.0, 2.0), rng.uniform(-2.0, 2.0)
+        start = int(rng.integers(0, frames - win + 1))
+        for f in range(frames):
+            if start <= f < start + win:
+                yi, xi = int(y), int(x)
+                t[yi:yi + h, xi:xi + w, :, f] = colour
+            y += vy
+            x += vx
+            if y < 0 or y > height - h:
+                vy = -vy
+                y = min(max(y, 0.0), float(height - h))
+            if x < 0 or x > width - w:
+                vx = -vx
+                x = min(max(x, 0.0), float(width - w))
+    e0 = t - l0
+    support = np.flatnonzero(e0.reshape(-1) != 0)
+    desc = f"video {height}x{width}x3x{frames} rect={n_rect} coverage={coverage} seed={seed}"
+    return Problem(T=t.astype(np.float32), L0=l0, E0=e0, support=support, desc=desc)

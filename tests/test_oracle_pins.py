@@ -343,3 +343,32 @@ def test_recovers_planted_tensor_and_stops():
     # recovered sparse part sits on the corrupted support
     big = np.abs(r.E.ravel()) > 1e-6 * np.abs(pr.T).max()
     assert np.mean(np.isin(np.flatnonzero(big), pr.support)) > 0.99
+
+
+def test_fp32_state_floor_dense_sparse_part():
+    # Not a pin of the oracle: the size of the difference any FP32-storage solver
+    # must show against it. Rounding the oracle's own state (E, Y_n, U_n, V_n) to
+    # float32 after every loop body moves E by more than 1e-5 relative on the
+    # reduced video-shaped tensor (dense E of magnitude ~1e-2, formed from
+    # differences of O(0.3) values), while on a planted cube with sparse outliers
+    # the same rounding stays near 1e-7. This is why the GPU parity test holds the
+    # video case's E to 1e-4 and every sparse-E case to 1e-5.
+    r32 = lambda x: x.astype(np.float32).astype(np.float64)
+
+    def floor(pr, ranks, iters):
+        T = pr.T.astype(np.float64)
+        p = O.Params(ranks=ranks, lambdas=O.paper_lambdas(pr.T.shape), stop="fixed", max_iter=iters)
+        exact = O.pasd(T, p)
+        st = O.init_state(T, p.ranks, p.mu0)
+        for _ in range(iters):
+            O.step(T, st, p)
+            st.E = r32(st.E)
+            st.Y = [r32(y) for y in st.Y]
+            st.U = [r32(u) for u in st.U]
+            st.V = [r32(v) for v in st.V]
+        return np.linalg.norm(st.E - exact.E) / np.linalg.norm(exact.E)
+
+    video = floor(synth.video(height=36, width=44, frames=40, n_rect=4, seed=3), (10, 10, 3, 5), 150)
+    cube = floor(synth.planted((24, 20, 16), (3, 3, 2), 0.1, 7, scale="std", amp=5.0), (4, 4, 3), 150)
+    assert 1e-5 < video < 1e-4
+    assert cube < 1e-6
