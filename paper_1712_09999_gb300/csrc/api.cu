@@ -81,6 +81,15 @@ struct pasd_plan {
     bool want_tma = false;
     FusedTmaPlan* tma = nullptr;
     float* Tc = nullptr;     // plan-owned copy of the observation
+    // The last mode is padded to a multiple of 4 (zeros) when that lets the TMA
+    // kernels run (N <= 4): the padded entries stay exactly zero through every
+    // step (T = 0 there gives E' = 0, Y' = 0, and U's padded rows stay zero), so the
+    // result on the real entries is the unpadded one. D and the mode geometry are
+    // the padded ones; D_real, I_real are the caller's.
+    bool pad = false;
+    int64_t D_real = 0;
+    int64_t I_last_real = 0;
+    float* Lpad = nullptr;   // output-pass target when padded
     int ncta_ap[PASD_MAXN];
     int n_mp[PASD_MAXN];
     size_t footprint = 0;
@@ -227,13 +236,29 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
         pl->alpha[n] = a;
         asum += a;
     }
+    int64_t dint[PASD_MAXN];
+    for (int n = 0; n < N; ++n) dint[n] = p.dims[n];
+    pl->D_real = D;
+    pl->I_last_real = p.dims[N - 1];
+    if (N <= 4 && p.dims[N - 1] % 4 != 0) {
+        const char* nt0 = std::getenv("PASD_NO_TMA");
+        if (!(nt0 && nt0[0] == '1')) {
+            pl->pad = true;
+            dint[N - 1] = (p.dims[N - 1] + 3) / 4 * 4;
+            pl->D = D / p.dims[N - 1] * dint[N - 1];
+        }
+    }
     for (int n = 0; n < N; ++n) {
         ModeGeom& g = pl->m[n];
-        g.I = p.dims[n];
+        // default lambda_n from the caller's sizes
+        int64_t preR = 1, postR = 1;
+        for (int m = 0; m < n; ++m) preR *= p.dims[m];
+        for (int m = n + 1; m < N; ++m) postR *= p.dims[m];
+        g.I = dint[n];
         g.pre = 1;
-        for (int m = 0; m < n; ++m) g.pre *= p.dims[m];
+        for (int m = 0; m < n; ++m) g.pre *= dint[m];
         g.post = 1;
-        for (int m = n + 1; m < N; ++m) g.post *= p.dims[m];
+        for (int m = n + 1; m < N; ++m) g.post *= dint[m];
         g.P = g.pre * g.post;
         g.R = p.rank_bound[n];
         g.Rp = rank_bucket(g.R);
@@ -241,7 +266,7 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
         if (p.lambda > 0) lam = pl->alpha[n] / p.lambda;
         else if (p.lambda_n[n] > 0) lam = p.lambda_n[n];
         else if (p.lambda_n[n] < 0) { delete pl; return fail(PASD_ERR_INVALID_ARG, "lambda_n must be > 0"); }
-        else lam = std::sqrt((double)std::max<int64_t>(g.I, g.P)) / N;
+        else lam = std::sqrt((double)std::max<int64_t>(p.dims[n], preR * postR)) / N;
         pl->lam[n] = lam;
     }
     pl->p = p;
@@ -344,13 +369,14 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
         pl->mpt_smem = smem;
     }
     int nparts = std::max(pl->fg.nregions, pl->fg_plain.nregions);
-    // footprint
+    // footprint (padded sizes)
+    const int64_t Dp = pl->D;
     size_t f = align256(sizeof(DevScalars));
-    f += align256(D * 4);                                   // T copy
-    f += align256(D * 4);                                   // E
+    f += align256(Dp * 4);                                  // T copy
+    f += align256(Dp * 4);                                  // E
     for (int n = 0; n < N; ++n) {
         const ModeGeom& g = pl->m[n];
-        f += align256(D * 4);                               // G_n
+        f += align256(Dp * 4);                              // G_n
         f += 2 * align256((size_t)g.P * g.Rp * 4);          // A_n, Vrot_n
         f += 2 * align256((size_t)g.I * g.Rp * 4);          // U_n, Urot_n
         f += align256((size_t)g.Rp * g.Rp * 4) + 2 * align256(g.Rp * 4);
@@ -362,6 +388,7 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     f += align256((size_t)nparts * (3 + N) * 4);
     f += align256(1024 * 4) + align256(PASD_MAXN * 4);
     f += align256((size_t)p.max_iter * PASD_TRACE_STRIDE * 8);
+    if (pl->pad) f += align256(Dp * 4);                    // output-pass target
     pl->footprint = f;
     if (footprint_bytes) *footprint_bytes = f;
     const char* ng = std::getenv("PASD_NO_GRAPH");
@@ -435,6 +462,8 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
     pl->sq_part = reinterpret_cast<float*>(take(1024 * 4));
     pl->kept = reinterpret_cast<int32_t*>(take(PASD_MAXN * 4));
     pl->trace = reinterpret_cast<double*>(take((size_t)pl->p.max_iter * PASD_TRACE_STRIDE * 8));
+    if (pl->pad) pl->Lpad = reinterpret_cast<float*>(take(D * 4));
+    // zeros everywhere once: the padded entries of T, E, G_n are never written
     CUDA_TRY(cudaMemset(pl->arena, 0, pl->footprint));
     CUDA_TRY(cudaMallocHost(&pl->host_sc, sizeof(DevScalars)));
     CUDA_TRY(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
@@ -630,7 +659,13 @@ extern "C" pasd_status pasd_begin(pasd_plan_t* pl, const float* T, void* stream)
     if (st != PASD_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int N = pl->N;
-    CUDA_TRY(cudaMemcpyAsync(pl->Tc, T, pl->D * 4, cudaMemcpyDeviceToDevice, s));
+    if (pl->pad) {
+        // caller's rows of I_real floats into rows of the padded length (padding stays zero)
+        const int64_t Ip = pl->m[N - 1].I, Ir = pl->I_last_real;
+        CUDA_TRY(cudaMemcpy2DAsync(pl->Tc, Ip * 4, T, Ir * 4, Ir * 4, pl->D_real / Ir, cudaMemcpyDeviceToDevice, s));
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(pl->Tc, T, pl->D * 4, cudaMemcpyDeviceToDevice, s));
+    }
     CUDA_TRY(cudaMemsetAsync(pl->E, 0, pl->D * 4, s));
     for (int n = 0; n < N; ++n) CUDA_TRY(cudaMemcpyAsync(pl->G[n], pl->Tc, pl->D * 4, cudaMemcpyDeviceToDevice, s));
     int64_t Is[PASD_MAXN];
@@ -687,8 +722,15 @@ extern "C" pasd_status pasd_finish(pasd_plan_t* pl, float* L, float* E, pasd_res
         return fail((pasd_status)r.status, "solve failed: non-finite values in the iterate");
     }
     // output: L = sum_n alpha_n Z_n / sum alpha_n, E (Algorithm 1, Output)
-    launch_fused_pass(pl, 1, L, s);   // the output pass ignores the stop flag
-    CUDA_TRY(cudaMemcpyAsync(E, pl->E, pl->D * 4, cudaMemcpyDeviceToDevice, s));
+    if (pl->pad) {
+        const int64_t Ip = pl->m[pl->N - 1].I, Ir = pl->I_last_real, rows = pl->D_real / Ir;
+        launch_fused_pass(pl, 1, pl->Lpad, s);   // the output pass ignores the stop flag
+        CUDA_TRY(cudaMemcpy2DAsync(L, Ir * 4, pl->Lpad, Ip * 4, Ir * 4, rows, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpy2DAsync(E, Ir * 4, pl->E, Ip * 4, Ir * 4, rows, cudaMemcpyDeviceToDevice, s));
+    } else {
+        launch_fused_pass(pl, 1, L, s);   // the output pass ignores the stop flag
+        CUDA_TRY(cudaMemcpyAsync(E, pl->E, pl->D * 4, cudaMemcpyDeviceToDevice, s));
+    }
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());
     return (pasd_status)r.status;
@@ -736,15 +778,16 @@ extern "C" pasd_status pasd_solve_host(pasd_plan_t* pl, const float* Th, float* 
                                        pasd_result* res, void* stream) {
     if (!pl || !Th || !Lh || !Eh) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    if (!pl->dev_io) CUDA_TRY(cudaMalloc(&pl->dev_io, (size_t)3 * pl->D * 4));
+    const int64_t Dr = pl->D_real;
+    if (!pl->dev_io) CUDA_TRY(cudaMalloc(&pl->dev_io, (size_t)3 * Dr * 4));
     float* Td = pl->dev_io;
-    float* Ld = Td + pl->D;
-    float* Ed = Ld + pl->D;
-    CUDA_TRY(cudaMemcpyAsync(Td, Th, pl->D * 4, cudaMemcpyHostToDevice, s));
+    float* Ld = Td + Dr;
+    float* Ed = Ld + Dr;
+    CUDA_TRY(cudaMemcpyAsync(Td, Th, Dr * 4, cudaMemcpyHostToDevice, s));
     pasd_status st = pasd_solve(pl, Td, Ld, Ed, res, stream);
     if (st != PASD_OK && st != PASD_NOT_CONVERGED) return st;
-    CUDA_TRY(cudaMemcpyAsync(Lh, Ld, pl->D * 4, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(Eh, Ed, pl->D * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(Lh, Ld, Dr * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(Eh, Ed, Dr * 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return st;
 }
@@ -768,13 +811,33 @@ extern "C" pasd_status pasd_state_get(pasd_plan_t* pl, int32_t item, int32_t mod
         return PASD_OK;
     };
     switch (item) {
-        case PASD_STATE_U: return copy2d(pl->U[mode], pl->m[mode].I, pl->m[mode].R, pl->m[mode].Rp);
+        case PASD_STATE_U: {
+            const int64_t rows = (pl->pad && mode == N - 1) ? pl->I_last_real : pl->m[mode].I;
+            return copy2d(pl->U[mode], rows, pl->m[mode].R, pl->m[mode].Rp);
+        }
         case PASD_STATE_W: return copy2d(pl->W[mode], pl->m[mode].R, pl->m[mode].R, pl->m[mode].Rp);
         case PASD_STATE_SIGMA: return copy2d(pl->sigma[mode], 1, pl->m[mode].R, pl->m[mode].Rp);
         case PASD_STATE_F: return copy2d(pl->F[mode], 1, pl->m[mode].R, pl->m[mode].Rp);
         case PASD_STATE_A: {
             // device layout [pre][Rp][post] -> host [R][pre*post] (unfolding column order)
             const ModeGeom& g = pl->m[mode];
+            if (pl->pad && mode < N - 1) {
+                // columns with a padded last-mode index are dropped
+                const int64_t Ip = pl->m[N - 1].I, Ir = pl->I_last_real;
+                const int64_t post_r = g.post / Ip * Ir, P_r = g.pre * post_r;
+                if (bytes != (size_t)g.R * P_r * 4) return fail(PASD_ERR_INVALID_ARG, "size mismatch");
+                std::vector<float> tmp((size_t)g.pre * g.Rp * g.post);
+                CUDA_TRY(cudaMemcpyAsync(tmp.data(), pl->A[mode], tmp.size() * 4, cudaMemcpyDeviceToHost, s));
+                CUDA_TRY(cudaStreamSynchronize(s));
+                float* h = (float*)dst;
+                const int64_t rest = g.post / Ip;
+                for (int r = 0; r < g.R; ++r)
+                    for (int64_t a = 0; a < g.pre; ++a)
+                        for (int64_t b = 0; b < rest; ++b)
+                            std::memcpy(h + (size_t)r * P_r + a * post_r + b * Ir,
+                                        tmp.data() + ((size_t)a * g.Rp + r) * g.post + b * Ip, Ir * 4);
+                return PASD_OK;
+            }
             if (bytes != (size_t)g.R * g.P * 4) return fail(PASD_ERR_INVALID_ARG, "size mismatch");
             float* h = (float*)dst;
             for (int r = 0; r < g.R; ++r) {
@@ -787,16 +850,18 @@ extern "C" pasd_status pasd_state_get(pasd_plan_t* pl, int32_t item, int32_t mod
             return PASD_OK;
         }
         case PASD_STATE_E:
+            if (pl->pad) return copy2d(pl->E, pl->D_real / pl->I_last_real, (int)pl->I_last_real, (int)pl->m[N - 1].I);
             if (bytes != (size_t)pl->D * 4) return fail(PASD_ERR_INVALID_ARG, "size mismatch");
             CUDA_TRY(cudaMemcpyAsync(dst, pl->E, bytes, cudaMemcpyDeviceToHost, s));
             CUDA_TRY(cudaStreamSynchronize(s));
             return PASD_OK;
         case PASD_STATE_Y: {
-            if (bytes != (size_t)pl->D * 4) return fail(PASD_ERR_INVALID_ARG, "size mismatch");
+            if (bytes != (size_t)pl->D_real * 4) return fail(PASD_ERR_INVALID_ARG, "size mismatch");
             if (!pl->y_tmp) CUDA_TRY(cudaMalloc(&pl->y_tmp, pl->D * 4));
             pasd_status st = read_scalars(pl, s);
             if (st != PASD_OK) return st;
             launch_export_y(pl->G[mode], pl->host_sc->T, pl->E, pl->sc, pl->y_tmp, pl->D, s);
+            if (pl->pad) return copy2d(pl->y_tmp, pl->D_real / pl->I_last_real, (int)pl->I_last_real, (int)pl->m[N - 1].I);
             CUDA_TRY(cudaMemcpyAsync(dst, pl->y_tmp, bytes, cudaMemcpyDeviceToHost, s));
             CUDA_TRY(cudaStreamSynchronize(s));
             return PASD_OK;
