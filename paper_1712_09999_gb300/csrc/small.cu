@@ -357,7 +357,7 @@ __host__ __device__ inline int polar_ld(int Rp) { return ((Rp / 4) & 1) ? Rp : R
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int svt_red_floats(int Rp) { return Rp * Rp > 2048 ? Rp * Rp : 2048; }
 
-__global__ void __launch_bounds__(SM_THREADS) svt_kernel(SmallArgs sa) {
+__global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
     DevScalars* sc = sa.sc;
     if (sc->done) return;
     const double mu = sc->mu;
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(SM_THREADS) svt_kernel(SmallArgs sa) {
     float* red = reinterpret_cast<float*>(perm + ld);   // svt_red_floats(Rp)
 
     // 1. Gram matrix = sum over the A-pass CTA partials. Thread (f, g) adds
-    //    float4 f of partials g, g + G, ... (eight loads in flight), then the G
+    //    float4 f of partials g, g + G, ... (sixteen loads in flight), then the G
     //    group sums are added in order; the upper triangle is mirrored, so the
     //    matrix is exactly symmetric.
     {
@@ -384,12 +384,12 @@ __global__ void __launch_bounds__(SM_THREADS) svt_kernel(SmallArgs sa) {
             const int f = w % nf4, g = w / nf4;
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             int p = g;
-            for (; p + 7 * G < m.n_gram; p += 8 * G) {
-                float4 v[8];
+            for (; p + 15 * G < m.n_gram; p += 16 * G) {
+                float4 v[16];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = part[(size_t)(p + u * G) * nf4 + f];
+                for (int u = 0; u < 16; ++u) v[u] = part[(size_t)(p + u * G) * nf4 + f];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
+                for (int u = 0; u < 16; ++u) {
                     acc.x += v[u].x; acc.y += v[u].y; acc.z += v[u].z; acc.w += v[u].w;
                 }
             }
@@ -493,6 +493,29 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
     const int s = *m.kept;
     const int q = R - s;
     const int s4 = (s + 3) & ~3, q4 = (q + 3) & ~3;
+
+    if (s == 0) {
+        // Nothing kept: the polar factor of Urot = U W. U and W are orthogonal to
+        // rounding, so Urot^T Urot = I + O(1e-6) and one Newton-Schulz step gives
+        // the polar factor to O(1e-12), the step the general path also ends with.
+        // Urot's padding columns are zero, so the products run over Rp.
+        tile_AtB(m.Urot, Rp, R, m.Urot, Rp, R, I, K, ld, true, tsc);
+        int far = 0;
+        for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
+            const int i = idx / R, j = idx % R;
+            far |= fabsf(K[i * ld + j] - (i == j ? 1.f : 0.f)) > 1e-3f;
+        }
+        if (!__syncthreads_or(far)) {
+            for (int idx = threadIdx.x; idx < Rp * Rp; idx += blockDim.x) {
+                const int i = idx / Rp, j = idx % Rp;
+                Z[i * ld + j] = (i < R && j < R) ? ((i == j) ? 1.5f : 0.f) - 0.5f * K[i * ld + j] : 0.f;
+            }
+            __syncthreads();
+            tile_AB(m.Urot, Rp, Rp, Z, ld, Rp, I, m.U, Rp, false);
+            return;
+        }
+        // (not near-orthonormal: the general path below)
+    }
 
     if (s > 0) {
         // M in the W basis: G_n Vrot^T, summed over regions by the finalize kernel
