@@ -42,37 +42,37 @@ struct ApLayout {
     static constexpr int gs_stage = rowmajor ? AP_BN * gs_ld : AP_BK * gs_ld;
 };
 
-// Shared memory of the Gram partial reduction (after the A tile [AP_BN][RP + 4]).
-static inline __host__ __device__ int gram_red_floats(int RP) {
+// Shared memory of the Gram partial reduction with NT threads (after the A tile
+// [AP_BN][RP + 4]).
+static inline __host__ __device__ int gram_red_floats(int RP, int NT) {
     const int nb = RP / 4, nbt = nb * (nb + 1) / 2;
-    const int nsl = nbt >= AP_THREADS ? 1 : AP_THREADS / nbt;
+    const int nsl = nbt >= NT ? 1 : NT / nbt;
     return nsl * nbt * 16;
 }
 
-// Per-CTA Gram partial: the sum over this CTA's columns of A[:, j] A[:, j]^T,
-// columns t and t + 128 of the thread in acc0 / acc1 (zero for absent columns).
+// Per-CTA Gram partial: the sum over this CTA's AP_BN columns of A[:, j] A[:, j]^T;
+// thread t holds columns t + NT q (q < CPT) in acc[q] (zero for absent columns).
 // 4 x 4 blocks on and above the diagonal, each summed over NSL column slices
 // and then over the slices in order (deterministic); written with its mirror.
 // `smem` must be free (no copy in flight) and hold AP_BN (RP + 4) +
-// gram_red_floats(RP) floats.
-template <int RP>
-__device__ __forceinline__ void gram_epilogue(const float* acc0, const float* acc1, float* smem, float* gp) {
+// gram_red_floats(RP, NT) floats.
+template <int RP, int NT, int CPT>
+__device__ __forceinline__ void gram_epilogue(const float (&acc)[CPT][RP], float* smem, float* gp) {
     const int t = threadIdx.x;
     constexpr int ALD = RP + 4;
     float* As = smem;   // [AP_BN][ALD]
 #pragma unroll
-    for (int r4 = 0; r4 < RP / 4; ++r4) {
-        *reinterpret_cast<float4*>(As + t * ALD + 4 * r4) =
-            make_float4(acc0[4 * r4], acc0[4 * r4 + 1], acc0[4 * r4 + 2], acc0[4 * r4 + 3]);
-        *reinterpret_cast<float4*>(As + (t + 128) * ALD + 4 * r4) =
-            make_float4(acc1[4 * r4], acc1[4 * r4 + 1], acc1[4 * r4 + 2], acc1[4 * r4 + 3]);
-    }
+    for (int q = 0; q < CPT; ++q)
+#pragma unroll
+        for (int r4 = 0; r4 < RP / 4; ++r4)
+            *reinterpret_cast<float4*>(As + (t + NT * q) * ALD + 4 * r4) =
+                make_float4(acc[q][4 * r4], acc[q][4 * r4 + 1], acc[q][4 * r4 + 2], acc[q][4 * r4 + 3]);
     constexpr int NB = RP / 4;
     constexpr int NBT = NB * (NB + 1) / 2;
-    constexpr int NSL = NBT >= AP_THREADS ? 1 : AP_THREADS / NBT;
+    constexpr int NSL = NBT >= NT ? 1 : NT / NBT;
     float* red = smem + AP_BN * ALD;
     __syncthreads();
-    for (int w = t; w < NBT * NSL; w += AP_THREADS) {
+    for (int w = t; w < NBT * NSL; w += NT) {
         int blk = w % NBT, sl = w / NBT;
         int bi = 0, rem = blk;
         while (rem >= NB - bi) { rem -= NB - bi; ++bi; }
@@ -93,7 +93,7 @@ __device__ __forceinline__ void gram_epilogue(const float* acc0, const float* ac
         for (int q = 0; q < 16; ++q) red[(sl * NBT + blk) * 16 + q] = g[q];
     }
     __syncthreads();
-    for (int o = t; o < NBT * 16; o += AP_THREADS) {
+    for (int o = t; o < NBT * 16; o += NT) {
         int blk = o / 16, q = o % 16;
         float sum = 0.f;
         for (int sl = 0; sl < NSL; ++sl) sum += red[(sl * NBT + blk) * 16 + q];
@@ -110,7 +110,7 @@ size_t apass_smem_bytes(int Rp, bool rowmajor) {
     size_t gs = (size_t)AP_STAGES * (rowmajor ? AP_BN * (AP_BK + 4) : AP_BK * (AP_BN + 4));
     size_t us = (size_t)AP_STAGES * AP_BK * Rp;
     size_t pipe = gs + us;
-    size_t epi = (size_t)AP_BN * (Rp + 4) + gram_red_floats(Rp);
+    size_t epi = (size_t)AP_BN * (Rp + 4) + gram_red_floats(Rp, AP_THREADS);
     return 4 * (pipe > epi ? pipe : epi);
 }
 
@@ -201,7 +201,9 @@ __device__ __forceinline__ void apass_body(const ApassArgs& a, int cta, float* s
         }
     };
 
-    float acc0[RP], acc1[RP];
+    float acc[2][RP];
+    float* acc0 = acc[0];
+    float* acc1 = acc[1];
 #pragma unroll
     for (int r = 0; r < RP; ++r) { acc0[r] = 0.f; acc1[r] = 0.f; }
 
@@ -290,7 +292,7 @@ __device__ __forceinline__ void apass_body(const ApassArgs& a, int cta, float* s
         }
     }
 
-    gram_epilogue<RP>(acc0, acc1, smem, a.gram_part + (size_t)cta * RP * RP);
+    gram_epilogue<RP, AP_THREADS, 2>(acc, smem, a.gram_part + (size_t)cta * RP * RP);
 }
 
 static int apass_variant(const ApassArgs& a) {
@@ -402,8 +404,14 @@ static inline __host__ __device__ int at_stage_floats(int BN, int RP) {
     return (AP_BK * BN + AP_BK * RP + 127) / 128 * 128;
 }
 
+// Columns per thread: four while the 4 x RP accumulators fit in registers, two beyond.
+template <int RP> struct AtShape {
+    static constexpr int COLS = RP <= 40 ? 4 : 2;
+    static constexpr int THREADS = AP_BN / COLS;
+};
+
 template <int RP>
-__global__ void __launch_bounds__(AP_THREADS) apass_tma_kernel(const __grid_constant__ ApassTmaMaps maps,
+__global__ void __launch_bounds__(AtShape<RP>::THREADS) apass_tma_kernel(const __grid_constant__ ApassTmaMaps maps,
                                                                const ApassTmaArgs aa) {
     extern __shared__ __align__(16) float sm_raw[];
     float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 511) & ~uintptr_t(511));
@@ -412,6 +420,7 @@ __global__ void __launch_bounds__(AP_THREADS) apass_tma_kernel(const __grid_cons
     while (k + 1 < aa.count && (int)blockIdx.x >= aa.cta_start[k + 1]) ++k;
     const ApassTmaMode& m = aa.m[k];
     DevScalars* sc = aa.sc;
+    constexpr int NT = AtShape<RP>::THREADS, NC = AtShape<RP>::COLS;
     if (sc->done) return;
     const int task = blockIdx.x - aa.cta_start[k];
     const int t = threadIdx.x;
@@ -455,9 +464,13 @@ __global__ void __launch_bounds__(AP_THREADS) apass_tma_kernel(const __grid_cons
     if (t == 0)
         for (int s2 = 0; s2 < AT_STAGES - 1 && s2 < nk; ++s2) issue(s2);
 
-    float acc0[RP], acc1[RP];
+    // thread t: columns t + NT q of the task (q < NC); several columns per
+    // thread amortise each broadcast read of a U row over NC x RP multiply-adds
+    float acc[NC][RP];
 #pragma unroll
-    for (int r = 0; r < RP; ++r) { acc0[r] = 0.f; acc1[r] = 0.f; }
+    for (int q = 0; q < NC; ++q)
+#pragma unroll
+        for (int r = 0; r < RP; ++r) acc[q][r] = 0.f;
     bool failed = false;
     for (int kc = 0; kc < nk; ++kc) {
         const int st = kc % AT_STAGES;
@@ -469,50 +482,50 @@ __global__ void __launch_bounds__(AP_THREADS) apass_tma_kernel(const __grid_cons
         const float* gs = smem + st * sst;
         const float* us = gs + gfl;
         if (!m.rowmajor) {
-            const int c1 = t + 128 < BN ? t + 128 : t;    // a column past the task is never stored
-#pragma unroll 4
+            int col[NC];     // a column past the task reads a valid one and is never stored
+#pragma unroll
+            for (int q = 0; q < NC; ++q) col[q] = t + NT * q < BN ? t + NT * q : t;
+#pragma unroll 2
             for (int kk = 0; kk < AP_BK; ++kk) {
-                const float g0 = gs[kk * BN + t];
-                const float g1 = gs[kk * BN + c1];
+                float g[NC];
+#pragma unroll
+                for (int q = 0; q < NC; ++q) g[q] = gs[kk * BN + col[q]];
                 const float4* u4 = reinterpret_cast<const float4*>(us + kk * RP);
 #pragma unroll
                 for (int r4 = 0; r4 < RP / 4; ++r4) {
                     const float4 u = u4[r4];
-                    acc0[4 * r4 + 0] = fmaf(g0, u.x, acc0[4 * r4 + 0]);
-                    acc0[4 * r4 + 1] = fmaf(g0, u.y, acc0[4 * r4 + 1]);
-                    acc0[4 * r4 + 2] = fmaf(g0, u.z, acc0[4 * r4 + 2]);
-                    acc0[4 * r4 + 3] = fmaf(g0, u.w, acc0[4 * r4 + 3]);
-                    acc1[4 * r4 + 0] = fmaf(g1, u.x, acc1[4 * r4 + 0]);
-                    acc1[4 * r4 + 1] = fmaf(g1, u.y, acc1[4 * r4 + 1]);
-                    acc1[4 * r4 + 2] = fmaf(g1, u.z, acc1[4 * r4 + 2]);
-                    acc1[4 * r4 + 3] = fmaf(g1, u.w, acc1[4 * r4 + 3]);
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) {
+                        acc[q][4 * r4 + 0] = fmaf(g[q], u.x, acc[q][4 * r4 + 0]);
+                        acc[q][4 * r4 + 1] = fmaf(g[q], u.y, acc[q][4 * r4 + 1]);
+                        acc[q][4 * r4 + 2] = fmaf(g[q], u.z, acc[q][4 * r4 + 2]);
+                        acc[q][4 * r4 + 3] = fmaf(g[q], u.w, acc[q][4 * r4 + 3]);
+                    }
                 }
             }
         } else {
-            const int sw = (t >> 1) & 3;    // the same for columns t and t + 128
-            const float* r0 = gs + t * AP_BK;
-            const float* r1 = gs + (t + 128) * AP_BK;
+            const int sw = (t >> 1) & 3;    // the same for every column t + NT q (NT even)
 #pragma unroll
             for (int k4 = 0; k4 < AP_BK / 4; ++k4) {
-                const float4 g0v = *reinterpret_cast<const float4*>(r0 + 4 * (k4 ^ sw));
-                const float4 g1v = *reinterpret_cast<const float4*>(r1 + 4 * (k4 ^ sw));
-                const float g0s[4] = {g0v.x, g0v.y, g0v.z, g0v.w};
-                const float g1s[4] = {g1v.x, g1v.y, g1v.z, g1v.w};
+                float gq[NC][4];
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    const float4 v = *reinterpret_cast<const float4*>(gs + (t + NT * q) * AP_BK + 4 * (k4 ^ sw));
+                    gq[q][0] = v.x; gq[q][1] = v.y; gq[q][2] = v.z; gq[q][3] = v.w;
+                }
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const float4* u4 = reinterpret_cast<const float4*>(us + (4 * k4 + kk) * RP);
-                    const float g0 = g0s[kk], g1 = g1s[kk];
 #pragma unroll
                     for (int r4 = 0; r4 < RP / 4; ++r4) {
                         const float4 u = u4[r4];
-                        acc0[4 * r4 + 0] = fmaf(g0, u.x, acc0[4 * r4 + 0]);
-                        acc0[4 * r4 + 1] = fmaf(g0, u.y, acc0[4 * r4 + 1]);
-                        acc0[4 * r4 + 2] = fmaf(g0, u.z, acc0[4 * r4 + 2]);
-                        acc0[4 * r4 + 3] = fmaf(g0, u.w, acc0[4 * r4 + 3]);
-                        acc1[4 * r4 + 0] = fmaf(g1, u.x, acc1[4 * r4 + 0]);
-                        acc1[4 * r4 + 1] = fmaf(g1, u.y, acc1[4 * r4 + 1]);
-                        acc1[4 * r4 + 2] = fmaf(g1, u.z, acc1[4 * r4 + 2]);
-                        acc1[4 * r4 + 3] = fmaf(g1, u.w, acc1[4 * r4 + 3]);
+#pragma unroll
+                        for (int q = 0; q < NC; ++q) {
+                            acc[q][4 * r4 + 0] = fmaf(gq[q][kk], u.x, acc[q][4 * r4 + 0]);
+                            acc[q][4 * r4 + 1] = fmaf(gq[q][kk], u.y, acc[q][4 * r4 + 1]);
+                            acc[q][4 * r4 + 2] = fmaf(gq[q][kk], u.z, acc[q][4 * r4 + 2]);
+                            acc[q][4 * r4 + 3] = fmaf(gq[q][kk], u.w, acc[q][4 * r4 + 3]);
+                        }
                     }
                 }
             }
@@ -532,37 +545,35 @@ __global__ void __launch_bounds__(AP_THREADS) apass_tma_kernel(const __grid_cons
     __syncthreads();   // every stage consumed and no copy in flight: smem is free for the epilogue
 
     // columns past the task carry no data: zero them for the Gram sums
-    const bool v0 = t < ncol, v1 = t + 128 < ncol;
 #pragma unroll
-    for (int r = 0; r < RP; ++r) {
-        if (!v0) acc0[r] = 0.f;
-        if (!v1) acc1[r] = 0.f;
-    }
+    for (int q = 0; q < NC; ++q)
+        if (t + NT * q >= ncol)
+#pragma unroll
+            for (int r = 0; r < RP; ++r) acc[q][r] = 0.f;
     // ---- store A (layout [pre][Rp][post]) ----
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const float* acc = h ? acc1 : acc0;
-        const int c = t + 128 * h;
+    for (int q = 0; q < NC; ++q) {
+        const int c = t + NT * q;
         if (c < ncol) {
             if (m.rowmajor) {
                 float4* dst = reinterpret_cast<float4*>(m.A + (a0 + c) * RP);
 #pragma unroll
                 for (int r4 = 0; r4 < RP / 4; ++r4)
-                    dst[r4] = make_float4(acc[4 * r4], acc[4 * r4 + 1], acc[4 * r4 + 2], acc[4 * r4 + 3]);
+                    dst[r4] = make_float4(acc[q][4 * r4], acc[q][4 * r4 + 1], acc[q][4 * r4 + 2], acc[q][4 * r4 + 3]);
             } else {
                 float* dst = m.A + a0 * RP * post + b0 + c;
 #pragma unroll
-                for (int r = 0; r < RP; ++r) dst[(int64_t)r * post] = acc[r];
+                for (int r = 0; r < RP; ++r) dst[(int64_t)r * post] = acc[q][r];
             }
         }
     }
-    gram_epilogue<RP>(acc0, acc1, smem, m.gram_part + (size_t)task * RP * RP);
+    gram_epilogue<RP, NT, NC>(acc, smem, m.gram_part + (size_t)task * RP * RP);
 }
 
 template <int RP>
 static void launch_tma_rp(const ApassTmaPlan& p, cudaStream_t s) {
     cudaFuncSetAttribute(apass_tma_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-    apass_tma_kernel<RP><<<p.args.cta_start[p.args.count], AP_THREADS, p.smem, s>>>(p.maps, p.args);
+    apass_tma_kernel<RP><<<p.args.cta_start[p.args.count], AtShape<RP>::THREADS, p.smem, s>>>(p.maps, p.args);
 }
 
 void launch_apass_tma(const ApassTmaPlan* p, cudaStream_t s) {
@@ -634,7 +645,7 @@ ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, ch
         }
         if (!ok) { delete p; return nullptr; }
         const size_t pipe = (size_t)AT_STAGES * at_stage_floats(mm.BN, Rp);
-        const size_t epi = (size_t)AP_BN * (Rp + 4) + gram_red_floats(Rp);
+        const size_t epi = (size_t)AP_BN * (Rp + 4) + gram_red_floats(Rp, Rp <= 40 ? AP_BN / 4 : AP_BN / 2);
         smem = std::max(smem, 4 * std::max(pipe, epi) + 512);
     }
     p->args.cta_start[count] = start;
