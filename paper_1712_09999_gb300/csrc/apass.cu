@@ -12,6 +12,7 @@
 // is broadcast from shared memory. Columns past P and rows past I are zero-filled
 // by the copy, so they contribute nothing to A or to the Gram sums.
 #include "pasd_impl.cuh"
+#include "tc.cuh"
 #include "tma.cuh"
 
 #include <algorithm>
@@ -44,23 +45,30 @@ struct ApLayout {
 
 // Shared memory of the Gram partial reduction with NT threads (after the A tile
 // [AP_BN][RP + 4]).
-static inline __host__ __device__ int gram_red_floats(int RP, int NT) {
+static constexpr inline __host__ __device__ int gram_red_floats(int RP, int NT) {
     const int nb = RP / 4, nbt = nb * (nb + 1) / 2;
     const int nsl = nbt >= NT ? 1 : NT / nbt;
     return nsl * nbt * 16;
 }
 
-// Per-CTA Gram partial: the sum over this CTA's AP_BN columns of A[:, j] A[:, j]^T;
+// Per-CTA Gram partial: the sum over this CTA's BN columns of A[:, j] A[:, j]^T;
 // thread t holds columns t + NT q (q < CPT) in acc[q] (zero for absent columns).
 // 4 x 4 blocks on and above the diagonal, each summed over NSL column slices
 // and then over the slices in order (deterministic); written with its mirror.
-// `smem` must be free (no copy in flight) and hold AP_BN (RP + 4) +
+// `smem` must be free (no copy in flight) and hold BN (RP + 4) +
 // gram_red_floats(RP, NT) floats.
-template <int RP, int NT, int CPT>
-__device__ __forceinline__ void gram_epilogue(const float (&acc)[CPT][RP], float* smem, float* gp) {
-    const int t = threadIdx.x;
+// BAR = 0 synchronises the whole CTA; BAR > 0 only the NT threads that run the
+// epilogue (named barrier BAR), whose index among them is t.
+template <int BAR, int NT>
+__device__ __forceinline__ void epi_sync() {
+    if (BAR == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;\n" ::"n"(BAR), "n"(NT) : "memory");
+}
+template <int RP, int NT, int CPT, int BN = AP_BN, int BAR = 0>
+__device__ __forceinline__ void gram_epilogue(const float (&acc)[CPT][RP], float* smem, float* gp,
+                                              int t = threadIdx.x) {
     constexpr int ALD = RP + 4;
-    float* As = smem;   // [AP_BN][ALD]
+    float* As = smem;   // [BN][ALD]
 #pragma unroll
     for (int q = 0; q < CPT; ++q)
 #pragma unroll
@@ -70,8 +78,8 @@ __device__ __forceinline__ void gram_epilogue(const float (&acc)[CPT][RP], float
     constexpr int NB = RP / 4;
     constexpr int NBT = NB * (NB + 1) / 2;
     constexpr int NSL = NBT >= NT ? 1 : NT / NBT;
-    float* red = smem + AP_BN * ALD;
-    __syncthreads();
+    float* red = smem + BN * ALD;
+    epi_sync<BAR, NT>();
     for (int w = t; w < NBT * NSL; w += NT) {
         int blk = w % NBT, sl = w / NBT;
         int bi = 0, rem = blk;
@@ -80,7 +88,7 @@ __device__ __forceinline__ void gram_epilogue(const float (&acc)[CPT][RP], float
         float g[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) g[q] = 0.f;
-        for (int c = sl; c < AP_BN; c += NSL) {
+        for (int c = sl; c < BN; c += NSL) {
             float4 x = *reinterpret_cast<const float4*>(As + c * ALD + 4 * bi);
             float4 y = *reinterpret_cast<const float4*>(As + c * ALD + 4 * bj);
             float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
@@ -92,7 +100,7 @@ __device__ __forceinline__ void gram_epilogue(const float (&acc)[CPT][RP], float
 #pragma unroll
         for (int q = 0; q < 16; ++q) red[(sl * NBT + blk) * 16 + q] = g[q];
     }
-    __syncthreads();
+    epi_sync<BAR, NT>();
     for (int o = t; o < NBT * 16; o += NT) {
         int blk = o / 16, q = o % 16;
         float sum = 0.f;
@@ -396,6 +404,8 @@ struct ApassTmaPlan {
     ApassTmaMaps maps;
     ApassTmaArgs args;
     size_t smem;
+    int kind;      // ApassKind
+    int grid;      // persistent grid of the tensor-core kernel (one CTA per SM)
 };
 
 // Stage stride in floats: 512-byte multiples, the period of the 64-byte swizzle,
@@ -570,13 +580,368 @@ __global__ void __launch_bounds__(AtShape<RP>::THREADS) apass_tma_kernel(const _
     gram_epilogue<RP, NT, NC>(acc, smem, m.gram_part + (size_t)task * RP * RP);
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core A-pass (tcgen05, kind::tf32, accumulators in tensor memory),
+// persistent and warp-specialised.
+// A task is TC_BN = 128 consecutive unfolding columns; the MMA forms the
+// transposed product A^T[col][r] = sum_i G[i][col] U[i][r] with M = 128
+// (columns, one tensor-memory lane each), N = Rp rounded up to 16, and K = I
+// streamed in stages of 16 rows. Both operands must be K-major (i contiguous),
+// so every stage is rewritten into that layout in shared memory:
+//   post > 1 : the copy lands [k][col]; each converter thread transposes a column
+//   post == 1: the copy lands [col][k] with the 64-byte swizzle (operand layout)
+// and U's [k][r] rows likewise become [r][k].
+// TF32 keeps the top 19 bits of each FP32 operand (the MMA ignores the rest),
+// so x = hi + lo with hi and lo rounded to TF32 (x = hi + lo up to 2^-24 |x|),
+// and all four products are formed as two MMAs per step: G_hi and then G_lo
+// against [U_hi; U_lo] stacked along N, so the first half of the accumulator
+// collects g_hi u_hi + g_lo u_hi and the second half g_hi u_lo + g_lo u_lo;
+// the halves are added in the epilogue. Each product is then good to about
+// 2^-23 relative, the accuracy of FP32 multiply-adds. (A single TF32 product
+// per term leaves the Gram eigenvalues of the discarded directions too noisy
+// for the SVT threshold, so no cheaper form is offered.)
+// Roles (one CTA per SM, looping over tasks):
+//   warp 0      : bulk tensor copies of G and U into TP_RAW raw stages
+//   warp 1      : tensor-memory owner and MMA issuer (one thread)
+//   warps 2..9  : converters, raw stage -> one of NOPS operand buffers (a
+//                 thread takes 8 rows of one column; the conversion is latency-
+//                 bound, so it gets most of the warps)
+//   warps 10..13: epilogue, accumulator -> A and the Gram partial, while the
+//                 MMAs of the next task fill the other accumulator
+// Hand-offs are mbarriers; every wait is bounded and a timeout stops all roles.
+// ---------------------------------------------------------------------------
+constexpr int TC_BN = 128;
+constexpr int TC_BK = 16;
+constexpr int TP_RAW = 6;
+constexpr int TP_MAX_OPS = 6;
+constexpr int TP_THREADS = 448;
+constexpr int TP_CONV_WARPS = 8;
+
+template <int RP>
+struct TcShape {
+    static constexpr int NP = (RP + 15) / 16 * 16;            // N of the U_hi block
+    static constexpr int NB = 2 * NP;                          // rows of [U_hi; U_lo]
+    static constexpr int TMEM_COLS = 2 * NB <= 64 ? 64 : 2 * NB <= 128 ? 128 : 256;   // two accumulators
+    static constexpr int RAWG = TC_BN * TC_BK * 4;             // bytes of a raw G box
+    static constexpr int RAWU = (TC_BK * RP * 4 + 1023) / 1024 * 1024;
+    static constexpr int RAW_STRIDE = RAWG + RAWU;
+    static constexpr int GHI = 0;
+    static constexpr int GLO = RAWG;
+    static constexpr int UB = 2 * RAWG;
+    static constexpr int OP_STRIDE = UB + (NB * 64 + 1023) / 1024 * 1024;
+    static constexpr int EPI_BYTES = 4 * (TC_BN * (RP + 4) + gram_red_floats(RP, 128));
+    static constexpr int OPS = TP_RAW * RAW_STRIDE;
+    // operand buffers: as many as fit (up to TP_MAX_OPS); more buffers hide the
+    // completion latency of each stage's MMAs from the converters
+    static constexpr int NOPS_FIT = (226 * 1024 - 1024 - OPS - EPI_BYTES) / OP_STRIDE;
+    static constexpr int NOPS = NOPS_FIT < TP_MAX_OPS ? NOPS_FIT : TP_MAX_OPS;
+    static constexpr int EPI = OPS + NOPS * OP_STRIDE;
+    static constexpr int SMEM = EPI + EPI_BYTES;
+    static_assert(NOPS >= 2, "A-pass tensor-core stages do not fit shared memory");
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Column range, a-row and contraction length of global task `gt`.
+struct TcTask {
+    int k;            // mode slot
+    int64_t a0, b0;
+    int ncol, nk;
+};
+__device__ __forceinline__ TcTask tc_task(const ApassTmaArgs& aa, int gt) {
+    TcTask r;
+    int k = 0;
+    while (k + 1 < aa.count && gt >= aa.cta_start[k + 1]) ++k;
+    const ApassTmaMode& m = aa.m[k];
+    const int task = gt - aa.cta_start[k];
+    r.k = k;
+    if (!m.rowmajor) {
+        r.a0 = task / m.nbb;
+        r.b0 = (int64_t)(task % m.nbb) * TC_BN;
+        r.ncol = (int)((m.post - r.b0) < TC_BN ? (m.post - r.b0) : TC_BN);
+    } else {
+        r.a0 = (int64_t)task * TC_BN;
+        r.b0 = 0;
+        r.ncol = (int)((m.pre - r.a0) < TC_BN ? (m.pre - r.a0) : TC_BN);
+    }
+    r.nk = (int)((m.I + TC_BK - 1) / TC_BK);
+    return r;
+}
+
+template <int RP>
+__global__ void __launch_bounds__(TP_THREADS, 1) apass_tc_kernel(const __grid_constant__ ApassTmaMaps maps,
+                                                                const ApassTmaArgs aa) {
+    using S = TcShape<RP>;
+    extern __shared__ __align__(1024) unsigned char tc_sm_raw[];
+    unsigned char* sm =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_sm_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t raw_full[TP_RAW], raw_empty[TP_RAW];
+    __shared__ __align__(8) uint64_t op_full[TP_MAX_OPS], op_empty[TP_MAX_OPS];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+    DevScalars* sc = aa.sc;
+    if (sc->done) return;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int ntask = aa.cta_start[aa.count];
+
+    if (warp == 1) tmem_alloc(&tmem_base, S::TMEM_COLS);
+    if (t == 0) {
+        for (int i = 0; i < TP_RAW; ++i) { mbar_init(&raw_full[i], 1); mbar_init(&raw_empty[i], TP_CONV_WARPS); }
+        for (int i = 0; i < S::NOPS; ++i) { mbar_init(&op_full[i], TP_CONV_WARPS); mbar_init(&op_empty[i], 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], 128); }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = tmem_base;
+    auto give_up = [&]() {
+        abort_flag = 1;
+        sc->status = -5;   // PASD_ERR_TIMEOUT
+        sc->done = 1;
+        __threadfence();
+    };
+    auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+        for (uint32_t i = 0; i < kWaitPolls; ++i) {
+            if (mbar_try_wait(bar, parity)) return true;
+            if ((i & 255) == 255 && abort_flag) return false;
+        }
+        give_up();
+        return false;
+    };
+
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            const uint32_t tx = (uint32_t)(S::RAWG + TC_BK * RP * 4);
+            int n = 0;
+            for (int gt = blockIdx.x; gt < ntask && !abort_flag; gt += gridDim.x) {
+                const TcTask tk = tc_task(aa, gt);
+                for (int kc = 0; kc < tk.nk; ++kc, ++n) {
+                    const int s = n % TP_RAW;
+                    if (!wait(&raw_empty[s], (uint32_t)(((n / TP_RAW) & 1) ^ 1))) break;
+                    unsigned char* raw = sm + s * S::RAW_STRIDE;
+                    mbar_expect_tx(&raw_full[s], tx);
+                    if (!aa.m[tk.k].rowmajor) {
+                        const int c[3] = {(int)tk.b0, kc * TC_BK, (int)tk.a0};
+                        tma_load<3>(raw, &maps.g[tk.k], &raw_full[s], c);
+                    } else {
+                        const int c[2] = {kc * TC_BK, (int)tk.a0};
+                        tma_load<2>(raw, &maps.g[tk.k], &raw_full[s], c);
+                    }
+                    const int cu[2] = {0, kc * TC_BK};
+                    tma_load<2>(raw + S::RAWG, &maps.u[tk.k], &raw_full[s], cu);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            int n = 0, j = 0;
+            for (int gt = blockIdx.x; gt < ntask && !abort_flag; gt += gridDim.x, ++j) {
+                const TcTask tk = tc_task(aa, gt);
+                const int a = j & 1;
+                if (!wait(&acc_empty[a], (uint32_t)(((j >> 1) & 1) ^ 1))) break;
+                const uint32_t dt = tm + (uint32_t)(a * S::NB);
+                bool ok = true;
+                for (int kc = 0; kc < tk.nk; ++kc, ++n) {
+                    const int o = n % S::NOPS;
+                    if (!wait(&op_full[o], (uint32_t)((n / S::NOPS) & 1))) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t ob = smem_u32(sm + S::OPS + o * S::OP_STRIDE);
+#pragma unroll
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const uint64_t bd = tc_desc_sw64(ob + S::UB + 32 * jj);
+                        tc_mma_tf32(dt, tc_desc_sw64(ob + S::GHI + 32 * jj), bd, tc_idesc_tf32(128, S::NB),
+                                    (kc > 0 || jj > 0) ? 1u : 0u);
+                        tc_mma_tf32(dt, tc_desc_sw64(ob + S::GLO + 32 * jj), bd, tc_idesc_tf32(128, S::NB), 1u);
+                    }
+                    tc_commit(&op_empty[o]);    // operand buffer o may be refilled once these MMAs are done
+                }
+                if (!ok) break;
+                tc_commit(&acc_full[a]);        // accumulator a complete
+            }
+        }
+    } else if (warp < 2 + TP_CONV_WARPS) {
+        // ---------------- converters ----------------
+        const int ct = t - 64;                  // 0 .. 255
+        const int c = ct & (TC_BN - 1);         // column of the task
+        const int kh = ct >> 7;                 // rows 8 kh .. 8 kh + 7 of the stage
+        const int sw = (c >> 1) & 3;
+        int n = 0;
+        for (int gt = blockIdx.x; gt < ntask && !abort_flag; gt += gridDim.x) {
+            const TcTask tk = tc_task(aa, gt);
+            const bool rowmajor = aa.m[tk.k].rowmajor;
+            bool ok = true;
+            for (int kc = 0; kc < tk.nk; ++kc, ++n) {
+                const int s = n % TP_RAW, o = n % S::NOPS;
+                if (!wait(&raw_full[s], (uint32_t)((n / TP_RAW) & 1))) { ok = false; break; }
+                if (!wait(&op_empty[o], (uint32_t)(((n / S::NOPS) & 1) ^ 1))) { ok = false; break; }
+                const unsigned char* raw = sm + s * S::RAW_STRIDE;
+                unsigned char* op = sm + S::OPS + o * S::OP_STRIDE;
+                const float* rg = reinterpret_cast<const float*>(raw);
+                float* ghi = reinterpret_cast<float*>(op + S::GHI);
+                float* glo = reinterpret_cast<float*>(op + S::GLO);
+#pragma unroll
+                for (int kq = 0; kq < 2; ++kq) {
+                    const int k4 = 2 * kh + kq;
+                    const int off = c * 16 + ((k4 ^ sw) << 2);
+                    float4 v;
+                    if (!rowmajor) {
+                        v.x = rg[(4 * k4 + 0) * TC_BN + c];
+                        v.y = rg[(4 * k4 + 1) * TC_BN + c];
+                        v.z = rg[(4 * k4 + 2) * TC_BN + c];
+                        v.w = rg[(4 * k4 + 3) * TC_BN + c];
+                    } else {
+                        v = *reinterpret_cast<const float4*>(rg + off);
+                    }
+                    float4 h, l;
+                    tf32_split(v.x, h.x, l.x);
+                    tf32_split(v.y, h.y, l.y);
+                    tf32_split(v.z, h.z, l.z);
+                    tf32_split(v.w, h.w, l.w);
+                    *reinterpret_cast<float4*>(ghi + off) = h;
+                    *reinterpret_cast<float4*>(glo + off) = l;
+                }
+                const float* ru = reinterpret_cast<const float*>(raw + S::RAWG);
+                float* ub = reinterpret_cast<float*>(op + S::UB);
+                for (int u = ct; u < S::NP * 4; u += 32 * TP_CONV_WARPS) {
+                    const int r = u % S::NP, k4 = u / S::NP;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (r < RP) {
+                        v.x = ru[(4 * k4 + 0) * RP + r];
+                        v.y = ru[(4 * k4 + 1) * RP + r];
+                        v.z = ru[(4 * k4 + 2) * RP + r];
+                        v.w = ru[(4 * k4 + 3) * RP + r];
+                    }
+                    float4 h, l;
+                    tf32_split(v.x, h.x, l.x);
+                    tf32_split(v.y, h.y, l.y);
+                    tf32_split(v.z, h.z, l.z);
+                    tf32_split(v.w, h.w, l.w);
+                    const int rl = S::NP + r;
+                    *reinterpret_cast<float4*>(ub + r * 16 + ((k4 ^ ((r >> 1) & 3)) << 2)) = h;
+                    *reinterpret_cast<float4*>(ub + rl * 16 + ((k4 ^ ((rl >> 1) & 3)) << 2)) = l;
+                }
+                fence_proxy_async_smem();      // operand writes visible to the tensor cores
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&raw_empty[s]);    // raw stage s read (this warp's part)
+                    mbar_arrive(&op_full[o]);      // operand buffer o written (this warp's part)
+                }
+            }
+            if (!ok) break;
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3;                 // tensor-memory lane quarter of this warp
+        const int c = 32 * q + lane;            // column of the task
+        float* epi = reinterpret_cast<float*>(sm + S::EPI);
+        int j = 0;
+        for (int gt = blockIdx.x; gt < ntask && !abort_flag; gt += gridDim.x, ++j) {
+            const TcTask tk = tc_task(aa, gt);
+            const ApassTmaMode& m = aa.m[tk.k];
+            const int a = j & 1;
+            if (!wait(&acc_full[a], (uint32_t)((j >> 1) & 1))) break;
+            tc_fence_after();
+            float acc[1][RP];
+            {
+                const uint32_t la = tm + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * S::NB);
+                float v[16];
+#pragma unroll
+                for (int c16 = 0; c16 < S::NP / 16; ++c16) {
+                    tmem_ld16(la + 16 * c16, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (16 * c16 + i < RP) acc[0][16 * c16 + i] = v[i];
+                }
+#pragma unroll
+                for (int c16 = 0; c16 < S::NP / 16; ++c16) {
+                    tmem_ld16(la + S::NP + 16 * c16, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (16 * c16 + i < RP) acc[0][16 * c16 + i] += v[i];
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[a]);         // accumulator a may be overwritten
+            if (c >= tk.ncol)
+#pragma unroll
+                for (int r = 0; r < RP; ++r) acc[0][r] = 0.f;
+            else if (m.rowmajor) {
+                float4* dst = reinterpret_cast<float4*>(m.A + (tk.a0 + c) * RP);
+#pragma unroll
+                for (int r4 = 0; r4 < RP / 4; ++r4)
+                    dst[r4] = make_float4(acc[0][4 * r4], acc[0][4 * r4 + 1], acc[0][4 * r4 + 2], acc[0][4 * r4 + 3]);
+            } else {
+                float* dst = m.A + tk.a0 * RP * m.post + tk.b0 + c;
+#pragma unroll
+                for (int r = 0; r < RP; ++r) dst[(int64_t)r * m.post] = acc[0][r];
+            }
+            const int task = gt - aa.cta_start[tk.k];
+            gram_epilogue<RP, 128, 1, TC_BN, 1>(acc, epi, m.gram_part + (size_t)task * RP * RP, c);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tm, S::TMEM_COLS);
+}
+
 template <int RP>
 static void launch_tma_rp(const ApassTmaPlan& p, cudaStream_t s) {
     cudaFuncSetAttribute(apass_tma_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     apass_tma_kernel<RP><<<p.args.cta_start[p.args.count], AtShape<RP>::THREADS, p.smem, s>>>(p.maps, p.args);
 }
 
+template <int RP>
+static void launch_tc_rp(const ApassTmaPlan& p, cudaStream_t s) {
+    cudaFuncSetAttribute(apass_tc_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    const int ntask = p.args.cta_start[p.args.count];
+    const int grid = ntask < p.grid ? ntask : p.grid;
+    apass_tc_kernel<RP><<<grid, TP_THREADS, p.smem, s>>>(p.maps, p.args);
+}
+
+static void launch_tc(const ApassTmaPlan& p, cudaStream_t s) {
+    switch (p.args.Rp) {
+        case 4: launch_tc_rp<4>(p, s); break;
+        case 8: launch_tc_rp<8>(p, s); break;
+        case 12: launch_tc_rp<12>(p, s); break;
+        case 16: launch_tc_rp<16>(p, s); break;
+        case 20: launch_tc_rp<20>(p, s); break;
+        case 24: launch_tc_rp<24>(p, s); break;
+        case 28: launch_tc_rp<28>(p, s); break;
+        case 32: launch_tc_rp<32>(p, s); break;
+        case 40: launch_tc_rp<40>(p, s); break;
+        case 48: launch_tc_rp<48>(p, s); break;
+        case 56: launch_tc_rp<56>(p, s); break;
+        case 64: launch_tc_rp<64>(p, s); break;
+        default: break;
+    }
+}
+
+static size_t tc_smem(int Rp) {
+    switch (Rp) {
+        case 4: return TcShape<4>::SMEM;
+        case 8: return TcShape<8>::SMEM;
+        case 12: return TcShape<12>::SMEM;
+        case 16: return TcShape<16>::SMEM;
+        case 20: return TcShape<20>::SMEM;
+        case 24: return TcShape<24>::SMEM;
+        case 28: return TcShape<28>::SMEM;
+        case 32: return TcShape<32>::SMEM;
+        case 40: return TcShape<40>::SMEM;
+        case 48: return TcShape<48>::SMEM;
+        case 56: return TcShape<56>::SMEM;
+        default: return TcShape<64>::SMEM;
+    }
+}
+
 void launch_apass_tma(const ApassTmaPlan* p, cudaStream_t s) {
+    if (p->kind == APASS_TC) { launch_tc(*p, s); return; }
     switch (p->args.Rp) {
         case 4: launch_tma_rp<4>(*p, s); break;
         case 8: launch_tma_rp<8>(*p, s); break;
@@ -599,16 +964,25 @@ bool apass_tma_supported(int64_t I, int64_t post) {
     return post % 4 == 0;
 }
 
-int apass_tma_tasks(int64_t I, int64_t pre, int64_t post) {
+// Columns per task of each A-pass kind (post > 1: within one a-row).
+static int64_t task_cols(int64_t post, int kind) {
+    if (kind != APASS_FFMA) return TC_BN;
+    return post == 1 ? 256 : (post < 256 ? post : 256);
+}
+
+int apass_tma_tasks(int64_t I, int64_t pre, int64_t post, int kind) {
     (void)I;
-    if (post == 1) return (int)((pre + 255) / 256);
-    const int64_t BN = post < 256 ? post : 256;
+    const int64_t BN = task_cols(post, kind);
+    if (post == 1) return (int)((pre + BN - 1) / BN);
     return (int)(pre * ((post + BN - 1) / BN));
 }
 
-ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, char* err, size_t errlen) {
+ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, int kind, int num_sms, char* err,
+                             size_t errlen) {
     ApassTmaPlan* p = new ApassTmaPlan();
     std::memset(&p->maps, 0, sizeof(p->maps));
+    p->kind = kind;
+    p->grid = num_sms;
     p->args = ApassTmaArgs{};
     p->args.count = count;
     p->args.sc = const_cast<DevScalars*>(a[modes[0]].sc);
@@ -620,11 +994,11 @@ ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, ch
         ApassTmaMode& mm = p->args.m[q];
         mm.I = x.I; mm.pre = x.pre; mm.post = x.post; mm.P = x.P;
         mm.rowmajor = x.post == 1;
-        mm.BN = mm.rowmajor ? 256 : (int)(x.post < 256 ? x.post : 256);
+        mm.BN = (int)task_cols(x.post, kind);
         mm.nbb = mm.rowmajor ? 1 : (int)((x.post + mm.BN - 1) / mm.BN);
         mm.A = x.A;
         mm.gram_part = x.gram_part;
-        const int ntask = apass_tma_tasks(x.I, x.pre, x.post);
+        const int ntask = apass_tma_tasks(x.I, x.pre, x.post, kind);
         p->args.cta_start[q] = start;
         start += ntask;
         const int Rp = x.Rp;
@@ -635,7 +1009,7 @@ ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, ch
             ok = encode_tiled_f32(&p->maps.g[q], x.G, 3, d, b, CU_TENSOR_MAP_SWIZZLE_NONE, err, errlen, "A-pass G");
         } else {
             uint64_t d[2] = {(uint64_t)x.I, (uint64_t)x.pre};
-            uint32_t b[2] = {(uint32_t)AP_BK, 256u};
+            uint32_t b[2] = {(uint32_t)AP_BK, (uint32_t)mm.BN};
             ok = encode_tiled_f32(&p->maps.g[q], x.G, 2, d, b, CU_TENSOR_MAP_SWIZZLE_64B, err, errlen, "A-pass G");
         }
         if (ok) {
@@ -644,9 +1018,13 @@ ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, ch
             ok = encode_tiled_f32(&p->maps.u[q], x.U, 2, d, b, CU_TENSOR_MAP_SWIZZLE_NONE, err, errlen, "A-pass U");
         }
         if (!ok) { delete p; return nullptr; }
-        const size_t pipe = (size_t)AT_STAGES * at_stage_floats(mm.BN, Rp);
-        const size_t epi = (size_t)AP_BN * (Rp + 4) + gram_red_floats(Rp, Rp <= 40 ? AP_BN / 4 : AP_BN / 2);
-        smem = std::max(smem, 4 * std::max(pipe, epi) + 512);
+        if (kind == APASS_FFMA) {
+            const size_t pipe = (size_t)AT_STAGES * at_stage_floats(mm.BN, Rp);
+            const size_t epi = (size_t)AP_BN * (Rp + 4) + gram_red_floats(Rp, Rp <= 40 ? AP_BN / 4 : AP_BN / 2);
+            smem = std::max(smem, 4 * std::max(pipe, epi) + 512);
+        } else {
+            smem = std::max(smem, tc_smem(Rp) + 1024);
+        }
     }
     p->args.cta_start[count] = start;
     p->smem = smem;

@@ -118,6 +118,7 @@ struct pasd_plan {
     MpassTmaPlan* mp_tma = nullptr;
     // A-pass: TMA plans (one per padded rank) and the modes on the cp.async kernel
     bool ap_use_tma[PASD_MAXN];
+    int ap_kind = APASS_FFMA;            // arithmetic of the TMA-fed A-pass (ApassKind)
     ApassTmaPlan* ap_tma[PASD_MAXN];
     int n_ap_tma = 0;
     ApassArgs ap_plain[PASD_MAXN];
@@ -292,11 +293,17 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     }
     if (!pl->want_tma) pl->fg = pl->fg_plain;
     const bool tma_ok = !(nt && nt[0] == '1');
+    // A-pass products: FP32 multiply-adds (FP32 precision), or the tensor cores
+    // with the TF32 hi/lo split (mixed precision). The split products land about
+    // 2x further from FP64 than the FMAs, and at these skinny shapes (N = Rp)
+    // converting each stage into split operands costs more than the FMAs, so the
+    // FP32 path keeps the FMA kernel.
+    pl->ap_kind = p.precision == PASD_PREC_MIXED ? APASS_TC : APASS_FFMA;
     for (int n = 0; n < N; ++n) {
         const ModeGeom& g = pl->m[n];
         pl->ap_use_tma[n] = tma_ok && apass_tma_supported(g.I, g.post);
         // Gram partials: room for either kernel's CTA count (the TMA plan may be refused later)
-        pl->ncta_ap[n] = std::max(apass_ncta(g.P), apass_tma_tasks(g.I, g.pre, g.post));
+        pl->ncta_ap[n] = std::max(apass_ncta(g.P), apass_tma_tasks(g.I, g.pre, g.post, pl->ap_kind));
     }
     // M-pass: row strips x column ranges, as many CTAs as fit on the device at
     // once (one wave), split over the modes in proportion to their columns
@@ -572,14 +579,14 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
             for (int k = n; k < N; ++k)
                 if (pl->ap_use_tma[k] && !grouped[k] && pl->m[k].Rp == pl->m[n].Rp) { modes[cnt++] = k; grouped[k] = true; }
             char err[256] = {0};
-            ApassTmaPlan* tp = make_apass_tma(pl->ap, modes, cnt, err, sizeof(err));
+            ApassTmaPlan* tp = make_apass_tma(pl->ap, modes, cnt, pl->ap_kind, pl->ctx->num_sms, err, sizeof(err));
             if (tp) pl->ap_tma[pl->n_ap_tma++] = tp;
             else for (int q = 0; q < cnt; ++q) pl->ap_use_tma[modes[q]] = false;
         }
         for (int n = 0; n < N; ++n) {
             const ModeGeom& g = pl->m[n];
             if (!pl->ap_use_tma[n]) pl->ap_plain[pl->n_ap_plain++] = pl->ap[n];
-            sa.m[n].n_gram = pl->ap_use_tma[n] ? apass_tma_tasks(g.I, g.pre, g.post) : apass_ncta(g.P);
+            sa.m[n].n_gram = pl->ap_use_tma[n] ? apass_tma_tasks(g.I, g.pre, g.post, pl->ap_kind) : apass_ncta(g.P);
         }
     }
 

@@ -84,10 +84,14 @@ struct ApassTmaArgs {
     int cta_start[PASD_MAXN + 1];
 };
 struct ApassTmaPlan;
+// Arithmetic of a TMA-fed A-pass launch: FP32 FMAs, or the tensor cores
+// (tcgen05, TF32 with the hi/lo split that keeps FP32 accuracy).
+enum ApassKind { APASS_FFMA = 0, APASS_TC = 1 };
 bool apass_tma_supported(int64_t I, int64_t post);
-int apass_tma_tasks(int64_t I, int64_t pre, int64_t post);
+int apass_tma_tasks(int64_t I, int64_t pre, int64_t post, int kind);
 // modes[0..count) index `a`; all share a[modes[0]].Rp. nullptr (with err) if a map is refused.
-ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, char* err, size_t errlen);
+ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, int kind, int num_sms, char* err,
+                             size_t errlen);
 void launch_apass_tma(const ApassTmaPlan* p, cudaStream_t s);
 void destroy_apass_tma(ApassTmaPlan* p);
 // All modes in as few launches as possible (one per distinct padded rank);

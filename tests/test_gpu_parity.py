@@ -244,6 +244,72 @@ def test_full_size_trajectory_matches_oracle_golden(env):
     P.pasd_plan_destroy(plan)
 
 
+MIXED_TOL = 1e-3
+
+
+def _check_mixed(g, ref, n_modes):
+    # mixed precision (tensor-core TF32-split V-step products): the same kept
+    # counts at every iteration and the same stopping iteration, L and E within 1e-3
+    gk = g["trace"][:, 5:5 + n_modes].astype(int).tolist()
+    rk = [s.kept for s in ref.trace]
+    assert g["res"].iters == ref.iters
+    assert gk == rk, "kept counts differ (first at %s)" % next(i for i, (a, b) in enumerate(zip(gk, rk)) if a != b)
+    assert _rel(g["L"], ref.L) <= MIXED_TOL
+    assert _rel(g["E"], ref.E) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("stop,iters", [(2, 150), (0, 1000)])
+def test_mixed_small_cube_matches_oracle(env, stop, iters):
+    _, P, _ = env
+    pr = synth.planted((24, 20, 16), (3, 3, 2), 0.1, 7, scale="std", amp=5.0)
+    ref = _oracle(pr.T, (4, 4, 3), stop, iters)
+    g = _gpu_solve(env, pr.T, (4, 4, 3), stop, iters, precision=P.PREC_MIXED)
+    _check_mixed(g, ref, 3)
+
+
+@pytest.mark.parametrize("dims,tucker,ranks", [
+    ((40, 36, 32), (3, 3, 3), (12, 12, 12)),
+    ((64, 48, 40), (4, 4, 4), (20, 20, 20)),
+    ((12, 10, 3, 20), (2, 2, 2, 2), (3, 3, 2, 4)),
+])
+def test_mixed_shapes_match_oracle(env, dims, tucker, ranks):
+    _, P, _ = env
+    pr = synth.planted(dims, tucker, 0.1, 3, scale="std", amp=5.0)
+    ref = _oracle(pr.T, ranks, 0, 1000)
+    g = _gpu_solve(env, pr.T, ranks, 0, 1000, precision=P.PREC_MIXED)
+    _check_mixed(g, ref, len(dims))
+
+
+def test_mixed_full_size_trajectory_matches_oracle_golden(env):
+    # the 200^3 workload solved with mixed precision against the oracle's stored
+    # solve: identical kept counts per iteration, same stopping iteration, sampled
+    # L and E within 1e-3, recovery error within 1e-4 of the FP64 solve's
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "cube200_trajectory.json")
+    gold = json.load(open(path))
+    torch, P, ctx = env
+    pr = synth.cube_200(1)
+    params = P.make_params(pr.T.shape, tuple(gold["ranks"]), alpha=tuple(gold["alpha"]), lam=gold["lambda"],
+                           stop=P.STOP_FRO_REL, tol=gold["tol"], max_iter=1000, precision=P.PREC_MIXED)
+    plan, _ = P.pasd_plan(ctx, params)
+    Td = torch.from_numpy(pr.T).cuda()
+    L = torch.empty_like(Td)
+    E = torch.empty_like(Td)
+    res = P.pasd_solve(plan, Td, L, E)
+    trace = np.zeros((res.iters, P.TRACE_STRIDE))
+    P.pasd_state_get(plan, P.STATE_TRACE, 0, trace)
+    assert trace[:, 5:8].astype(int).tolist() == gold["kept"]
+    assert res.iters == gold["iters"] and res.status == 0
+    idx = torch.from_numpy(np.asarray(gold["sample_index"])).cuda()
+    assert _rel(L.reshape(-1)[idx].cpu().numpy().astype(np.float64), np.asarray(gold["L_sample"])) <= MIXED_TOL
+    assert _rel(E.reshape(-1)[idx].cpu().numpy().astype(np.float64), np.asarray(gold["E_sample"])) <= MIXED_TOL
+    L0 = torch.from_numpy(pr.L0).cuda()
+    rse = float(torch.linalg.vector_norm(L.double() - L0) / torch.linalg.vector_norm(L0))
+    assert abs(rse - gold["rse"]) <= 1e-4
+    P.pasd_plan_destroy(plan)
+
+
 def test_multiplier_bound_and_orthonormality_on_gpu(env):
     # ||sum_n Y_n||_inf <= 1 (App. A) and U_n^T U_n = I along a GPU run.
     torch, P, ctx = env
