@@ -83,8 +83,17 @@ typedef struct {
     int32_t precision;                    /* pasd_precision                             */
     int32_t check_every;                  /* loop bodies between host reads of the
                                              device stop flag; 0 -> 8                  */
-    uint32_t flags;                       /* reserved, must be 0                        */
+    uint32_t flags;                       /* PASD_F_* bits                              */
 } pasd_params;
+
+/* Skip the idle start. While V_n = 0 and E = 0 a loop body of Algorithm 1 only
+ * rescales the multipliers (G_n = T - E + Y_n/mu becomes g T), and it stays so
+ * while g sigma_max(U_n^T T_(n)) <= lambda_n/mu for every n and g max|T| <=
+ * 1/(N mu). After the first body the solver evaluates these conditions from
+ * that body's singular values and residual and replaces the idle bodies that
+ * follow (all but the last) by their closed form: the same iterate, the same
+ * trace records (kept 0), counted in `iters` and reported in `skipped`. */
+#define PASD_F_SKIP_IDLE 1u
 
 typedef struct {
     int32_t status;                       /* pasd_status of the solve                  */
@@ -97,6 +106,9 @@ typedef struct {
     double mu_final;                      /* mu after the last loop body               */
     int32_t kept[PASD_MAX_ORDER];         /* singular values kept by the last SVT      */
     double latency_s;                     /* served solves: submit -> retire, seconds  */
+    int32_t skipped;                      /* loop bodies replaced by the idle-start
+                                             closed form (PASD_F_SKIP_IDLE), included
+                                             in iters                                  */
 } pasd_result;
 
 typedef struct pasd_ctx pasd_ctx;

@@ -133,6 +133,10 @@ struct pasd_plan {
     cudaEvent_t ev = nullptr;
     bool busy = false;
     int ap_launches = 1;
+    // idle-start skip (PASD_F_SKIP_IDLE): armed by pasd_begin, run after the first body
+    float* idle_g = nullptr;
+    IdleSkipArgs idle{};
+    bool skip_pending = false;
 };
 
 // ---------------------------------------------------------------------------
@@ -223,7 +227,7 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     if (p.stop_rule < 0 || p.stop_rule > 2) return fail(PASD_ERR_INVALID_ARG, "bad stop rule");
     if (p.precision != PASD_PREC_FP32 && p.precision != PASD_PREC_MIXED)
         return fail(PASD_ERR_INVALID_ARG, "bad precision");
-    if (p.flags != 0) return fail(PASD_ERR_INVALID_ARG, "flags must be 0");
+    if (p.flags & ~(uint32_t)PASD_F_SKIP_IDLE) return fail(PASD_ERR_INVALID_ARG, "unknown flag bits");
 
     pasd_plan_t* pl = new pasd_plan_t();
     pl->ctx = c;
@@ -393,7 +397,7 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
         f += align256((size_t)g.I * g.Rp * 4);              // Mred_n
     }
     f += align256((size_t)nparts * (3 + N) * 4);
-    f += align256(1024 * 4) + align256(PASD_MAXN * 4);
+    f += align256(1024 * 4) + align256(PASD_MAXN * 4) + align256(4);   // + idle-skip factor
     f += align256((size_t)p.max_iter * PASD_TRACE_STRIDE * 8);
     if (pl->pad) f += align256(Dp * 4);                    // output-pass target
     pl->footprint = f;
@@ -468,6 +472,7 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
     pl->part = reinterpret_cast<float*>(take((size_t)std::max(pl->fg.nregions, pl->fg_plain.nregions) * (3 + N) * 4));
     pl->sq_part = reinterpret_cast<float*>(take(1024 * 4));
     pl->kept = reinterpret_cast<int32_t*>(take(PASD_MAXN * 4));
+    pl->idle_g = reinterpret_cast<float*>(take(4));
     pl->trace = reinterpret_cast<double*>(take((size_t)pl->p.max_iter * PASD_TRACE_STRIDE * 8));
     if (pl->pad) pl->Lpad = reinterpret_cast<float*>(take(D * 4));
     // zeros everywhere once: the padded entries of T, E, G_n are never written
@@ -531,6 +536,19 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
     for (int n = 0; n < N; ++n) fi.lambda[n] = pl->lam[n];
     fi.rho = pl->p.rho; fi.mu_max = pl->p.mu_max; fi.tol = pl->p.tol;
     fi.stop_rule = pl->p.stop_rule; fi.max_iter = pl->p.max_iter; fi.trace = pl->trace;
+    {
+        IdleSkipArgs& ia = pl->idle;
+        ia.sc = pl->sc;
+        ia.N = N;
+        for (int n = 0; n < N; ++n) { ia.sigma[n] = pl->sigma[n]; ia.lambda[n] = pl->lam[n]; ia.G[n] = pl->G[n]; }
+        ia.rho = pl->p.rho;
+        ia.mu_max = pl->p.mu_max;
+        ia.max_iter = pl->p.max_iter;
+        ia.trace = pl->trace;
+        ia.T = pl->Tc;
+        ia.D = pl->D;
+        ia.g = pl->idle_g;
+    }
     {
         int maxRp = 4;
         for (int n = 0; n < N; ++n) maxRp = std::max(maxRp, pl->m[n].Rp);
@@ -680,6 +698,7 @@ extern "C" pasd_status pasd_begin(pasd_plan_t* pl, const float* T, void* stream)
     for (int n = 0; n < N; ++n) { Is[n] = pl->m[n].I; Rs[n] = pl->m[n].R; Rps[n] = pl->m[n].Rp; }
     launch_init_state(pl->sc, pl->Tc, pl->p.mu0, N, pl->U, Is, Rs, Rps, pl->W, pl->F, pl->Urot, pl->kept, s);
     launch_norm_fro(pl->Tc, pl->D, pl->sq_part, 1024, pl->sc, s);
+    pl->skip_pending = (pl->p.flags & PASD_F_SKIP_IDLE) != 0;
     CUDA_TRY(cudaGetLastError());
     return PASD_OK;
 }
@@ -691,6 +710,11 @@ extern "C" pasd_status pasd_iterate(pasd_plan_t* pl, int32_t iters, void* stream
     for (int i = 0; i < iters; ++i) {
         if (pl->use_graph) CUDA_TRY(cudaGraphLaunch(pl->exec, s));
         else enqueue_iteration(pl, s);
+        if (pl->skip_pending) {
+            // first body after pasd_begin: replace the provably idle bodies that follow
+            launch_idle_skip(pl->idle, pl->ctx->num_sms, s);
+            pl->skip_pending = false;
+        }
     }
     CUDA_TRY(cudaGetLastError());
     return PASD_OK;
@@ -713,6 +737,7 @@ static void fill_result(pasd_plan_t* pl, pasd_result* r) {
     r->l1_E = h.l1_E;
     r->mu_final = h.mu;
     for (int n = 0; n < pl->N; ++n) { r->kept[n] = h.kept[n]; r->nuclear[n] = h.nuclear[n]; }
+    r->skipped = h.skipped;
 }
 
 extern "C" pasd_status pasd_finish(pasd_plan_t* pl, float* L, float* E, pasd_result* res,

@@ -37,7 +37,7 @@ struct DevScalars {
     double nuclear[PASD_MAXN];
     double res_inf, res_fro_rel, objective, l1_E, mu_used;
     int32_t nonfinite;
-    int32_t pad_;
+    int32_t skipped;       // idle loop bodies replaced by their closed form
 };
 
 struct ModeGeom {
@@ -149,6 +149,23 @@ void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 void launch_init_state(DevScalars* sc, const float* T, double mu0, int N, float** U,
                        const int64_t* I, const int* R, const int* Rp, float** W, float** F,
                        float** Urot, int32_t* kept, cudaStream_t s);
+
+// Idle-start skip (idle.cu): after the first loop body, replaces the bodies
+// that provably keep V = E = 0 by their closed form.
+struct IdleSkipArgs {
+    DevScalars* sc;
+    int N;
+    const float* sigma[PASD_MAXN];   // singular values of U_n^T G_n, descending
+    double lambda[PASD_MAXN];
+    double rho, mu_max;
+    int max_iter;
+    double* trace;                   // [max_iter][13] or null
+    const float* T;                  // plan copy of T
+    float* G[PASD_MAXN];
+    int64_t D;
+    float* g;                        // device scalar: the factor g (0: no skip)
+};
+void launch_idle_skip(const IdleSkipArgs& a, int num_sms, cudaStream_t s);
 
 struct VrotMode {
     const float* A;        // [pre][Rp][post]

@@ -865,6 +865,7 @@ __global__ void init_kernel(InitArgs a) {
         sc->done = 0;
         sc->status = 2;
         sc->nonfinite = 0;
+        sc->skipped = 0;
         for (int m = 0; m < PASD_MAXN; ++m) { sc->kept[m] = 0; sc->nuclear[m] = 0.0; }
         sc->res_inf = sc->res_fro_rel = sc->objective = sc->l1_E = 0.0;
         sc->mu_used = a.mu0;

@@ -22,6 +22,7 @@ OK, PENDING, NOT_CONVERGED = 0, 1, 2
 ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE = -1, -2, -3, -4
 ERR_TIMEOUT, ERR_BUSY, ERR_UNKNOWN_TICKET, ERR_UNSUPPORTED = -5, -6, -7, -8
 PREC_FP32, PREC_MIXED = 0, 1
+F_SKIP_IDLE = 1
 STOP_INF_ABS, STOP_FRO_REL, STOP_FIXED_ITERS = 0, 1, 2
 STATE_U, STATE_A, STATE_W, STATE_SIGMA, STATE_F, STATE_E, STATE_Y, STATE_MU, STATE_KEPT, STATE_TRACE = range(10)
 
@@ -58,6 +59,7 @@ class pasd_result(ctypes.Structure):
         ("mu_final", ctypes.c_double),
         ("kept", ctypes.c_int32 * MAX_ORDER),
         ("latency_s", ctypes.c_double),
+        ("skipped", ctypes.c_int32),
     ]
 
 
@@ -274,7 +276,8 @@ def pasd_last_error() -> str:
 # --- convenience -------------------------------------------------------------
 
 def make_params(dims, ranks, *, alpha=None, lam=None, lambda_n=None, mu0=0.0, mu_max=0.0, rho=0.0,
-                tol=0.0, stop=STOP_INF_ABS, max_iter=0, precision=PREC_FP32, check_every=0) -> pasd_params:
+                tol=0.0, stop=STOP_INF_ABS, max_iter=0, precision=PREC_FP32, check_every=0,
+                flags=0) -> pasd_params:
     p = pasd_params_default(dims, ranks)
     if alpha is not None:
         for n, a in enumerate(alpha):
@@ -292,10 +295,12 @@ def make_params(dims, ranks, *, alpha=None, lam=None, lambda_n=None, mu0=0.0, mu
     if max_iter: p.max_iter = max_iter
     p.precision = precision
     if check_every: p.check_every = check_every
+    p.flags = flags
     return p
 
 
 def result_dict(r: pasd_result, order: int) -> dict:
     return {"status": r.status, "iters": r.iters, "res_inf": r.res_inf, "res_fro_rel": r.res_fro_rel,
             "objective": r.objective, "nuclear": list(r.nuclear)[:order], "l1_E": r.l1_E,
-            "mu_final": r.mu_final, "kept": list(r.kept)[:order], "latency_s": r.latency_s}
+            "mu_final": r.mu_final, "kept": list(r.kept)[:order], "latency_s": r.latency_s,
+            "skipped": r.skipped}

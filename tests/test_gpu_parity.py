@@ -244,6 +244,58 @@ def test_full_size_trajectory_matches_oracle_golden(env):
     P.pasd_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("case", ["small_fixed", "small_converged", "cube50"])
+def test_idle_skip_matches_oracle(env, case):
+    # PASD_F_SKIP_IDLE replaces the idle bodies after the first by their closed
+    # form; the trace (kept counts per iteration), the iteration count and L, E
+    # must still be the oracle's, and bodies must actually have been skipped.
+    _, P, _ = env
+    if case == "cube50":
+        pr = synth.cube_small(0)
+        ranks, stop, iters, lp = (10,) * 3, 2, 100, ((1 / 3,) * 3, 1 / 50)
+        kw = dict(alpha=lp[0], lam=lp[1])
+    else:
+        pr = synth.planted((24, 20, 16), (3, 3, 2), 0.1, 7, scale="std", amp=5.0)
+        ranks, lp, kw = (4, 4, 3), None, {}
+        stop, iters = (2, 150) if case == "small_fixed" else (0, 1000)
+    ref = _oracle(pr.T, ranks, stop, iters, lp)
+    g = _gpu_solve(env, pr.T, ranks, stop, iters, flags=P.F_SKIP_IDLE, **kw)
+    _check_parity(g, ref, 3)
+    first_active = next(i for i, s in enumerate(ref.trace) if any(s.kept))
+    assert 0 < g["res"].skipped < first_active
+    # replaced bodies are recorded like computed idle ones
+    tr = g["trace"]
+    assert np.all(tr[:first_active, 5:8] == 0)
+    assert np.array_equal(tr[:, 0], np.arange(1, g["res"].iters + 1))
+
+
+def test_idle_skip_full_size_trajectory(env):
+    # the 200^3 workload with the idle-start skip against the oracle's stored solve
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "cube200_trajectory.json")
+    gold = json.load(open(path))
+    torch, P, ctx = env
+    pr = synth.cube_200(1)
+    params = P.make_params(pr.T.shape, tuple(gold["ranks"]), alpha=tuple(gold["alpha"]), lam=gold["lambda"],
+                           stop=P.STOP_FRO_REL, tol=gold["tol"], max_iter=1000, flags=P.F_SKIP_IDLE)
+    plan, _ = P.pasd_plan(ctx, params)
+    Td = torch.from_numpy(pr.T).cuda()
+    L = torch.empty_like(Td)
+    E = torch.empty_like(Td)
+    res = P.pasd_solve(plan, Td, L, E)
+    trace = np.zeros((res.iters, P.TRACE_STRIDE))
+    P.pasd_state_get(plan, P.STATE_TRACE, 0, trace)
+    assert trace[:, 5:8].astype(int).tolist() == gold["kept"]
+    assert res.iters == gold["iters"] and res.status == 0
+    first_active = next(i for i, k in enumerate(gold["kept"]) if any(k))
+    assert 50 <= res.skipped < first_active
+    idx = torch.from_numpy(np.asarray(gold["sample_index"])).cuda()
+    assert _rel(L.reshape(-1)[idx].cpu().numpy().astype(np.float64), np.asarray(gold["L_sample"])) <= TOL
+    assert _rel(E.reshape(-1)[idx].cpu().numpy().astype(np.float64), np.asarray(gold["E_sample"])) <= TOL
+    P.pasd_plan_destroy(plan)
+
+
 MIXED_TOL = 1e-3
 
 

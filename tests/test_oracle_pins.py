@@ -372,3 +372,36 @@ def test_fp32_state_floor_dense_sparse_part():
     cube = floor(synth.planted((24, 20, 16), (3, 3, 2), 0.1, 7, scale="std", amp=5.0), (4, 4, 3), 150)
     assert 1e-5 < video < 1e-4
     assert cube < 1e-6
+
+
+def test_idle_start_closed_form():
+    # Algorithm 1 from V_n = 0, E = 0 at the paper's mu0: while nothing is kept
+    # and E stays 0, a loop body only adds mu T to every multiplier, so
+    # Y_n^i = mu0 T (rho^i - 1) / (rho - 1) and G_n^i = T + Y_n^i / mu^i = g_i T.
+    # Iteration i stays idle exactly while g_i sigma_max(T_(n)[:R_n]) <= lambda_n / mu^i
+    # for every n (Eq. 13 with U_n = eye) and g_i max|T| <= 1 / (N mu^i) (Eq. 15).
+    # The first active iteration predicted from these two tests must be the
+    # oracle's, which is what the solver's idle-start skip relies on.
+    pr = synth.planted((16, 14, 12), (2, 2, 2), 0.1, 5, scale="std", amp=5.0)
+    T = pr.T.astype(np.float64)
+    ranks = (3, 3, 3)
+    p = O.Params(ranks=ranks, lambdas=O.paper_lambdas(T.shape), stop="fixed", max_iter=400)
+    smax = [np.linalg.svd(O.unfold(T, n)[:ranks[n]], compute_uv=False)[0] for n in range(3)]
+    tmax = float(np.abs(T).max())
+    mu, c, i_a = p.mu0, 0.0, 0
+    while (1 + c) * tmax <= 1 / (mu * 3) and all((1 + c) * smax[n] <= p.lambdas[n] / mu for n in range(3)):
+        mn = min(p.rho * mu, p.mu_max)
+        c = (c + 1) * mu / mn
+        mu = mn
+        i_a += 1
+    assert i_a > 10
+    st = O.init_state(T, ranks, p.mu0)
+    for it in range(i_a + 1):
+        info = O.step(T, st, p)
+        if it < i_a:
+            assert info.kept == [0, 0, 0] and not st.E.any()
+            closed = p.mu0 * T * (p.rho ** (it + 1) - 1) / (p.rho - 1)
+            for n in range(3):
+                assert np.allclose(st.Y[n], closed, rtol=1e-12, atol=0)
+        else:
+            assert any(info.kept) or st.E.any()
