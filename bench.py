@@ -17,9 +17,11 @@ Extra keys: roofline of the dominant kernel (CUDA-event duration of the fused
 elementwise pass vs its algorithmic bytes), clocks sampled during the timed
 region, e2e (whole solves through pasd_solve_host with pinned host buffers),
 serving (Poisson arrivals of planted cubes of sides 32-256 through
-pasd_submit / pasd_poll: solves/s, p50 / p99 latency, and the same requests
-solved one at a time), video (loop bodies/s on the 144x176x3x300 colour-video
-shape) and cpu_baseline (the FP64 oracle on the host cores, a bounded sample).
+pasd_submit / pasd_poll, served with the FP32 path and with mixed precision,
+both with the idle-start skip: solves/s, p50 / p99 latency, against the same
+requests solved one at a time with the plain FP32 path), video (loop bodies/s
+on the 144x176x3x300 colour-video shape, FP32 and mixed) and cpu_baseline (the
+FP64 oracle on the host cores, a bounded sample).
 
 --impl reference times the FP64 oracle (the method as the paper defines it),
 each step one loop body on the same 200^3 workload.
@@ -182,7 +184,9 @@ def _percentile(xs, q):
 
 def _serving(P, torch, ctx, args):
     """Continuous-batching service: Poisson arrivals of planted cubes through
-    pasd_submit / pasd_poll, against the same requests solved one at a time."""
+    pasd_submit / pasd_poll, served once with the FP32 path and once with mixed
+    precision (both with the idle-start skip), against the same requests solved
+    one at a time with the plain FP32 path."""
     import numpy as np
     from paper_1712_09999_gb300 import synth
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -191,63 +195,87 @@ def _serving(P, torch, ctx, args):
     probs = [synth.serving_problem(sp) for sp in specs]
     gen_s = time.perf_counter() - tg
     Ts = [torch.from_numpy(pr.T).to(dev) for pr in probs]
-    slots = []
-    serial_ms = []
-    iters = []
-    for q, sp in enumerate(specs):
-        prm = P.make_params(sp.dims, sp.rank_bounds, max_iter=1000)
-        row = []
-        for _ in range(args.serve_slots):
-            plan, _ = P.pasd_plan(ctx, prm)
-            L = torch.empty_like(Ts[q])
-            E = torch.empty_like(Ts[q])
-            P.pasd_solve(plan, Ts[q], L, E)          # allocation, graph capture, warm-up
-            row.append((plan, L, E))
-        slots.append(row)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        r = P.pasd_solve(row[0][0], Ts[q], row[0][1], row[0][2])
-        e1.record()
-        torch.cuda.synchronize()
-        serial_ms.append(e0.elapsed_time(e1))
-        iters.append(int(r.iters))
     n_req = int(args.serve_rate * args.serve_seconds)
     arrivals = synth.poisson_arrivals(args.serve_rate, n_req, seed=5)
     which = np.random.Generator(np.random.PCG64(6)).integers(0, len(specs), size=n_req)
-    nxt = [0] * len(specs)
-    pending = {}
-    lat, finish, bad = [], [], 0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    i = 0
-    while i < n_req or pending:
-        now = time.perf_counter() - t0
-        while i < n_req and arrivals[i] <= now:
-            q = int(which[i])
-            plan, L, E = slots[q][nxt[q]]
-            nxt[q] = (nxt[q] + 1) % len(slots[q])
-            pending[P.pasd_submit(ctx, plan, Ts[q], L, E)] = float(arrivals[i])
-            i += 1
-        for tk in list(pending):
-            st, _ = P.pasd_poll(ctx, tk)
-            if st != P.PENDING:
-                f = time.perf_counter() - t0
-                lat.append(f - pending.pop(tk))
-                finish.append(f)
-                bad += st not in (P.OK, P.NOT_CONVERGED)
-        time.sleep(0.0002)
-    span = max(finish) - float(arrivals[0])
+
+    def timed_solve(plan, q, L, E):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = P.pasd_solve(plan, Ts[q], L, E)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    # serial baseline: plain FP32 solves, one at a time
+    serial_ms, iters = [], []
+    for q, sp in enumerate(specs):
+        plan, _ = P.pasd_plan(ctx, P.make_params(sp.dims, sp.rank_bounds, max_iter=1000))
+        L = torch.empty_like(Ts[q])
+        E = torch.empty_like(Ts[q])
+        P.pasd_solve(plan, Ts[q], L, E)                  # allocation, graph capture, warm-up
+        ms, r = timed_solve(plan, q, L, E)
+        serial_ms.append(ms)
+        iters.append(int(r.iters))
+        P.pasd_plan_destroy(plan)
     serial_s = sum(serial_ms[int(q)] for q in which) / 1000.0
-    for row in slots:
-        for plan, _, _ in row:
-            P.pasd_plan_destroy(plan)
-    return {"offered_rate": args.serve_rate, "requests": n_req, "solves_per_s": n_req / span,
-            "p50_ms": 1000 * _percentile(lat, 50), "p99_ms": 1000 * _percentile(lat, 99),
-            "serial_solves_per_s": n_req / serial_s, "failed": bad, "precision": "fp32",
+
+    def serve(precision):
+        slots, outs, skipped, one_ms = [], [], [], []
+        for q, sp in enumerate(specs):
+            prm = P.make_params(sp.dims, sp.rank_bounds, max_iter=1000, precision=precision, flags=P.F_SKIP_IDLE)
+            row = []
+            for _ in range(args.serve_slots):
+                plan, _ = P.pasd_plan(ctx, prm)
+                L = torch.empty_like(Ts[q])
+                E = torch.empty_like(Ts[q])
+                P.pasd_solve(plan, Ts[q], L, E)          # allocation, graph capture, warm-up
+                row.append((plan, L, E))
+            ms, r = timed_solve(row[0][0], q, row[0][1], row[0][2])
+            one_ms.append(round(ms, 2))
+            skipped.append(int(r.skipped))
+            outs.append(row[0][1].clone())
+            slots.append(row)
+        nxt = [0] * len(specs)
+        pending = {}
+        lat, finish, bad = [], [], 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        i = 0
+        while i < n_req or pending:
+            now = time.perf_counter() - t0
+            while i < n_req and arrivals[i] <= now:
+                q = int(which[i])
+                plan, L, E = slots[q][nxt[q]]
+                nxt[q] = (nxt[q] + 1) % len(slots[q])
+                pending[P.pasd_submit(ctx, plan, Ts[q], L, E)] = float(arrivals[i])
+                i += 1
+            for tk in list(pending):
+                st, _ = P.pasd_poll(ctx, tk)
+                if st != P.PENDING:
+                    f = time.perf_counter() - t0
+                    lat.append(f - pending.pop(tk))
+                    finish.append(f)
+                    bad += st not in (P.OK, P.NOT_CONVERGED)
+            time.sleep(0.0002)
+        span = max(finish) - float(arrivals[0])
+        for row in slots:
+            for plan, _, _ in row:
+                P.pasd_plan_destroy(plan)
+        return {"solves_per_s": n_req / span, "p50_ms": 1000 * _percentile(lat, 50),
+                "p99_ms": 1000 * _percentile(lat, 99), "failed": bad, "skipped_per_solve": skipped,
+                "solo_ms_per_solve": one_ms}, outs
+
+    fp32, out32 = serve(P.PREC_FP32)
+    mixed, outmx = serve(P.PREC_MIXED)
+    mixed["L_rel_vs_fp32_max"] = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+                                     for a, b in zip(outmx, out32))
+    return {"offered_rate": args.serve_rate, "requests": n_req, "fp32": fp32, "mixed": mixed,
+            "serial_plain_fp32_solves_per_s": n_req / serial_s,
             "mix": f"{len(specs)} planted cubes, side log-uniform 32-256, Tucker 3-20, R=floor(1.2 r), "
                    f"5-30% corruption (seed 4); {args.serve_slots} plans per problem; Poisson arrivals "
-                   f"(seed 5) for {args.serve_seconds} s",
+                   f"(seed 5) for {args.serve_seconds} s; served solves use the idle-start skip",
             "sides": [sp.dims[0] for sp in specs], "iters_per_solve": iters,
             "serial_ms_per_solve": [round(x, 2) for x in serial_ms], "generation_s": round(gen_s, 1)}
 
@@ -259,26 +287,29 @@ def _video(P, torch, ctx, args):
     dev = torch.device("cuda", torch.cuda.current_device())
     pr = synth.video()
     T = torch.from_numpy(pr.T).to(dev)
-    plan, footprint = P.pasd_plan(ctx, P.make_params(pr.T.shape, (20, 20, 3, 5), stop=P.STOP_FIXED_ITERS,
-                                                     max_iter=10 ** 6))
     stream = torch.cuda.current_stream()
-    P.pasd_begin(plan, T, stream)
-    P.pasd_iterate(plan, args.video_pre, stream)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    P.pasd_iterate(plan, args.video_iters, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    tr = __import__("numpy").zeros((args.video_pre + args.video_iters, P.TRACE_STRIDE))
-    P.pasd_state_get(plan, P.STATE_TRACE, 0, tr)
-    P.pasd_plan_destroy(plan)
-    return {"workload": "video 144x176x3x300 (rank-1 background, 16 moving rectangles, 5% voxels, seed 2), "
-                        "R=(20,20,3,5), paper-default lambda_n", "iters_per_s": args.video_iters / (ms / 1000.0),
-            "bodies_timed": [args.video_pre + 1, args.video_pre + args.video_iters],
-            "kept_at_end": tr[-1, 5:9].astype(int).tolist(), "footprint_bytes": footprint}
+    out = {"workload": "video 144x176x3x300 (rank-1 background, 16 moving rectangles, 5% voxels, seed 2), "
+                       "R=(20,20,3,5), paper-default lambda_n",
+           "bodies_timed": [args.video_pre + 1, args.video_pre + args.video_iters]}
+    for name, prec in (("fp32", P.PREC_FP32), ("mixed", P.PREC_MIXED)):
+        plan, footprint = P.pasd_plan(ctx, P.make_params(pr.T.shape, (20, 20, 3, 5), stop=P.STOP_FIXED_ITERS,
+                                                         max_iter=10 ** 6, precision=prec))
+        P.pasd_begin(plan, T, stream)
+        P.pasd_iterate(plan, args.video_pre, stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.pasd_iterate(plan, args.video_iters, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tr = __import__("numpy").zeros((args.video_pre + args.video_iters, P.TRACE_STRIDE))
+        P.pasd_state_get(plan, P.STATE_TRACE, 0, tr)
+        P.pasd_plan_destroy(plan)
+        out[name] = {"iters_per_s": args.video_iters / (ms / 1000.0), "kept_at_end": tr[-1, 5:9].astype(int).tolist()}
+        out["footprint_bytes"] = footprint
+    return out
 
 
 def run_ours(args):
