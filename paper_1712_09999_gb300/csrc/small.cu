@@ -201,16 +201,16 @@ __device__ void tile_AtB(const float* X, int ldx, int na, const float* Y, int ld
             a4 = tile / tb;
             b4 = tile % tb;
         }
-        const int64_t r0 = rows * sp / S, r1 = rows * (sp + 1) / S;
+        const int r0 = (int)(rows * sp / S), r1 = (int)(rows * (sp + 1) / S);
         float acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        const float* xp = X + r0 * ldx + 4 * a4;
-        const float* yp = Y + r0 * ldy + 4 * b4;
+        const float* xp = X + (int64_t)r0 * ldx + 4 * a4;
+        const float* yp = Y + (int64_t)r0 * ldy + 4 * b4;
 #pragma unroll 2
-        for (int64_t r = r0; r < r1; ++r, xp += ldx, yp += ldy) {
+        for (int r = r0; r < r1; ++r, xp += ldx, yp += ldy) {
             const float4 x = *reinterpret_cast<const float4*>(xp);
             const float4 y = *reinterpret_cast<const float4*>(yp);
             const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
@@ -250,13 +250,14 @@ __device__ void tile_AtB(const float* X, int ldx, int na, const float* Y, int ld
 __device__ void tile_AB(const float* X, int ldx, int inner, const float* S, int lds, int cols, int64_t rows,
                         float* Y, int ldy, bool sub) {
     const int c4n = cols / 4;
-    for (int64_t w = threadIdx.x; w < rows * c4n; w += blockDim.x) {
-        const int64_t i = w / c4n;
-        const int c4 = (int)(w % c4n);
-        float4* yp = reinterpret_cast<float4*>(Y + i * ldy + 4 * c4);
+    const int tot = (int)rows * c4n;
+    for (int w = threadIdx.x; w < tot; w += blockDim.x) {
+        const int i = w / c4n;
+        const int c4 = w - i * c4n;
+        float4* yp = reinterpret_cast<float4*>(Y + (int64_t)i * ldy + 4 * c4);
         float4 acc = sub ? *yp : make_float4(0.f, 0.f, 0.f, 0.f);
         const float sg = sub ? -1.f : 1.f;
-        const float* xr = X + i * ldx;
+        const float* xr = X + (int64_t)i * ldx;
         const float* sc = S + 4 * c4;
         int k = 0;
 #pragma unroll 2
@@ -306,27 +307,25 @@ __device__ void inv_sqrt_from_eig(const float* D, const float* Q, int n, int ld,
 // dst[i][c] = src[i][c0 + c] for c < w, 0 for w <= c < round4(w); rows x ...
 // (eight elements per thread per pass, loaded before any is stored, so the
 // global reads overlap instead of forming a chain)
+// (32-bit index arithmetic: rows x 64 columns stays below 2^31 for every mode
+// the planner accepts.)
 __device__ void copy_cols(const float* src, int lds, int c0, int w, int64_t rows, float* dst, int ldd) {
     const int w4 = (w + 3) & ~3;
-    const int64_t tot = rows * w4;
-    const int64_t step = (int64_t)blockDim.x;
-    for (int64_t base = threadIdx.x; base < tot; base += 8 * step) {
+    const int tot = (int)rows * w4;
+    const int step = blockDim.x;
+    for (int base = threadIdx.x; base < tot; base += 8 * step) {
         float v[8];
+        int off[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int64_t idx = base + u * step;
-            v[u] = 0.f;
-            if (idx < tot) {
-                const int64_t i = idx / w4;
-                const int c = (int)(idx % w4);
-                if (c < w) v[u] = src[i * lds + c0 + c];
-            }
+            const int idx = base + u * step;
+            const int i = idx / w4, c = idx - (idx / w4) * w4;
+            off[u] = idx < tot ? i * ldd + c : -1;
+            v[u] = (idx < tot && c < w) ? src[(int64_t)i * lds + c0 + c] : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int64_t idx = base + u * step;
-            if (idx < tot) dst[(idx / w4) * ldd + (idx % w4)] = v[u];
-        }
+        for (int u = 0; u < 8; ++u)
+            if (off[u] >= 0) dst[off[u]] = v[u];
     }
 }
 
@@ -547,9 +546,9 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
         inv_sqrt_from_eig(Ae, Ve, q, ld, Z);
         tile_AB(Bw, LD, q, Z, ld, q4, I, Xb, LD, false);
         __syncthreads();
-        for (int64_t idx = threadIdx.x; idx < I * q; idx += blockDim.x) {
-            const int64_t i = idx / q;
-            const int c = (int)(idx % q);
+        for (int idx = threadIdx.x; idx < (int)I * q; idx += blockDim.x) {
+            const int i = idx / q;
+            const int c = idx - i * q;
             Mw[i * LD + s + c] = Xb[i * LD + c];
         }
         __syncthreads();
