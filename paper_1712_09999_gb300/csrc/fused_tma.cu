@@ -14,8 +14,10 @@
 // Out-of-range parts of a box are zero-filled by the copy engine, so the
 // arithmetic below needs no masks: a zero element stays zero through the
 // update and adds nothing to the residual sums.
-// Results (E', G_n') overwrite E and G_n in the stage and go back to HBM as
-// bulk tensor stores, clipped to the tensor by the copy engine.
+// Results (E', G_n') go from registers straight to HBM as 16-byte stores (four
+// consecutive elements of the contiguous mode, whose length is a multiple of 4
+// here), so a stage is free for the next copy as soon as every thread has read
+// it: no shared-memory write-back and no store to wait for before a refill.
 #include "pasd_impl.cuh"
 #include "tma.cuh"
 
@@ -161,17 +163,23 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         }
     };
 
+    // Refill schedule. With nothing kept (pure streaming) the other stage is
+    // refilled before this tile's data is awaited, two copies in flight, at the
+    // cost of a second barrier per tile that releases the stage. With a refold
+    // to compute, a tile's arithmetic covers one copy's latency and the refill
+    // goes out after the wait, whose barrier also releases the stage.
+    bool early = !output;
+#pragma unroll
+    for (int n = 0; n < N; ++n) early = early && sp[n] == 0;
     bool failed = false;
     if (t == 0 && ntile > 0) issue(0);
     for (int64_t it = 0; it < ntile; ++it) {
         const int st = (int)(it & 1);
         const uint32_t par = (uint32_t)((it >> 1) & 1);
-        if (t == 0 && it + 1 < ntile) {
-            bulk_wait_read0();          // stores issued from the other stage have read their data
-            issue(st ^ 1);
-        }
+        if (early && t == 0 && it + 1 < ntile) issue(st ^ 1);
         bool ok = mbar_wait_bounded(&full_bar[st], par, kWaitPolls);
         if (__syncthreads_or(!ok)) { failed = true; break; }
+        if (!early && t == 0 && it + 1 < ntile) issue(st ^ 1);
         float* stg = sm + st * g.stage_floats;
         float* Xs = stg + g.xs_off;
         int o[N];
@@ -277,14 +285,19 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
                     }
                 }
             }
-            __syncthreads();
             continue;
         }
 
-        // ---- elementwise update, in place in the stage ----
+        // ---- elementwise update; results to HBM from registers ----
         //   gz_n = G_n - Z_n,  Ebar = mean_n(G_n + E - Z_n) = E + mean(gz),
         //   E' = prox(Ebar),  d = T - E',  r_n = d - Z_n,
         //   G_n' = d + (mu/mu') (gz_n + E - E')
+        int64_t gbase = 0;
+        bool valid = o[N - 1] + u0[N - 1] < g.I[N - 1];
+#pragma unroll
+        for (int n = 0; n < N; ++n) gbase += (int64_t)(o[n] + u0[n]) * g.stride[n];
+#pragma unroll
+        for (int n = 0; n < N - 2; ++n) valid = valid && (o[n] + u0[n] < g.I[n]);
 #pragma unroll
         for (int d2 = 0; d2 < 2; ++d2) {
             const int eb = e0 + (d2 << g.esh[N - 2]);
@@ -325,25 +338,16 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
                 l1 += fabsf(e);
                 chk += e;
             }
-            *reinterpret_cast<float4*>(Xs + B + eb) = make_float4(en[0], en[1], en[2], en[3]);
+            if (valid && o[N - 2] + u0[N - 2] + d2 < g.I[N - 2]) {
+                const int64_t e = gbase + (int64_t)d2 * g.stride[N - 2];
+                *reinterpret_cast<float4*>(fa.E + e) = make_float4(en[0], en[1], en[2], en[3]);
 #pragma unroll
-            for (int n = 0; n < N; ++n)
-                *reinterpret_cast<float4*>(Xs + (2 + n) * B + eb) = make_float4(gv[n][0], gv[n][1], gv[n][2], gv[n][3]);
+                for (int n = 0; n < N; ++n)
+                    *reinterpret_cast<float4*>(fa.G[n] + e) = make_float4(gv[n][0], gv[n][1], gv[n][2], gv[n][3]);
+            }
         }
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (t == 0) {
-            int cx[N];
-#pragma unroll
-            for (int k = 0; k < N; ++k) cx[k] = o[N - 1 - k];
-#pragma unroll
-            for (int a = 1; a < N + 2; ++a) tma_store<N>(&tm.tm_x[a], Xs + a * B, cx);
-            bulk_commit();
-        }
-
-        __syncthreads();
+        if (early) __syncthreads();   // stage st fully read: the next iteration refills it first
     }
-    if (t == 0) bulk_wait_read0();
     if (failed) {
         // a copy never arrived: record it and leave (the stage may still be written
         // by a straggling copy, so wait on both barriers once more, bounded)
