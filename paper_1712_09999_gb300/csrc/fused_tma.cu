@@ -98,10 +98,15 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
 #pragma unroll
     for (int n = 0; n < N; ++n) tc[n] = (int)ts[n];
 
-    // micro-box of this thread: 2 along mode N-2, 4 along mode N-1
+    // micro-box of this thread: 4 consecutive elements along mode N-1 and two
+    // rows dstep = b_{N-2} / 2 apart along mode N-2, so the 8 lanes of a
+    // quarter-warp read 8 consecutive 16-byte groups (no bank conflicts) in the
+    // element tiles and in the Vrot slices of the modes before N-2
+    const int dstep = g.b[N - 2] / 2;
     int u0[N];
 #pragma unroll
-    for (int n = 0; n < N; ++n) u0[n] = ((t >> g.mbsh[n]) & (g.b[n] / g.mb[n] - 1)) * g.mb[n];
+    for (int n = 0; n < N; ++n)
+        u0[n] = ((t >> g.mbsh[n]) & (g.b[n] / g.mb[n] - 1)) * (n == N - 2 ? 1 : g.mb[n]);
     int e0 = 0;
 #pragma unroll
     for (int n = 0; n < N; ++n) e0 += u0[n] << g.esh[n];
@@ -201,13 +206,14 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
             if (n == N - 1) {
                 const float* Wt = Ws + u0[n] * h;
                 const float* At = As + cb[n] * h;
+                const int a2 = (dstep << g.csh[n][N - 2]) * h;    // column of the second row
                 for (int r = 0; r < h; r += 4) {
                     float4 w[4];
 #pragma unroll
                     for (int d1 = 0; d1 < 4; ++d1) w[d1] = *reinterpret_cast<const float4*>(Wt + d1 * h + r);
 #pragma unroll
                     for (int d2 = 0; d2 < 2; ++d2) {
-                        const float4 a = *reinterpret_cast<const float4*>(At + d2 * h + r);
+                        const float4 a = *reinterpret_cast<const float4*>(At + d2 * a2 + r);
 #pragma unroll
                         for (int d1 = 0; d1 < 4; ++d1) {
                             float acc = z[n][d2 * 4 + d1];
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
                 if (n == N - 2) {
                     for (int r = 0; r < h; r += 4) {
                         const float4 w0 = *reinterpret_cast<const float4*>(Wt + r);
-                        const float4 w1 = *reinterpret_cast<const float4*>(Wt + h + r);
+                        const float4 w1 = *reinterpret_cast<const float4*>(Wt + dstep * h + r);
                         const float w0s[4] = {w0.x, w0.y, w0.z, w0.w}, w1s[4] = {w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
@@ -243,7 +249,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
                         }
                     }
                 } else {
-                    const int s2 = 1 << g.csh[n][N - 2];
+                    const int s2 = dstep << g.csh[n][N - 2];
                     for (int r = 0; r < h; r += 4) {
                         const float4 w = *reinterpret_cast<const float4*>(Wt + r);
                         const float ws[4] = {w.x, w.y, w.z, w.w};
@@ -273,8 +279,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
             for (int n = 0; n < N - 2; ++n) vbase = vbase && (o[n] + u0[n] < g.I[n]);
 #pragma unroll
             for (int d2 = 0; d2 < 2; ++d2) {
-                const bool v2 = vbase && (o[N - 2] + u0[N - 2] + d2 < g.I[N - 2]);
-                const int64_t rowoff = tbase + (int64_t)d2 * g.stride[N - 2];
+                const bool v2 = vbase && (o[N - 2] + u0[N - 2] + d2 * dstep < g.I[N - 2]);
+                const int64_t rowoff = tbase + (int64_t)(d2 * dstep) * g.stride[N - 2];
 #pragma unroll
                 for (int d1 = 0; d1 < 4; ++d1) {
                     if (v2 && (o[N - 1] + u0[N - 1] + d1 < g.I[N - 1])) {
@@ -300,7 +306,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         for (int n = 0; n < N - 2; ++n) valid = valid && (o[n] + u0[n] < g.I[n]);
 #pragma unroll
         for (int d2 = 0; d2 < 2; ++d2) {
-            const int eb = e0 + (d2 << g.esh[N - 2]);
+            const int eb = e0 + ((d2 * dstep) << g.esh[N - 2]);
             float4 x = *reinterpret_cast<const float4*>(Xs + eb);
             const float tv[4] = {x.x, x.y, x.z, x.w};
             x = *reinterpret_cast<const float4*>(Xs + B + eb);
@@ -338,8 +344,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
                 l1 += fabsf(e);
                 chk += e;
             }
-            if (valid && o[N - 2] + u0[N - 2] + d2 < g.I[N - 2]) {
-                const int64_t e = gbase + (int64_t)d2 * g.stride[N - 2];
+            if (valid && o[N - 2] + u0[N - 2] + d2 * dstep < g.I[N - 2]) {
+                const int64_t e = gbase + (int64_t)(d2 * dstep) * g.stride[N - 2];
                 *reinterpret_cast<float4*>(fa.E + e) = make_float4(en[0], en[1], en[2], en[3]);
 #pragma unroll
                 for (int n = 0; n < N; ++n)
