@@ -35,6 +35,7 @@ bool plan_geom_impl(FusedGeom& g, int N, const int64_t* I, const int* Rp, int nu
 // copies take their address. Everything else goes in a plain by-value
 // parameter (constant-bank operands, no memory loads).
 constexpr int kTmaMaxN = 4;            // the TMA pass handles N <= 4
+constexpr int kMaxStages = 4;          // element-tile stages while nothing is kept
 constexpr int kHeights = PASD_MAXR / 4;  // one map per row count 4, 8, ..., 64
 struct FusedTmaMaps {
     CUtensorMap tm_x[kTmaMaxN + 2];          // T copy, E, G_0..G_{N-1}
@@ -66,8 +67,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
     extern __shared__ __align__(1024) float sm_raw[];
     // stage buffers aligned to 1024 bytes (the launch adds 1 KB of slack)
     float* sm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full_bar[2];
-    __shared__ int tile_o[2][N];      // origins of the tiles in the two stages
+    __shared__ __align__(8) uint64_t full_bar[kMaxStages];
+    __shared__ int tile_o[kMaxStages][N];   // origins of the tiles in the stages
     const int t = threadIdx.x;
     const int nthr = blockDim.x;
     const int B = g.B;
@@ -130,9 +131,25 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
 #pragma unroll
     for (int n = 0; n < N; ++n) res2[n] = 0.f;
 
+    // Refill schedule. With nothing kept (pure streaming) a stage holds only the
+    // element tiles, so the same shared memory holds up to kMaxStages of them:
+    // the refills run nst - 1 tiles ahead, each issued before the current tile
+    // is awaited, and a second barrier per tile releases the stage. With a
+    // refold to compute, two full stages alternate: a tile's arithmetic covers
+    // one copy's latency and the refill goes out after the wait, whose barrier
+    // also releases the stage.
+    bool early = !output;
+#pragma unroll
+    for (int n = 0; n < N; ++n) early = early && sp[n] == 0;
+    const int xs_stride = (((N + 2) * B + 255) / 256) * 256;   // 1 KB multiples
+    int nst = 2, sstride = g.stage_floats;
+    if (early) {
+        nst = g.smem_floats / xs_stride;
+        nst = nst < kMaxStages ? nst : kMaxStages;
+        if (nst >= 2 && g.xs_off == 0) sstride = xs_stride; else nst = 2;
+    }
     if (t == 0) {
-        mbar_init(&full_bar[0], 1);
-        mbar_init(&full_bar[1], 1);
+        for (int i = 0; i < nst; ++i) mbar_init(&full_bar[i], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -146,7 +163,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
             if (++tc[n] < te[n]) break;
             tc[n] = (int)ts[n];
         }
-        float* stg = sm + st * g.stage_floats;
+        float* stg = sm + st * sstride;
         uint64_t* bar = &full_bar[st];
         mbar_expect_tx(bar, tx);
         int cx[N];
@@ -168,24 +185,17 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         }
     };
 
-    // Refill schedule. With nothing kept (pure streaming) the other stage is
-    // refilled before this tile's data is awaited, two copies in flight, at the
-    // cost of a second barrier per tile that releases the stage. With a refold
-    // to compute, a tile's arithmetic covers one copy's latency and the refill
-    // goes out after the wait, whose barrier also releases the stage.
-    bool early = !output;
-#pragma unroll
-    for (int n = 0; n < N; ++n) early = early && sp[n] == 0;
     bool failed = false;
-    if (t == 0 && ntile > 0) issue(0);
+    if (t == 0)
+        for (int i = 0; i < (early ? nst - 1 : 1) && i < ntile; ++i) issue(i);
     for (int64_t it = 0; it < ntile; ++it) {
-        const int st = (int)(it & 1);
-        const uint32_t par = (uint32_t)((it >> 1) & 1);
-        if (early && t == 0 && it + 1 < ntile) issue(st ^ 1);
+        const int st = (int)(it % nst);
+        const uint32_t par = (uint32_t)((it / nst) & 1);
+        if (early && t == 0 && it + nst - 1 < ntile) issue((int)((it + nst - 1) % nst));
         bool ok = mbar_wait_bounded(&full_bar[st], par, kWaitPolls);
         if (__syncthreads_or(!ok)) { failed = true; break; }
         if (!early && t == 0 && it + 1 < ntile) issue(st ^ 1);
-        float* stg = sm + st * g.stage_floats;
+        float* stg = sm + st * sstride;
         float* Xs = stg + g.xs_off;
         int o[N];
 #pragma unroll
@@ -358,8 +368,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         // a copy never arrived: record it and leave (the stage may still be written
         // by a straggling copy, so wait on both barriers once more, bounded)
         if (t == 0) {
-            mbar_wait_bounded(&full_bar[0], 0, kWaitPolls);
-            mbar_wait_bounded(&full_bar[1], 0, kWaitPolls);
+            for (int i = 0; i < nst; ++i) mbar_wait_bounded(&full_bar[i], 0, kWaitPolls);
             sc->status = -5;   // PASD_ERR_TIMEOUT
             sc->done = 1;
             __threadfence();
