@@ -20,8 +20,9 @@ serving (Poisson arrivals of planted cubes of sides 32-256 through
 pasd_submit / pasd_poll, served with the FP32 path and with mixed precision,
 both with the idle-start skip: solves/s, p50 / p99 latency, against the same
 requests solved one at a time with the plain FP32 path), video (loop bodies/s
-on the 144x176x3x300 colour-video shape, FP32 and mixed) and cpu_baseline (the
-FP64 oracle on the host cores, a bounded sample).
+on the 144x176x3x300 colour-video shape, FP32 and mixed), batched (64 uneven
+tensors, 8 of them hyperspectral-shaped, submitted at once) and cpu_baseline
+(the FP64 oracle on the host cores, a bounded sample).
 
 --impl reference times the FP64 oracle (the method as the paper defines it),
 each step one loop body on the same 200^3 workload.
@@ -280,6 +281,82 @@ def _serving(P, torch, ctx, args):
             "serial_ms_per_solve": [round(x, 2) for x in serial_ms], "generation_s": round(gen_s, 1)}
 
 
+def _batched(P, torch, ctx, args):
+    """The batched workload: 56 planted tensors with uneven sides (32-160 per mode)
+    and 8 hyperspectral-shaped 128x128x191 cubes, all 64 submitted at once through
+    pasd_submit (one stream per solve, overlapping on the GPU; one captured graph
+    per loop body), with the FP32 path and with mixed precision (both with the
+    idle-start skip), against the same solves run one at a time with the plain
+    FP32 path. Recovery error is against the planted low-rank part."""
+    import numpy as np
+    from paper_1712_09999_gb300 import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    specs = synth.batch_mix(seed=3)
+    tg = time.perf_counter()
+    probs = [synth.serving_problem(sp) for sp in specs]
+    gen_s = time.perf_counter() - tg
+    Ts = [torch.from_numpy(pr.T).to(dev) for pr in probs]
+    L0s = [torch.from_numpy(pr.L0).to(dev) for pr in probs]
+
+    serial_ms = []
+    for q, sp in enumerate(specs):
+        plan, _ = P.pasd_plan(ctx, P.make_params(sp.dims, sp.rank_bounds, max_iter=1000))
+        L = torch.empty_like(Ts[q])
+        E = torch.empty_like(Ts[q])
+        P.pasd_solve(plan, Ts[q], L, E)              # allocation, graph capture, warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.pasd_solve(plan, Ts[q], L, E)
+        e1.record()
+        torch.cuda.synchronize()
+        serial_ms.append(e0.elapsed_time(e1))
+        P.pasd_plan_destroy(plan)
+
+    def batch(precision):
+        plans, Ls, Es = [], [], []
+        for q, sp in enumerate(specs):
+            plan, _ = P.pasd_plan(ctx, P.make_params(sp.dims, sp.rank_bounds, max_iter=1000,
+                                                     precision=precision, flags=P.F_SKIP_IDLE))
+            L = torch.empty_like(Ts[q])
+            E = torch.empty_like(Ts[q])
+            P.pasd_solve(plan, Ts[q], L, E)          # allocation, graph capture, warm-up
+            plans.append(plan)
+            Ls.append(L)
+            Es.append(E)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pending = {P.pasd_submit(ctx, plans[q], Ts[q], Ls[q], Es[q]): q for q in range(len(specs))}
+        bad, iters, skipped = 0, [0] * len(specs), [0] * len(specs)
+        while pending:
+            for tk in list(pending):
+                st, r = P.pasd_poll(ctx, tk)
+                if st != P.PENDING:
+                    q = pending.pop(tk)
+                    bad += st not in (P.OK, P.NOT_CONVERGED)
+                    iters[q], skipped[q] = int(r.iters), int(r.skipped)
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        rse = [float(torch.linalg.vector_norm(Ls[q].double() - L0s[q]) / torch.linalg.vector_norm(L0s[q]))
+               for q in range(len(specs))]
+        for plan in plans:
+            P.pasd_plan_destroy(plan)
+        return {"solves_per_s": len(specs) / wall, "wall_s": wall, "failed": bad,
+                "rse_median": float(np.median(rse)), "rse_max": max(rse),
+                "iters_total": sum(iters), "skipped_total": sum(skipped)}, Ls
+
+    fp32, l32 = batch(P.PREC_FP32)
+    mixed, lmx = batch(P.PREC_MIXED)
+    mixed["L_rel_vs_fp32_max"] = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+                                     for a, b in zip(lmx, l32))
+    return {"workload": "56 planted tensors (sides U{32..160} per mode, Tucker 3-15, R = floor(1.2 r), 5-30% "
+                        "additive corruption) + 8 hyperspectral 128x128x191 (spatial rank 3-15, spectral rank 4, "
+                        "5-30% salt and pepper), seed 3; all submitted at once",
+            "solves": len(specs), "fp32": fp32, "mixed": mixed,
+            "serial_plain_fp32_solves_per_s": len(specs) / (sum(serial_ms) / 1000.0),
+            "generation_s": round(gen_s, 1)}
+
+
 def _video(P, torch, ctx, args):
     """Loop bodies per second on the colour-video shape 144x176x3x300, R = (20, 20, 3, 5),
     the paper's default lambda_n, timed over a fixed number of bodies past the activation."""
@@ -435,6 +512,8 @@ def run_ours(args):
         line["serving"] = _serving(P, torch, ctx, args)
     if rank == 0 and not args.no_video:
         line["video"] = _video(P, torch, ctx, args)
+    if rank == 0 and not args.no_batched:
+        line["batched"] = _batched(P, torch, ctx, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, el = _oracle_iters_per_s(pr.T, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -452,8 +531,8 @@ def run_ours(args):
 def run_profile_workload(args):
     """For ncu: plan the 200^3 workload, run `pre` loop bodies, then `iters` more, exit.
     Launch order per body: polar, A-pass (one launch per group of modes with the
-    same padded rank), SVT, Vrot, fused pass, finalize; pasd_begin launches 3
-    kernels first."""
+    same padded rank), SVT, Vrot, fused pass, M-pass, finalize; pasd_begin
+    launches 3 kernels first. --mixed plans it with mixed precision."""
     import torch
     import __graft_entry__ as ge
     ge.build()
@@ -464,7 +543,8 @@ def run_profile_workload(args):
     T = torch.from_numpy(pr.T).cuda()
     ctx = P.pasd_ctx_create(0)
     plan, _ = P.pasd_plan(ctx, P.make_params(DIMS, RANKS, alpha=ALPHA, lam=LAMBDA,
-                                             stop=P.STOP_FIXED_ITERS, max_iter=args.pre + args.iters + 1))
+                                             stop=P.STOP_FIXED_ITERS, max_iter=args.pre + args.iters + 1,
+                                             precision=P.PREC_MIXED if args.mixed else P.PREC_FP32))
     P.pasd_begin(plan, T)
     P.pasd_iterate(plan, args.pre)
     P.pasd_iterate(plan, args.iters)
@@ -481,6 +561,7 @@ def main():
                     help="run loop bodies of the 200^3 workload for an external profiler and exit")
     ap.add_argument("--pre", type=int, default=120)
     ap.add_argument("--iters", type=int, default=2)
+    ap.add_argument("--mixed", action="store_true", help="--profile-workload with mixed precision")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
@@ -494,6 +575,7 @@ def main():
     ap.add_argument("--serve-problems", type=int, default=8)
     ap.add_argument("--serve-slots", type=int, default=3, help="plans per problem")
     ap.add_argument("--no-video", action="store_true", help="skip the video-shape measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload measurement")
     ap.add_argument("--video-pre", type=int, default=150)
     ap.add_argument("--video-iters", type=int, default=200)
     args = ap.parse_args()

@@ -107,13 +107,14 @@ def random_tensor(dims, seed: int, dtype=np.float32) -> np.ndarray:
 
 @dataclass
 class RequestSpec:
-    """One served solve: a planted cube with its solver rank bounds."""
+    """One served solve: a planted tensor with its solver rank bounds."""
 
     dims: tuple
     tucker: tuple
     rank_bounds: tuple
     rho: float
     seed: int
+    kind: str = "planted"    # "planted" (additive) or "hyperspectral" (salt and pepper)
 
 
 def serving_mix(n: int, seed: int = 4, side_lo: int = 32, side_hi: int = 256) -> list:
@@ -135,7 +136,52 @@ def serving_mix(n: int, seed: int = 4, side_lo: int = 32, side_hi: int = 256) ->
 
 
 def serving_problem(spec: RequestSpec) -> Problem:
+    if spec.kind == "hyperspectral":
+        return hyperspectral(spec.dims, spec.tucker, spec.rho, spec.seed)
     return planted(spec.dims, spec.tucker, spec.rho, spec.seed, scale="max", amp=1.0)
+
+
+def hyperspectral(dims, tucker_ranks, rho: float, seed: int) -> Problem:
+    """Hyperspectral-shaped image cube (rows, columns, bands): a Tucker low-rank
+    tensor min-max scaled to [0, 1], with exactly floor(rho D) entries (drawn
+    without replacement) replaced by 0 or 1 with probability 1/2 each
+    (salt-and-pepper noise); E0 = T - L0."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dims = tuple(int(d) for d in dims)
+    l0 = tucker_tensor(rng, dims, tucker_ranks)
+    lo, hi = float(l0.min()), float(l0.max())
+    l0 = (l0 - lo) / (hi - lo) if hi > lo else np.zeros_like(l0)
+    total = int(np.prod(dims))
+    count = int(np.floor(rho * total))
+    support = rng.choice(total, size=count, replace=False) if count else np.zeros(0, np.int64)
+    x = l0.reshape(-1).copy()
+    x[support] = rng.integers(0, 2, size=count).astype(np.float64)
+    x = x.reshape(dims)
+    desc = f"hyperspectral tucker{tuple(tucker_ranks)} dims{dims} rho={rho} seed={seed}"
+    return Problem(T=x.astype(np.float32), L0=l0, E0=x - l0, support=np.sort(support), desc=desc)
+
+
+def batch_mix(seed: int = 3, n_random: int = 56, n_hyper: int = 8) -> list:
+    """The batched workload: `n_random` planted tensors with every side drawn
+    uniformly on {32, ..., 160}, Tucker rank r_n uniform on {3, ..., 15}, additive
+    U[-1,1] max|L0| corruption on a fraction uniform on [0.05, 0.30]; plus
+    `n_hyper` hyperspectral-shaped 128 x 128 x 191 cubes (spatial ranks uniform on
+    {3, ..., 15}, spectral rank 4, salt-and-pepper fraction uniform on [0.05, 0.30]).
+    Rank bounds floor(1.2 r_n), at most the side."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for q in range(n_random):
+        dims = tuple(int(rng.integers(32, 161)) for _ in range(3))
+        tucker = tuple(int(rng.integers(3, 16)) for _ in range(3))
+        bounds = tuple(min(d, int(np.floor(1.2 * r))) for d, r in zip(dims, tucker))
+        out.append(RequestSpec(dims, tucker, bounds, float(rng.uniform(0.05, 0.30)), 3000 + seed * 100 + q))
+    for q in range(n_hyper):
+        tucker = (int(rng.integers(3, 16)), int(rng.integers(3, 16)), 4)
+        dims = (128, 128, 191)
+        bounds = tuple(min(d, int(np.floor(1.2 * r))) for d, r in zip(dims, tucker))
+        out.append(RequestSpec(dims, tucker, bounds, float(rng.uniform(0.05, 0.30)), 4000 + seed * 100 + q,
+                               kind="hyperspectral"))
+    return out
 
 
 def poisson_arrivals(rate: float, count: int, seed: int = 5) -> np.ndarray:
