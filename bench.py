@@ -21,8 +21,11 @@ pasd_submit / pasd_poll, served with the FP32 path and with mixed precision,
 both with the idle-start skip: solves/s, p50 / p99 latency, against the same
 requests solved one at a time with the plain FP32 path), video (loop bodies/s
 on the 144x176x3x300 colour-video shape, FP32 and mixed), batched (64 uneven
-tensors, 8 of them hyperspectral-shaped, submitted at once) and cpu_baseline
-(the FP64 oracle on the host cores, a bounded sample).
+tensors, 8 of them hyperspectral-shaped, submitted at once), table1 (the
+paper's Table 1 workloads, 100^3 and 50^4, with the paper's own PASD results as
+context) and cpu_baseline (the FP64 oracle on the host cores, a bounded
+sample). Opt-in: --sweep (solve time against cube size) and --phase (the
+phase-transition map of the paper's Fig. 1 setting).
 
 --impl reference times the FP64 oracle (the method as the paper defines it),
 each step one loop body on the same 200^3 workload.
@@ -357,6 +360,129 @@ def _batched(P, torch, ctx, args):
             "generation_s": round(gen_s, 1)}
 
 
+# PASD's own results in the paper's Table 1 (RSE, seconds per solve; Matlab 8.1 on an
+# Intel Xeon E5-2620 at 2.0 GHz, averages over its own random tensors): context only.
+PAPER_TABLE1 = {("100^3", 0.05): (1.12e-7, 54.89), ("100^3", 0.10): (1.28e-7, 55.95),
+                ("100^3", 0.20): (1.44e-7, 57.65), ("50^4", 0.05): (2.99e-3, 469.46),
+                ("50^4", 0.10): (8.33e-3, 483.37), ("50^4", 0.20): (4.27e-2, 544.28)}
+
+
+def _table1(P, torch, ctx, args):
+    """The paper's Table 1 workloads: 100^3 and 50^4, Tucker rank 10, R_n = 12,
+    U[-1,1] additive corruption on 5/10/20% of entries, paper-default lambda_n,
+    Algorithm 1's stop test with eps = 1e-5, at most 1000 bodies; one solve each
+    (plain FP32 path), time per solve by CUDA events, recovery error."""
+    from paper_1712_09999_gb300 import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rows = []
+    for name, dims in (("100^3", (100,) * 3), ("50^4", (50,) * 4)):
+        for rho in (0.05, 0.10, 0.20):
+            pr = synth.table1(dims, rho, seed=7)
+            T = torch.from_numpy(pr.T).to(dev)
+            L0 = torch.from_numpy(pr.L0).to(dev)
+            plan, _ = P.pasd_plan(ctx, P.make_params(dims, (12,) * len(dims), tol=1e-5, max_iter=1000))
+            L = torch.empty_like(T)
+            E = torch.empty_like(T)
+            P.pasd_solve(plan, T, L, E)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = P.pasd_solve(plan, T, L, E)
+            e1.record()
+            torch.cuda.synchronize()
+            P.pasd_plan_destroy(plan)
+            rse = float(torch.linalg.vector_norm(L.double() - L0) / torch.linalg.vector_norm(L0))
+            prse, psec = PAPER_TABLE1[(name, rho)]
+            rows.append({"size": name, "rho": rho, "iters": int(r.iters), "status": int(r.status),
+                         "ms_per_solve": round(e0.elapsed_time(e1), 2), "rse": rse,
+                         "paper_rse": prse, "paper_s_per_solve": psec})
+    return {"workload": "Table 1 family: Tucker rank 10, R_n = 12, U[-1,1] additive corruption, paper lambda_n, "
+                        "eps = 1e-5 (seed 7)", "paper_hardware": "Matlab 8.1, Intel Xeon E5-2620 2.0 GHz (context only)",
+            "rows": rows}
+
+
+def _sweep(P, torch, ctx, args):
+    """Solve time against cube size (Tucker rank 10, R_n = 12, 10% U[-1,1]
+    corruption, paper-default lambda_n, eps = 1e-5), inputs generated on the GPU."""
+    from paper_1712_09999_gb300 import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rows = []
+    for side in args.sweep_sides:
+        T, L0 = synth.planted_device((side,) * 3, (10,) * 3, 0.10, 11, dev)
+        plan, footprint = P.pasd_plan(ctx, P.make_params(T.shape, (12,) * 3, tol=1e-5, max_iter=1000))
+        L = torch.empty_like(T)
+        E = torch.empty_like(T)
+        P.pasd_solve(plan, T, L, E)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = P.pasd_solve(plan, T, L, E)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        P.pasd_plan_destroy(plan)
+        rse = float(torch.linalg.vector_norm(L.double() - L0.double()) / torch.linalg.vector_norm(L0.double()))
+        rows.append({"side": side, "iters": int(r.iters), "ms_per_solve": round(ms, 2),
+                     "us_per_body": round(1000 * ms / max(1, r.iters), 1), "rse": rse,
+                     "footprint_gb": round(footprint / 1e9, 2)})
+        del T, L0, L, E
+        torch.cuda.empty_cache()
+    return {"workload": "cubes, Tucker rank 10, R_n = 12, 10% U[-1,1] corruption, paper lambda_n, eps = 1e-5, "
+                        "generated on the GPU (seed 11)", "rows": rows}
+
+
+def _phase(P, torch, ctx, args):
+    """Phase-transition map on 100^3 (the paper's Fig. 1 setting with this
+    repository's random streams): Tucker rank r = 2..50 step 2 (R_n = floor(1.2 r)),
+    corruption fraction 2..50% step 2 (U[-1,1] additive), `phase_trials` trials per
+    cell, success when the recovery error is at most 1e-3. Solves run through
+    pasd_submit, `phase_slots` at a time per rank, with the idle-start skip."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1712_09999_gb300 import synth
+    ranks = list(range(2, 51, 2))
+    rhos = [k / 100 for k in range(2, 51, 2)]
+    grid = []
+    t0 = time.perf_counter()
+    n_solves = 0
+    for r in ranks:
+        R = int(1.2 * r)
+        slots = []
+        for _ in range(args.phase_slots):
+            plan, _ = P.pasd_plan(ctx, P.make_params((100,) * 3, (R,) * 3, tol=1e-5, max_iter=1000,
+                                                     flags=P.F_SKIP_IDLE))
+            slots.append((plan, torch.empty((100,) * 3, device=dev), torch.empty((100,) * 3, device=dev)))
+        jobs = [(rho, tr) for rho in rhos for tr in range(args.phase_trials)]
+        ok = {rho: 0 for rho in rhos}
+        free = list(range(len(slots)))
+        pending = {}
+        k = 0
+        while k < len(jobs) or pending:
+            while free and k < len(jobs):
+                rho, tr = jobs[k]
+                T, L0 = synth.planted_device((100,) * 3, (r,) * 3, rho, 100000 + 1000 * r + 10 * int(rho * 100) + tr, dev)
+                torch.cuda.current_stream().synchronize()   # the solve's own stream reads T
+                sl = free.pop()
+                plan, L, E = slots[sl]
+                pending[P.pasd_submit(ctx, plan, T, L, E)] = (sl, rho, T, L0)
+                k += 1
+            for tk in list(pending):
+                st, _ = P.pasd_poll(ctx, tk)
+                if st != P.PENDING:
+                    sl, rho, T, L0 = pending.pop(tk)
+                    L = slots[sl][1]
+                    rse = float(torch.linalg.vector_norm(L.double() - L0.double()) / torch.linalg.vector_norm(L0.double()))
+                    ok[rho] += int(st in (P.OK, P.NOT_CONVERGED) and rse <= 1e-3)
+                    free.append(sl)
+                    n_solves += 1
+            time.sleep(0.0001)
+        for plan, _, _ in slots:
+            P.pasd_plan_destroy(plan)
+        grid.append([ok[rho] / args.phase_trials for rho in rhos])
+    return {"workload": "100^3, Tucker rank r = 2..50 step 2 (R = floor(1.2 r)), corruption 2..50% step 2, "
+                        f"{args.phase_trials} trials per cell, success: RSE <= 1e-3", "ranks": ranks,
+            "rhos": rhos, "success": grid, "solves": n_solves, "seconds": round(time.perf_counter() - t0, 1)}
+
+
 def _video(P, torch, ctx, args):
     """Loop bodies per second on the colour-video shape 144x176x3x300, R = (20, 20, 3, 5),
     the paper's default lambda_n, timed over a fixed number of bodies past the activation."""
@@ -514,6 +640,12 @@ def run_ours(args):
         line["video"] = _video(P, torch, ctx, args)
     if rank == 0 and not args.no_batched:
         line["batched"] = _batched(P, torch, ctx, args)
+    if rank == 0 and not args.no_table1:
+        line["table1"] = _table1(P, torch, ctx, args)
+    if rank == 0 and args.sweep:
+        line["sweep"] = _sweep(P, torch, ctx, args)
+    if rank == 0 and args.phase:
+        line["phase"] = _phase(P, torch, ctx, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, el = _oracle_iters_per_s(pr.T, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -576,6 +708,12 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=3, help="plans per problem")
     ap.add_argument("--no-video", action="store_true", help="skip the video-shape measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload measurement")
+    ap.add_argument("--no-table1", action="store_true", help="skip the paper's Table 1 workloads")
+    ap.add_argument("--sweep", action="store_true", help="solve time against cube size")
+    ap.add_argument("--sweep-sides", type=int, nargs="+", default=[100, 200, 300, 400, 500, 600, 800])
+    ap.add_argument("--phase", action="store_true", help="phase-transition map on 100^3")
+    ap.add_argument("--phase-trials", type=int, default=2)
+    ap.add_argument("--phase-slots", type=int, default=16)
     ap.add_argument("--video-pre", type=int, default=150)
     ap.add_argument("--video-iters", type=int, default=200)
     args = ap.parse_args()

@@ -154,7 +154,9 @@ pasd_status pasd_solve_host(pasd_plan_t* plan, const float* T_host, float* L_hos
  * tensors T, L, E; the caller keeps them alive and untouched until pasd_poll
  * returns something other than PASD_PENDING. A solve is admitted when its
  * plan's footprint fits the context's HBM budget; admitted solves advance
- * together, each on its own stream, and retire as they converge.
+ * together, each on its own stream, and retire as they converge. The solve's
+ * stream is not ordered after any stream of the caller: T must be fully
+ * written (its producing stream synchronised) before pasd_submit is called.
  * One plan serves one solve at a time. Errors: BUSY when the queue is full. */
 pasd_status pasd_submit(pasd_ctx* ctx, pasd_plan_t* plan, const float* T, float* L,
                         float* E, uint64_t* ticket);

@@ -237,3 +237,29 @@ def video(height: int = 144, width: int = 176, frames: int = 300, seed: int = 2,
     support = np.flatnonzero(e0.reshape(-1) != 0)
     desc = f"video {height}x{width}x3x{frames} rect={n_rect} coverage={coverage} seed={seed}"
     return Problem(T=t.astype(np.float32), L0=l0, E0=e0, support=support, desc=desc)
+
+
+def planted_device(dims, tucker_ranks, rho: float, seed: int, device, amp: float = 1.0):
+    """planted(..., scale="none") generated on a CUDA device with torch (for sizes and
+    counts the host generator is too slow for): Haar factors (QR of a Gaussian matrix,
+    columns times sign(diag R)), N(0,1) core, exactly floor(rho D) positions drawn
+    without replacement carrying U[-amp, amp]. Returns (T float32, L0 float32) on
+    `device`; a different random stream from planted() for the same seed."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    dims = tuple(int(d) for d in dims)
+    core = torch.randn(*tucker_ranks, generator=g, device=device, dtype=torch.float64)
+    l0 = core
+    for n, (i_n, r_n) in enumerate(zip(dims, tucker_ranks)):
+        q, r = torch.linalg.qr(torch.randn(i_n, r_n, generator=g, device=device, dtype=torch.float64))
+        q = q * torch.sign(torch.diagonal(r)).unsqueeze(0)
+        l0 = torch.movedim(torch.tensordot(q, l0, dims=([1], [n])), 0, n)    # mode-n product
+    l0 = l0.to(torch.float32).contiguous()
+    total = l0.numel()
+    count = int(rho * total)
+    t = l0.clone().reshape(-1)
+    if count:
+        idx = torch.randperm(total, generator=g, device=device)[:count]
+        t[idx] += (torch.rand(count, generator=g, device=device) * 2 - 1) * amp
+    return t.reshape(dims), l0
