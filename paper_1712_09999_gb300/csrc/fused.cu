@@ -253,7 +253,9 @@ __global__ void __launch_bounds__(FU_THREADS, 1) fused_kernel(FusedArgs fa) {
         // ---- stage Wz rows and A columns ----
 #pragma unroll
         for (int n = 0; n < N; ++n) {
-            const int Rp = g.Rp[n], R4 = Rp / 4;
+            // only the first round4(kept) rows of Vrot_n are current (the rest are zero
+            // or left from an earlier body): stage and multiply those
+            const int Rp = g.Rp[n], R4 = (sc->kept[n] + 3) >> 2;
             float* Ws = sm + g.ws_off[n];
             for (int idx = t; idx < g.b[n] * R4; idx += FU_THREADS) {
                 int l = idx / R4, r4 = idx % R4;
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1) fused_kernel(FusedArgs fa) {
         if (active) {
 #pragma unroll
             for (int n = 0; n < N; ++n) {
-                const int Rp = g.Rp[n], R4 = Rp / 4, ald = Rp + 4;
+                const int Rp = g.Rp[n], R4 = (sc->kept[n] + 3) >> 2, ald = Rp + 4;
                 const float* Ws = sm + g.ws_off[n];
                 const float* As = sm + g.as_off[n];
                 if (n == N - 1) {

@@ -759,6 +759,10 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     const VrotMode& m = va.m[k];
     const int R = m.R, Rp = m.Rp;
     const int s = sc->kept[k];
+    // consumers read the first round4(s) rows only (rows s .. round4(s) - 1 are
+    // zero); with nothing kept there is nothing to write
+    const int s4 = (s + 3) & ~3;
+    if (s4 == 0) return;
     __shared__ float Wt[PASD_MAXR * PASD_MAXR];   // Wt[i][r] = F_i W[r][i]
     for (int idx = threadIdx.x; idx < s * R; idx += blockDim.x) {
         int i = idx / R, r = idx % R;
@@ -798,12 +802,12 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     if (m.post == 1) {
 #pragma unroll
         for (int i4 = 0; i4 < RB / 4; ++i4)
-            if (4 * i4 < Rp)
+            if (4 * i4 < s4)
                 reinterpret_cast<float4*>(dst)[i4] = make_float4(out[4 * i4], out[4 * i4 + 1], out[4 * i4 + 2], out[4 * i4 + 3]);
     } else {
 #pragma unroll
         for (int i = 0; i < RB; ++i)
-            if (i < Rp) dst[(int64_t)i * m.post] = out[i];
+            if (i < s4) dst[(int64_t)i * m.post] = out[i];
     }
 }
 
