@@ -381,20 +381,18 @@ __global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
         float4* red4 = reinterpret_cast<float4*>(red);
         for (int w = t; w < nf4 * G; w += blockDim.x) {
             const int f = w % nf4, g = w / nf4;
+            // batches of 16 loads, the last one predicated (absent partials read as
+            // zero, which leaves the in-order sums unchanged), so no load waits on an add
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            int p = g;
-            for (; p + 15 * G < m.n_gram; p += 16 * G) {
+            for (int p = g; p < m.n_gram; p += 16 * G) {
                 float4 v[16];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) v[u] = part[(size_t)(p + u * G) * nf4 + f];
+                for (int u = 0; u < 16; ++u)
+                    v[u] = p + u * G < m.n_gram ? part[(size_t)(p + u * G) * nf4 + f] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     acc.x += v[u].x; acc.y += v[u].y; acc.z += v[u].z; acc.w += v[u].w;
                 }
-            }
-            for (; p < m.n_gram; p += G) {
-                const float4 v = part[(size_t)p * nf4 + f];
-                acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
             }
             red4[g * nf4 + f] = acc;
         }
@@ -629,15 +627,15 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(FinalizeArgs fa) 
             const int64_t stride = fa.I[mode] * fa.Rp[mode];
             const float* src = fa.mp_part[mode] + i * fa.Rp[mode] + r;
             const int np = fa.n_mp[mode];
-            int p = h;
-            for (; p + 60 < np; p += 64) {          // 16 loads in flight, added in order
-                float v[16];
+            const float* sp = src + (int64_t)h * stride;
+            const int64_t st4 = 4 * stride;
+            for (int p = h; p < np; p += 16, sp += 4 * st4) {   // 4 loads in flight (absent ones read as 0), added in order
+                float v[4];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) v[u] = src[(int64_t)(p + 4 * u) * stride];
+                for (int u = 0; u < 4; ++u) v[u] = p + 4 * u < np ? sp[u * st4] : 0.f;
 #pragma unroll
-                for (int u = 0; u < 16; ++u) acc += v[u];
+                for (int u = 0; u < 4; ++u) acc += v[u];
             }
-            for (; p < np; p += 4) acc += src[(int64_t)p * stride];
         }
         sub[h][ol] = acc;
         __syncthreads();
