@@ -68,7 +68,7 @@ void launch_apass(const ApassArgs& a, cudaStream_t s);
 
 // TMA-fed A-pass (post % 4 == 0, or post == 1 with I % 4 == 0): one launch per
 // group of modes with the same padded rank; one CTA per task (column block).
-constexpr int AT_STAGES = 3;
+constexpr int AT_STAGES = 2;
 struct ApassTmaMode {
     int64_t I, pre, post, P;
     int BN;                // columns per task
