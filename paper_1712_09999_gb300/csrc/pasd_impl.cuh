@@ -38,6 +38,7 @@ struct DevScalars {
     double res_inf, res_fro_rel, objective, l1_E, mu_used;
     int32_t nonfinite;
     int32_t skipped;       // idle loop bodies replaced by their closed form
+    int32_t w_ident[PASD_MAXN];   // 1: the last SVT's eigenbasis W_n is exactly I (Urot = U)
 };
 
 struct ModeGeom {

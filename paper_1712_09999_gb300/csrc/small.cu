@@ -425,14 +425,18 @@ __global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
         m.sigma[t] = sig;
         m.F[t] = f;
     }
+    int moved = 0;
     for (int idx = t; idx < Rp * Rp; idx += blockDim.x) {
         const int i = idx / Rp, j = idx % Rp;
         const bool in = i < R && j < R;
         const float v = in ? Ve[i * ld + perm[j]] : (i == j ? 1.f : 0.f);
         m.W[idx] = v;
         Smat[i * ld + j] = in ? v : 0.f;
+        moved |= v != (i == j ? 1.f : 0.f);
     }
-    __syncthreads();
+    // W exactly I (no rotation, order unchanged): Urot = U W below is an exact copy of U
+    const int ident = !__syncthreads_or(moved);
+    if (t == 0) sc->w_ident[blockIdx.x] = ident;
     if (t < 32) {
         double nuc = 0.0;
         int kept = 0;
@@ -491,6 +495,13 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
     const int q = R - s;
     const int s4 = (s + 3) & ~3, q4 = (q + 3) & ~3;
 
+    if (s == 0 && sc->w_ident[blockIdx.x]) {
+        // Nothing kept and the last SVT left the basis exactly as it was (W = I, so
+        // Urot = U): Eq. 10 with M_n = 0 and every direction in the null space
+        // returns the polar factor of U, which is U itself (a previous U-step's
+        // orthonormal output, or eye at the start). U stays as it is.
+        return;
+    }
     if (s == 0) {
         // Nothing kept: the polar factor of Urot = U W. U and W are orthogonal to
         // rounding, so Urot^T Urot = I + O(1e-6) and one Newton-Schulz step gives
@@ -867,7 +878,7 @@ __global__ void init_kernel(InitArgs a) {
         sc->status = 2;
         sc->nonfinite = 0;
         sc->skipped = 0;
-        for (int m = 0; m < PASD_MAXN; ++m) { sc->kept[m] = 0; sc->nuclear[m] = 0.0; }
+        for (int m = 0; m < PASD_MAXN; ++m) { sc->kept[m] = 0; sc->nuclear[m] = 0.0; sc->w_ident[m] = 1; }
         sc->res_inf = sc->res_fro_rel = sc->objective = sc->l1_E = 0.0;
         sc->mu_used = a.mu0;
     }

@@ -58,6 +58,15 @@ def _oracle(T, ranks, stop, max_iter, lam_pair=None):
     return O.pasd(T, p)
 
 
+def _stop_tie(ref, g_iters, tol, tmax):
+    # The stop test compares a residual formed from FP32-stored tensors with tol.
+    # When the oracle's residual at the earlier of the two stopping bodies lies
+    # within FP32 rounding of tol (a few units of 2^-24 max|T|), stopping at
+    # either body is correct: a tie, like a singular value equal to tau.
+    k = min(g_iters, ref.iters)
+    return abs(g_iters - ref.iters) == 1 and abs(ref.trace[k - 1].res_inf - tol) <= 4 * 2.0 ** -24 * tmax
+
+
 def _check_parity(g, ref, n_modes):
     gk = g["trace"][:, 5:5 + n_modes].astype(int).tolist()
     rk = [s.kept for s in ref.trace]
@@ -122,17 +131,23 @@ def test_video_shape_matches_oracle(env):
     # after every body already moves E by 4e-5 relative
     # (tests/test_oracle_pins.py::test_fp32_state_floor_dense_sparse_part), so E is
     # held to 1e-4, the FP32 storage floor of this workload.
+    # A stop one body apart is accepted only as a tie (_stop_tie), and L, E are
+    # then compared with the oracle run to the GPU's stopping body.
     pr = synth.video(height=36, width=44, frames=40, n_rect=4, seed=3)
     ranks = (10, 10, 3, 5)
     for stop, iters in ((2, 150), (0, 1000)):
         ref = _oracle(pr.T, ranks, stop, iters)
         g = _gpu_solve(env, pr.T, ranks, stop, iters)
+        if stop == 0:
+            assert ref.converged and g["res"].status == 0
+            if g["res"].iters != ref.iters:
+                assert _stop_tie(ref, g["res"].iters, 1e-5, float(np.abs(pr.T).max()))
+                ref = _oracle(pr.T, ranks, 2, g["res"].iters)
         gk = g["trace"][:, 5:9].astype(int).tolist()
         assert g["res"].iters == ref.iters
         assert gk == [s.kept for s in ref.trace]
         assert _rel(g["L"], ref.L) <= TOL
         assert _rel(g["E"], ref.E) <= 1e-4
-    assert ref.converged
     assert abs(O.rse(g["L"], pr.L0) - O.rse(ref.L, pr.L0)) <= 1e-4
 
 
