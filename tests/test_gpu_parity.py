@@ -119,6 +119,17 @@ def test_shapes_match_oracle(env, dims, tucker, ranks):
     _check_parity(g, ref, len(dims))
 
 
+def test_hyperspectral_shape_matches_oracle(env):
+    # Hyperspectral-shaped cube (rows, columns, bands) with salt-and-pepper noise
+    # (entries replaced by 0 or 1) and an odd band count (19, padded to 20 inside
+    # the solver): kept counts per iteration, stopping body, L and E.
+    pr = synth.hyperspectral((24, 20, 19), (3, 3, 2), 0.10, 31)
+    ref = _oracle(pr.T, (4, 4, 3), 0, 1000)
+    g = _gpu_solve(env, pr.T, (4, 4, 3), 0, 1000)
+    _check_parity(g, ref, 3)
+    assert abs(O.rse(g["L"], pr.L0) - O.rse(ref.L, pr.L0)) <= 1e-4
+
+
 def test_video_shape_matches_oracle(env):
     # Colour-video-shaped tensor (height, width, channel, frame) at reduced size:
     # rank-1 background in the frame mode, moving rectangles replacing ~4% of the
@@ -421,18 +432,23 @@ def test_stepwise_and_host_paths_equal_solve(env):
     P.pasd_plan_destroy(plan)
 
 
-def test_served_results_equal_alone(env):
+@pytest.mark.parametrize("mode", ["fp32", "fp32_skip", "mixed_skip"])
+def test_served_results_equal_alone(env, mode):
     # Continuous batching: solves submitted together overlap on the device; each
-    # result equals the same solve run alone.
+    # result equals the same solve run alone (FP32, FP32 with the idle-start skip,
+    # mixed precision with the skip).
     torch, P, ctx = env
+    prec = P.PREC_MIXED if mode.startswith("mixed") else P.PREC_FP32
+    flags = P.F_SKIP_IDLE if mode.endswith("skip") else 0
     probs = [synth.planted(d, (3, 3, 3), 0.1, 20 + i, scale="std", amp=5.0)
              for i, d in enumerate([(32, 30, 28), (40, 24, 36), (28, 28, 28), (50, 20, 30)])]
-    plans, alone, bufs = [], [], []
+    plans, alone, bufs, skipped = [], [], [], []
     for pr in probs:
-        plan, _ = P.pasd_plan(ctx, P.make_params(pr.T.shape, (4, 4, 4), max_iter=1000))
+        plan, _ = P.pasd_plan(ctx, P.make_params(pr.T.shape, (4, 4, 4), max_iter=1000, precision=prec, flags=flags))
         Td = torch.from_numpy(pr.T).cuda()
         L = torch.empty_like(Td); E = torch.empty_like(Td)
-        P.pasd_solve(plan, Td, L, E)
+        r0 = P.pasd_solve(plan, Td, L, E)
+        skipped.append(r0.skipped)
         alone.append((L.clone(), E.clone()))
         L.zero_(); E.zero_()
         plans.append(plan)
@@ -455,6 +471,7 @@ def test_served_results_equal_alone(env):
         st, r = results[t]
         assert st == P.OK
         assert r.latency_s > 0
+        assert r.skipped == skipped[i] and (skipped[i] > 0) == bool(flags)
         assert torch.equal(bufs[i][1], alone[i][0]) and torch.equal(bufs[i][2], alone[i][1])
     for plan in plans:
         P.pasd_plan_destroy(plan)
