@@ -13,8 +13,9 @@ converging iterations are all in it, inputs resident in HBM. The tensors the
 loop streams (T, E, G_1..G_3: 160 MB) exceed the 129 MB L2, so no L2 flush is
 added between steps.
 
-Extra keys: roofline of the dominant kernel (CUDA-event duration of the fused
-elementwise pass vs its algorithmic bytes), clocks sampled during the timed
+Extra keys: roofline of the dominant kernel (algorithmic bytes of the fused
+elementwise pass over its CUDA-event durations, every launch of one solve, with
+the idle and active bodies also reported apart), clocks sampled during the timed
 region, e2e (whole solves through pasd_solve_host with pinned host buffers),
 serving (Poisson arrivals of planted cubes of sides 32-256 through
 pasd_submit / pasd_poll, served with the FP32 path and with mixed precision,
@@ -76,15 +77,16 @@ def _fused_src_hash():
 
 
 def _fused_traffic():
-    """dram bytes per fused-pass launch from the committed ncu summary, if the
-    kernel sources still match the ones that were profiled; else None."""
+    """DRAM bytes of one fused-pass launch in an idle body and in an active body,
+    from the committed ncu summary, if the kernel sources still match the ones
+    that were profiled; else (None, None)."""
     p = os.path.join(ROOT, "profiles", "fused_pass_200cube_traffic.json")
     if not os.path.exists(p):
-        return None
+        return None, None
     d = json.load(open(p))
     if _fused_src_hash() != d.get("fused_src_sha256"):
-        return None
-    return d.get("traffic_bytes_per_launch")
+        return None, None
+    return d.get("traffic_bytes_idle_launch"), d.get("traffic_bytes_active_launch")
 
 
 class ClockSampler:
@@ -587,29 +589,41 @@ def run_ours(args):
         ms = float(t.item())
     value = world * args.steps / (ms / 1000.0)
 
-    # dominant kernel: per-kernel CUDA-event durations over active-phase bodies
+    # dominant kernel: per-kernel CUDA-event durations for every body of one solve,
+    # i.e. the trajectory the timed region replays (idle and active bodies alike)
     P.pasd_begin(plan, T, stream)
-    P.pasd_iterate(plan, max(0, k_conv - 60), stream)
-    k0 = max(0, k_conv - 60)
-    prof = P.pasd_profile_iterations(plan, 30, stream)
-    fused_ms = prof["fused"] / 30
+    per_body = [P.pasd_profile_iterations(plan, 1, stream) for _ in range(k_conv)]
     D = int(np.prod(DIMS))
     N = len(DIMS)
-    # algorithmic bytes of one fused pass: read T, E, G_1..G_N, write E, G_1..G_N,
-    # read the kept rows of each Vrot_n once (mean kept count over the profiled bodies)
-    tr = np.zeros((k0 + 30, P.TRACE_STRIDE))
+    tr = np.zeros((k_conv, P.TRACE_STRIDE))
     P.pasd_state_get(plan, P.STATE_TRACE, 0, tr)
-    kept_mean = tr[k0:, 5:5 + N].mean(axis=0)
-    alg_bytes = (2 * N + 3) * 4 * D + 4 * sum(float(s) * (D // I) for s, I in zip(kept_mean, DIMS))
+    kept = tr[:, 5:5 + N]
+    # algorithmic bytes of one fused pass: read T, E, G_1..G_N, write E, G_1..G_N,
+    # read the kept rows of each Vrot_n once (kept counts of that body)
+    alg = np.array([(2 * N + 3) * 4 * D + 4 * sum(float(s) * (D // I) for s, I in zip(kept[b], DIMS))
+                    for b in range(k_conv)])
+    fused = np.array([pb["fused"] for pb in per_body]) / 1000.0        # seconds per launch
+    active = kept.sum(axis=1) > 0
     peak, peak_kind = _peaks()
-    achieved = alg_bytes / (fused_ms / 1000.0) / 1e9
-    traffic = _fused_traffic()
+
+    def phase(mask):
+        return {"bodies": int(mask.sum()), "launch_ms": float(fused[mask].mean() * 1000),
+                "alg_bytes_per_launch": float(alg[mask].mean()),
+                "achieved": float(alg[mask].sum() / fused[mask].sum() / 1e9),
+                "frac": float(alg[mask].sum() / fused[mask].sum() / 1e9 / peak)}
+
+    achieved = float(alg.sum() / fused.sum() / 1e9)
+    tr_idle, tr_active = _fused_traffic()
+    traffic = None
+    if tr_idle is not None and tr_active is not None:
+        traffic = (tr_idle * int((~active).sum()) + tr_active * int(active.sum())) / k_conv
     roofline = {"bound": "hbm", "kernel": "fused elementwise pass (refold Z_n, E-step, multipliers, residuals)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_kind": peak_kind, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
-                "profiled_bodies": [k0 + 1, k0 + 30], "kept_mean": kept_mean.tolist(),
-                "launch_ms": fused_ms,
-                "kernel_ms_per_iter": {k: v / 30 for k, v in prof.items()}}
+                "peak_kind": peak_kind, "traffic": traffic, "alg_bytes_per_launch": float(alg.mean()),
+                "launch_ms": float(fused.mean() * 1000),
+                "averaged_over": f"every launch of one {k_conv}-body solve (the trajectory the timed region replays)",
+                "phases": {"idle": phase(~active), "active": phase(active)},
+                "kernel_ms_per_iter": {k: float(np.mean([pb[k] for pb in per_body])) for k in per_body[0]}}
 
     # e2e: whole solves through the public host-buffer entry point
     Lh = torch.empty(DIMS, dtype=torch.float32).pin_memory()
