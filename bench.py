@@ -202,7 +202,6 @@ def _serving(P, torch, ctx, args):
     gen_s = time.perf_counter() - tg
     Ts = [torch.from_numpy(pr.T).to(dev) for pr in probs]
     n_req = int(args.serve_rate * args.serve_seconds)
-    arrivals = synth.poisson_arrivals(args.serve_rate, n_req, seed=5)
     which = np.random.Generator(np.random.PCG64(6)).integers(0, len(specs), size=n_req)
 
     def timed_solve(plan, q, L, E):
@@ -227,6 +226,40 @@ def _serving(P, torch, ctx, args):
         P.pasd_plan_destroy(plan)
     serial_s = sum(serial_ms[int(q)] for q in which) / 1000.0
 
+    def trace(rate):
+        n = int(rate * args.serve_seconds)
+        arr = synth.poisson_arrivals(rate, n, seed=5)
+        wh = np.random.Generator(np.random.PCG64(6)).integers(0, len(specs), size=n)
+        return n, arr, wh
+
+    def run(slots, rate):
+        n, arr, wh = trace(rate)
+        nxt = [0] * len(specs)
+        pending = {}
+        lat, finish, bad = [], [], 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        i = 0
+        while i < n or pending:
+            now = time.perf_counter() - t0
+            while i < n and arr[i] <= now:
+                q = int(wh[i])
+                plan, L, E = slots[q][nxt[q]]
+                nxt[q] = (nxt[q] + 1) % len(slots[q])
+                pending[P.pasd_submit(ctx, plan, Ts[q], L, E)] = float(arr[i])
+                i += 1
+            for tk in list(pending):
+                st, _ = P.pasd_poll(ctx, tk)
+                if st != P.PENDING:
+                    f = time.perf_counter() - t0
+                    lat.append(f - pending.pop(tk))
+                    finish.append(f)
+                    bad += st not in (P.OK, P.NOT_CONVERGED)
+            time.sleep(0.0002)
+        span = max(finish) - float(arr[0])
+        return {"offered_rate": rate, "requests": n, "solves_per_s": n / span,
+                "p50_ms": 1000 * _percentile(lat, 50), "p99_ms": 1000 * _percentile(lat, 99), "failed": bad}
+
     def serve(precision):
         slots, outs, skipped, one_ms = [], [], [], []
         for q, sp in enumerate(specs):
@@ -243,35 +276,15 @@ def _serving(P, torch, ctx, args):
             skipped.append(int(r.skipped))
             outs.append(row[0][1].clone())
             slots.append(row)
-        nxt = [0] * len(specs)
-        pending = {}
-        lat, finish, bad = [], [], 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        i = 0
-        while i < n_req or pending:
-            now = time.perf_counter() - t0
-            while i < n_req and arrivals[i] <= now:
-                q = int(which[i])
-                plan, L, E = slots[q][nxt[q]]
-                nxt[q] = (nxt[q] + 1) % len(slots[q])
-                pending[P.pasd_submit(ctx, plan, Ts[q], L, E)] = float(arrivals[i])
-                i += 1
-            for tk in list(pending):
-                st, _ = P.pasd_poll(ctx, tk)
-                if st != P.PENDING:
-                    f = time.perf_counter() - t0
-                    lat.append(f - pending.pop(tk))
-                    finish.append(f)
-                    bad += st not in (P.OK, P.NOT_CONVERGED)
-            time.sleep(0.0002)
-        span = max(finish) - float(arrivals[0])
+        out = run(slots, args.serve_rate)
+        del out["offered_rate"], out["requests"]
+        out["below_capacity"] = run(slots, args.serve_low_rate)
+        out["skipped_per_solve"] = skipped
+        out["solo_ms_per_solve"] = one_ms
         for row in slots:
             for plan, _, _ in row:
                 P.pasd_plan_destroy(plan)
-        return {"solves_per_s": n_req / span, "p50_ms": 1000 * _percentile(lat, 50),
-                "p99_ms": 1000 * _percentile(lat, 99), "failed": bad, "skipped_per_solve": skipped,
-                "solo_ms_per_solve": one_ms}, outs
+        return out, outs
 
     fp32, out32 = serve(P.PREC_FP32)
     mixed, outmx = serve(P.PREC_MIXED)
@@ -281,7 +294,8 @@ def _serving(P, torch, ctx, args):
             "serial_plain_fp32_solves_per_s": n_req / serial_s,
             "mix": f"{len(specs)} planted cubes, side log-uniform 32-256, Tucker 3-20, R=floor(1.2 r), "
                    f"5-30% corruption (seed 4); {args.serve_slots} plans per problem; Poisson arrivals "
-                   f"(seed 5) for {args.serve_seconds} s; served solves use the idle-start skip",
+                   f"(seed 5) for {args.serve_seconds} s; served solves use the idle-start skip; below_capacity: "
+                   f"the same trace at {args.serve_low_rate} requests/s",
             "sides": [sp.dims[0] for sp in specs], "iters_per_solve": iters,
             "serial_ms_per_solve": [round(x, 2) for x in serial_ms], "generation_s": round(gen_s, 1)}
 
@@ -718,6 +732,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the served-throughput measurement")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window (s)")
+    ap.add_argument("--serve-low-rate", type=float, default=40.0,
+                    help="second arrival rate, below capacity, for service-time latencies")
     ap.add_argument("--serve-problems", type=int, default=8)
     ap.add_argument("--serve-slots", type=int, default=3, help="plans per problem")
     ap.add_argument("--no-video", action="store_true", help="skip the video-shape measurement")
