@@ -531,6 +531,18 @@ def _video(P, torch, ctx, args):
     return out
 
 
+def _job_time_and_value(ms: float, steps: int, world: int, dist, device):
+    """The job's timed region is the slowest rank's (max over ranks of `ms`);
+    the throughput counts the steps of every rank (one replica per rank, no
+    data-path collective). With dist None the rank is alone."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(ms)], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps / (ms / 1000.0)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -596,12 +608,7 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1000.0)
+    ms, value = _job_time_and_value(ev0.elapsed_time(ev1), args.steps, world, dist, dev)
 
     # dominant kernel: per-kernel CUDA-event durations for every body of one solve,
     # i.e. the trajectory the timed region replays (idle and active bodies alike)
