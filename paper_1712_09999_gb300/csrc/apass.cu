@@ -392,8 +392,8 @@ void launch_apass(const ApassArgs& a, cudaStream_t s) { launch_apass_modes(&a, 1
 //   post == 1: a task is 256 consecutive columns (rows of G); the tile is
 //              [col][k] with the 64-byte swizzle (16-byte group g of row c sits
 //              at g ^ ((c >> 1) & 3)), so the float4 reads below are conflict-free.
-// The arithmetic is the cp.async kernel's (same per-thread column pairs and the
-// same order of accumulation), so both give identical results.
+// Each column of A accumulates over k in the same order as in the cp.async
+// kernel, so A is identical; the Gram partials group the columns differently.
 // ---------------------------------------------------------------------------
 struct ApassTmaMaps {
     CUtensorMap g[PASD_MAXN];

@@ -50,7 +50,7 @@ struct ModeGeom {
 // A-pass: A_n = U_n^T G_n (+ per-CTA Gram partials of A_n A_n^T)
 // ----------------------------------------------------------------------------
 constexpr int AP_THREADS = 128;
-constexpr int AP_BN = 256;       // columns of the unfolding per CTA (2 per thread)
+constexpr int AP_BN = 256;       // columns of the unfolding per CTA
 constexpr int AP_BK = 16;        // rows of the contraction per pipeline stage
 constexpr int AP_STAGES = 4;
 

@@ -1,4 +1,4 @@
-// Bulk tensor copies (TMA) and mbarriers: the PTX the streaming kernels share,
+// Bulk tensor loads (TMA) and mbarriers: the PTX the streaming kernels share,
 // and the host-side tensor-map encoder.
 #pragma once
 #include <cuda.h>
@@ -41,10 +41,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() {
-    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-}
 
 // Tiled bulk tensor load of rank R (coordinates innermost first) into shared
 // memory, completing on `bar` with the box's byte count.
@@ -67,24 +63,6 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint
     else
         asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, %7}], [%2];\n"
                      ::"r"(d), "l"(m), "r"(b), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]) : "memory");
-}
-
-template <int R>
-__device__ __forceinline__ void tma_store(const CUtensorMap* map, const void* src, const int* c) {
-    const uint32_t s = smem_u32(src);
-    const uint64_t m = reinterpret_cast<uint64_t>(map);
-    if (R == 2)
-        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n"
-                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]) : "memory");
-    else if (R == 3)
-        asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];\n"
-                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]), "r"(c[2]) : "memory");
-    else if (R == 4)
-        asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];\n"
-                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]) : "memory");
-    else
-        asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];\n"
-                     ::"l"(m), "r"(s), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]) : "memory");
 }
 
 // Host: encodes a tiled float32 tensor map over a dense C-order array.
