@@ -133,8 +133,8 @@ pasd_status pasd_params_default(pasd_params* p, int32_t order, const int64_t* di
  * receives the device bytes the state will take. Errors: INVALID_ARG when
  * N < 2, any R_n > I_n (the Stiefel set St(I_n, R_n) is empty) or R_n < 1,
  * a weight <= 0, rho <= 1 or mu_max < mu0; UNSUPPORTED when R_n > PASD_MAX_RANK.
- * Environment, read here (for comparisons and debugging; the results do not
- * change): PASD_NO_TMA=1 plans the kernels fed by per-thread asynchronous
+ * Environment, read here (for comparisons and debugging; the same arithmetic up
+ * to the grouping of partial sums): PASD_NO_TMA=1 plans the kernels fed by per-thread asynchronous
  * copies instead of bulk tensor copies; PASD_NO_GRAPH=1 launches each loop
  * body's kernels directly instead of replaying a captured CUDA graph. */
 pasd_status pasd_plan(pasd_ctx* ctx, const pasd_params* p, pasd_plan_t** out,
