@@ -173,7 +173,10 @@ pasd_status pasd_poll(pasd_ctx* ctx, uint64_t ticket, pasd_result* out);
  *   pasd_begin   - Algorithm 1 initialisation for observation T (device);
  *   pasd_iterate - enqueue `iters` loop bodies; bodies after the stop rule
  *                  holds are skipped on the device;
- *   pasd_finish  - write L and E (device) and fill `result` (synchronous). */
+ *   pasd_finish  - write L and E (device) and fill `result` (synchronous).
+ * The first pasd_begin on a plan (also inside pasd_solve and the served path)
+ * allocates the plan's device memory and clears it; the clear is complete
+ * before anything is enqueued on `stream`, whatever that stream is. */
 pasd_status pasd_begin(pasd_plan_t* plan, const float* T, void* stream);
 pasd_status pasd_iterate(pasd_plan_t* plan, int32_t iters, void* stream);
 pasd_status pasd_finish(pasd_plan_t* plan, float* L, float* E, pasd_result* result,
@@ -232,7 +235,8 @@ pasd_status pasd_mode_product(const float* X, int64_t pre, int64_t I, int64_t po
  * the call allocates nothing and is asynchronous on `stream`. Limit:
  * ceil(pre*post/256) * R * R <= 1048576, else UNSUPPORTED (outputs untouched).
  * The first call on a device looks up the scratch's device address (with that
- * device current); make it before any stream capture. All calls share the
+ * device current) and clears the scratch's flags on `stream`, waiting for that
+ * clear (so that call returns after it); make it before any stream capture. All calls share the
  * scratch and it keeps the last call's contents: calls whose work overlaps on
  * the GPU race on it and must be serialised by the caller. */
 pasd_status pasd_mode_product_noalloc(const float* X, int64_t pre, int64_t I, int64_t post,

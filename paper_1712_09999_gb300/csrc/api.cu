@@ -475,10 +475,15 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
     pl->idle_g = reinterpret_cast<float*>(take(4));
     pl->trace = reinterpret_cast<double*>(take((size_t)pl->p.max_iter * PASD_TRACE_STRIDE * 8));
     if (pl->pad) pl->Lpad = reinterpret_cast<float*>(take(D * 4));
-    // zeros everywhere once: the padded entries of T, E, G_n are never written
-    CUDA_TRY(cudaMemset(pl->arena, 0, pl->footprint));
-    CUDA_TRY(cudaMallocHost(&pl->host_sc, sizeof(DevScalars)));
+    // zeros everywhere once: the padded entries of T, E, G_n are never written.
+    // The clear runs on the plan's own non-blocking stream and is complete before
+    // this returns: a plain cudaMemset would be queued on the legacy default stream,
+    // which work on non-blocking streams (the served path's, or a caller's) does not
+    // wait for, so behind other work there it could land in the middle of a solve.
     CUDA_TRY(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaMemsetAsync(pl->arena, 0, pl->footprint, pl->cap_stream));
+    CUDA_TRY(cudaStreamSynchronize(pl->cap_stream));
+    CUDA_TRY(cudaMallocHost(&pl->host_sc, sizeof(DevScalars)));
     CUDA_TRY(cudaEventCreateWithFlags(&pl->ev, cudaEventDisableTiming));
 
     // launch descriptors

@@ -47,8 +47,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 DeviceScratch g_scratch[kMaxDevices];
 
-// Device addresses of the scratch on the current device (set up once per device).
-pasd_status scratch_for_current_device(DeviceScratch** out) {
+// Device addresses of the scratch on the current device (set up once per device;
+// the setup clears the flags on `stream` and waits for that clear).
+pasd_status scratch_for_current_device(DeviceScratch** out, cudaStream_t stream) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
@@ -77,10 +78,12 @@ pasd_status scratch_for_current_device(DeviceScratch** out) {
             return PASD_ERR_CUDA;
         }
         d.flags = static_cast<DevScalars*>(p);
-        // the product kernel returns early when flags->done is set: clear it once
-        e = cudaMemset(d.flags, 0, sizeof(DevScalars));
+        // the product kernel returns early when flags->done is set: clear it once,
+        // complete before any product is launched (on whatever stream)
+        e = cudaMemsetAsync(d.flags, 0, sizeof(DevScalars), stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) {
-            pasd_set_error(std::string("pasd_mode_product_noalloc: cudaMemset: ") + cudaGetErrorString(e));
+            pasd_set_error(std::string("pasd_mode_product_noalloc: clearing the flags: ") + cudaGetErrorString(e));
             return PASD_ERR_CUDA;
         }
         d.ready = true;
@@ -109,10 +112,10 @@ extern "C" pasd_status pasd_mode_product_noalloc(const float* X, int64_t pre, in
                        "of 1048576 floats; use pasd_mode_product");
         return PASD_ERR_UNSUPPORTED;
     }
-    DeviceScratch* d = nullptr;
-    pasd_status st = scratch_for_current_device(&d);
-    if (st != PASD_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    DeviceScratch* d = nullptr;
+    pasd_status st = scratch_for_current_device(&d, s);
+    if (st != PASD_OK) return st;
     ApassArgs a{};
     a.G = X; a.U = U; a.A = A; a.gram_part = d->part; a.sc = d->flags;
     a.I = I; a.pre = pre; a.post = post; a.P = P; a.R = R; a.Rp = R; a.ncta = ncta;

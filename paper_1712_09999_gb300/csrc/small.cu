@@ -772,10 +772,14 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     // zero); with nothing kept there is nothing to write
     const int s4 = (s + 3) & ~3;
     if (s4 == 0) return;
-    __shared__ float Wt[PASD_MAXR * PASD_MAXR];   // Wt[i][r] = F_i W[r][i]
-    for (int idx = threadIdx.x; idx < s * R; idx += blockDim.x) {
-        int i = idx / R, r = idx % R;
-        Wt[i * R + r] = m.F[i] * m.W[r * Rp + i];
+    // Wt[i][r] = F_i W[r][i] with row stride RB, zero for R <= r < RB: the
+    // product below runs over all RB entries of a row as float4 broadcasts, and
+    // the padding terms are exact zeros added last, so each sum is the same as
+    // over r < R
+    __shared__ __align__(16) float Wt[PASD_MAXR * PASD_MAXR];
+    for (int idx = threadIdx.x; idx < s * RB; idx += blockDim.x) {
+        const int i = idx / RB, r = idx % RB;
+        Wt[idx] = r < R ? m.F[i] * m.W[r * Rp + i] : 0.f;
     }
     __syncthreads();
     const int64_t j = (int64_t)(blockIdx.x - va.cta_start[k]) * blockDim.x + threadIdx.x;
@@ -784,7 +788,8 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     const float* src = m.A + a * Rp * m.post + b;
     float* dst = m.V + a * Rp * m.post + b;
     // the column of A_n in registers (RB >= Rp, fully unrolled), all loads in
-    // flight; with post == 1 the column is Rp contiguous floats (float4 moves)
+    // flight; with post == 1 the column is Rp contiguous floats (float4 moves).
+    // Entries past R are set to zero (A's padding rows are never multiplied).
     float av[RB];
     if (m.post == 1) {
 #pragma unroll
@@ -793,6 +798,9 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
             if (4 * r4 < Rp) v = reinterpret_cast<const float4*>(src)[r4];
             av[4 * r4] = v.x; av[4 * r4 + 1] = v.y; av[4 * r4 + 2] = v.z; av[4 * r4 + 3] = v.w;
         }
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+            if (r >= R) av[r] = 0.f;
     } else {
 #pragma unroll
         for (int r = 0; r < RB; ++r) av[r] = r < R ? src[(int64_t)r * m.post] : 0.f;
@@ -802,9 +810,15 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     for (int i = 0; i < RB; ++i) {
         float acc = 0.f;
         if (i < s) {
+            const float4* w4 = reinterpret_cast<const float4*>(Wt + i * RB);
 #pragma unroll
-            for (int r = 0; r < RB; ++r)
-                if (r < R) acc = fmaf(Wt[i * R + r], av[r], acc);
+            for (int r4 = 0; r4 < RB / 4; ++r4) {
+                const float4 w = w4[r4];
+                acc = fmaf(w.x, av[4 * r4], acc);
+                acc = fmaf(w.y, av[4 * r4 + 1], acc);
+                acc = fmaf(w.z, av[4 * r4 + 2], acc);
+                acc = fmaf(w.w, av[4 * r4 + 3], acc);
+            }
         }
         out[i] = acc;
     }

@@ -477,6 +477,65 @@ def test_served_results_equal_alone(env, mode):
         P.pasd_plan_destroy(plan)
 
 
+def test_first_solve_on_a_plan_is_ordered_after_its_setup(env):
+    # A plan's device memory is allocated and cleared on its first use. The clear
+    # must be complete before the solve starts on a stream that does not wait for
+    # the legacy default stream (the served path's streams, or a caller's
+    # non-blocking stream), even while other work holds that default stream: here
+    # a bounded spin kernel of about 10 ms. Results equal solves on used plans.
+    torch, P, ctx = env
+    probs = [synth.planted((100, 100, 100), (6, 6, 6), 0.1, 40 + i, scale="std", amp=5.0) for i in range(3)]
+    ref = []
+    for pr in probs:
+        plan, _ = P.pasd_plan(ctx, P.make_params(pr.T.shape, (8, 8, 8), max_iter=1000, flags=P.F_SKIP_IDLE))
+        Td = torch.from_numpy(pr.T).cuda()
+        L = torch.empty_like(Td); E = torch.empty_like(Td)
+        r = P.pasd_solve(plan, Td, L, E)
+        ref.append((r.iters, L.clone(), E.clone(), Td))
+        P.pasd_plan_destroy(plan)
+    torch.cuda.synchronize()
+
+    # served path: two solves on never-used plans
+    fresh = [P.pasd_plan(ctx, P.make_params(pr.T.shape, (8, 8, 8), max_iter=1000, flags=P.F_SKIP_IDLE))[0]
+             for pr in probs[:2]]
+    outs = [(torch.empty_like(ref[i][3]), torch.empty_like(ref[i][3])) for i in range(2)]
+    torch.cuda.synchronize()
+    torch.cuda._sleep(20_000_000)
+    tickets = [P.pasd_submit(ctx, fresh[i], ref[i][3], *outs[i]) for i in range(2)]
+    import time
+    t0 = time.time()
+    results = {}
+    while len(results) < 2 and time.time() - t0 < 60:
+        for t in tickets:
+            if t not in results:
+                st, r = P.pasd_poll(ctx, t)
+                if st != P.PENDING:
+                    results[t] = (st, r)
+        time.sleep(0.001)
+    torch.cuda.synchronize()
+    assert len(results) == 2
+    for i, t in enumerate(tickets):
+        st, r = results[t]
+        assert st == P.OK and r.iters == ref[i][0]
+        assert torch.equal(outs[i][0], ref[i][1]) and torch.equal(outs[i][1], ref[i][2])
+    for plan in fresh:
+        P.pasd_plan_destroy(plan)
+
+    # stepwise on a caller's non-blocking stream, on a never-used plan
+    plan, _ = P.pasd_plan(ctx, P.make_params(probs[2].T.shape, (8, 8, 8), max_iter=1000, flags=P.F_SKIP_IDLE))
+    L = torch.empty_like(ref[2][3]); E = torch.empty_like(ref[2][3])
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    torch.cuda._sleep(20_000_000)
+    P.pasd_begin(plan, ref[2][3], side)
+    P.pasd_iterate(plan, ref[2][0], side)
+    r = P.pasd_finish(plan, L, E, side)
+    torch.cuda.synchronize()
+    assert r.iters == ref[2][0]
+    assert torch.equal(L, ref[2][1]) and torch.equal(E, ref[2][2])
+    P.pasd_plan_destroy(plan)
+
+
 def test_invalid_and_nonfinite_inputs(env):
     torch, P, ctx = env
     with pytest.raises(P.PasdError) as ei:
