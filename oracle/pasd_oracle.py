@@ -76,16 +76,24 @@ def soft_threshold(x: np.ndarray, tau: float) -> np.ndarray:
 @dataclass
 class SvtOut:
     V: np.ndarray        # SVT_tau(X)
-    left: np.ndarray     # left singular vectors of X (R x R for a short-fat X)
-    sigma: np.ndarray    # singular values of X, descending
+    left: np.ndarray     # left singular vectors of X, a full R x R orthogonal basis
+    sigma: np.ndarray    # the R singular values of X, descending (zeros past min(R, P))
     kept: int            # number of singular values strictly above tau
     nuclear: float       # ||SVT_tau(X)||_* = sum max(sigma - tau, 0)
 
 
 def svt(x: np.ndarray, tau: float) -> SvtOut:
     """SVT_tau(X) = U diag(max(Sigma - tau, 0)) V^T from the SVD X = U Sigma V^T
-    (definition after Eq. 13). A singular value equal to tau is dropped."""
-    u, s, vt = np.linalg.svd(x, full_matrices=False)
+    (definition after Eq. 13). A singular value equal to tau is dropped.
+
+    X is R x P. ``left`` spans all of R^R: when R > P, the R - P directions
+    outside the range of X have singular value zero and belong with the other
+    dropped directions to the null space of SVT_tau(X)^T."""
+    rows, cols = x.shape
+    u, s, vt = np.linalg.svd(x, full_matrices=rows > cols)
+    if rows > cols:
+        vt = vt[:cols]
+        s = np.concatenate([s, np.zeros(rows - cols)])
     shrunk = np.maximum(s - tau, 0.0)
     kept = int(np.count_nonzero(s > tau))
     v = (u[:, :kept] * shrunk[:kept]) @ vt[:kept, :]

@@ -119,6 +119,22 @@ def test_shapes_match_oracle(env, dims, tucker, ranks):
     _check_parity(g, ref, len(dims))
 
 
+@pytest.mark.parametrize("dims,tucker,ranks", [
+    ((9, 8), (2, 2), (9, 8)),              # R_0 = I_0 = 9 above P_0 = 8
+    ((12, 3, 2), (2, 2, 1), (8, 3, 2)),    # R_0 = 8 above P_0 = 6, below I_0
+])
+def test_rank_bound_above_unfolding_columns(env, dims, tucker, ranks):
+    # A_0 = U_0^T G_0 is R_0 x P_0 with R_0 > P_0: R_0 - P_0 of its singular values
+    # are zero by shape, and their directions belong to the U-step's null space.
+    # Fixed 200 bodies (both solves converge near 160-190 bodies, the second with its
+    # last residual within 1% of tol, so a fixed count keeps the comparison free of
+    # a stopping tie).
+    pr = synth.planted(dims, tucker, 0.1, 3, scale="std", amp=5.0)
+    ref = _oracle(pr.T, ranks, 2, 200)
+    g = _gpu_solve(env, pr.T, ranks, 2, 200)
+    _check_parity(g, ref, len(dims))
+
+
 def test_hyperspectral_shape_matches_oracle(env):
     # Hyperspectral-shaped cube (rows, columns, bands) with salt-and-pepper noise
     # (entries replaced by 0 or 1) and an odd band count (19, padded to 20 inside

@@ -251,10 +251,14 @@ def _horpca(t, lambdas, iters, mu0=1e-4, rho=1.1, mu_max=1e10):
     return sum(zs) / nm, e
 
 
-def test_full_rank_bound_reduces_to_horpca():
+@pytest.mark.parametrize("dims,tucker", [((6, 5, 4), (2, 2, 2)), ((9, 8), (2, 2)), ((7, 2, 3), (2, 1, 2))])
+def test_full_rank_bound_reduces_to_horpca(dims, tucker):
     # With R_n = I_n the active subspace is square orthogonal, U U^T = I, and
     # fold_n(U_n V_n) = SVT(G_n): PASD becomes the HoRPCA iteration of Eq. 2.
-    pr = synth.planted((6, 5, 4), (2, 2, 2), 0.1, 21, scale="std", amp=5.0)
+    # The matrix and (7, 2, 3) cases have R_0 = I_0 larger than the number of
+    # columns P_0 of the first unfolding, so A_0 has R_0 - P_0 singular values that
+    # are zero by shape, and their directions belong to the U-step's null space.
+    pr = synth.planted(dims, tucker, 0.1, 21, scale="std", amp=5.0)
     t = pr.T.astype(np.float64)
     lam = O.paper_lambdas(t.shape)
     iters = 150

@@ -134,6 +134,7 @@ def _check(ref, L, E, res, comm_elements, dims, ranks, m):
     ((8, 6, 2), (2, 2, 1), (3, 3, 2), 2, 3),       # R_m = I_m, one rank holds no slab
     ((7, 6, 5, 4), (2, 2, 2, 2), (3, 3, 3, 2), 2, 3),
     ((12, 9), (2, 2), (3, 3), 0, 2),               # matrix case
+    ((12, 3, 2), (2, 2, 1), (8, 3, 2), 1, 2),      # R_0 = 8 above P_0 = 6
 ])
 def test_sharded_matches_oracle(dims, tucker, ranks, m, world):
     T, p = _problem(dims, tucker, ranks)
