@@ -57,6 +57,21 @@ def test_svt_closed_form_on_constructed_matrices():
         assert out.nuclear == pytest.approx(np.maximum(s - tau, 0).sum(), abs=1e-12)
 
 
+def test_svt_drops_a_singular_value_equal_to_tau():
+    # SVT_tau keeps max(sigma - tau, 0): a singular value exactly at tau contributes
+    # nothing and is not counted as kept (the tie reading of the SVT definition).
+    # Signed permutations of a diagonal have exact singular values 3, 2, 0.5.
+    rng = _rng(31)
+    for _ in range(6):
+        perm = rng.permutation(5)
+        x = np.zeros((3, 5))
+        x[np.arange(3), perm[:3]] = np.array([3.0, 2.0, 0.5]) * rng.choice([-1.0, 1.0], 3)
+        out = O.svt(x, 2.0)
+        assert out.kept == 1
+        assert out.nuclear == 1.0
+        assert np.allclose(out.V, np.where(np.abs(x) == 3.0, np.sign(x), 0.0), atol=1e-15)
+
+
 def test_svt_is_the_nuclear_prox():
     # SVT_tau(X) minimises tau ||V||_* + ||V - X||_F^2 / 2 (strongly convex), so no
     # perturbation can lower the objective.
