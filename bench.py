@@ -749,7 +749,7 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="solve time against cube size")
     ap.add_argument("--sweep-sides", type=int, nargs="+", default=[100, 200, 300, 400, 500, 600, 800])
     ap.add_argument("--phase", action="store_true", help="phase-transition map on 100^3")
-    ap.add_argument("--phase-trials", type=int, default=2)
+    ap.add_argument("--phase-trials", type=int, default=10)
     ap.add_argument("--phase-slots", type=int, default=16)
     ap.add_argument("--video-pre", type=int, default=150)
     ap.add_argument("--video-iters", type=int, default=200)
