@@ -161,7 +161,12 @@ pasd_status pasd_solve_host(pasd_plan_t* plan, const float* T_host, float* L_hos
  * together, each on its own stream, and retire as they converge. The solve's
  * stream is not ordered after any stream of the caller: T must be fully
  * written (its producing stream synchronised) before pasd_submit is called.
- * One plan serves one solve at a time. Errors: BUSY when the queue is full. */
+ * One plan serves one solve at a time (further submits of it wait in the
+ * queue). Until every ticket of a plan has been polled to a final status, the
+ * plan belongs to the served path: the caller must not destroy it, nor pass it
+ * to pasd_solve, pasd_solve_host, pasd_begin/iterate/finish, pasd_state_get or
+ * pasd_profile_iterations (nothing checks this). Errors: BUSY when the queue
+ * is full. */
 pasd_status pasd_submit(pasd_ctx* ctx, pasd_plan_t* plan, const float* T, float* L,
                         float* E, uint64_t* ticket);
 /* PASD_PENDING while the solve is queued or running; otherwise its final
