@@ -145,6 +145,30 @@ def _oracle_iters_per_s(T, seconds: float):
             return n / el, n, el
 
 
+ONE_CORE_ENV = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                  "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")}
+
+
+def _oracle_one_core(seconds: float):
+    """The same oracle timing with every BLAS/OpenMP pool limited to one thread. The
+    limits must be set before numpy loads its BLAS, so this runs in a child process
+    (this script with --oracle-one-core); returns (bodies/s, bodies, seconds) or None."""
+    env = dict(os.environ, **ONE_CORE_ENV)
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-one-core", str(seconds)],
+                           env=env, capture_output=True, text=True, timeout=seconds + 300)
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+        return out["value"], out["bodies"], out["seconds"]
+    except Exception:
+        return None
+
+
+def run_oracle_one_core(seconds: float):
+    from paper_1712_09999_gb300 import synth
+    v, n, el = _oracle_iters_per_s(synth.cube_200(1).T, seconds)
+    print(json.dumps({"value": v, "bodies": n, "seconds": el}), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -686,6 +710,11 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{n} FP64 loop bodies of the 200^3 workload in {el:.1f} s "
                                           "(numpy/LAPACK, BLAS threads = all cores)"}
+        one = _oracle_one_core(args.cpu_seconds)
+        if one is not None:
+            line["cpu_baseline"]["single_core"] = {
+                "value": one[0], "unit": UNIT, "cores": 1,
+                "sample": f"{one[1]} FP64 loop bodies in {one[2]:.1f} s, BLAS and OpenMP limited to one thread"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     P.pasd_plan_destroy(plan)
@@ -753,7 +782,11 @@ def main():
     ap.add_argument("--phase-slots", type=int, default=16)
     ap.add_argument("--video-pre", type=int, default=150)
     ap.add_argument("--video-iters", type=int, default=200)
+    ap.add_argument("--oracle-one-core", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_one_core is not None:
+        run_oracle_one_core(args.oracle_one_core)
+        return
     if args.profile_workload:
         run_profile_workload(args)
         return
