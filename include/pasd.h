@@ -162,11 +162,12 @@ pasd_status pasd_solve_host(pasd_plan_t* plan, const float* T_host, float* L_hos
  * stream is not ordered after any stream of the caller: T must be fully
  * written (its producing stream synchronised) before pasd_submit is called.
  * One plan serves one solve at a time (further submits of it wait in the
- * queue). Until every ticket of a plan has been polled to a final status, the
- * plan belongs to the served path: the caller must not destroy it, nor pass it
- * to pasd_solve, pasd_solve_host, pasd_begin/iterate/finish, pasd_state_get or
- * pasd_profile_iterations (nothing checks this). Errors: BUSY when the queue
- * is full. */
+ * queue). While a served solve of a plan is queued or running, the plan belongs
+ * to the served path: pasd_plan_destroy, pasd_solve, pasd_solve_host,
+ * pasd_begin/iterate/finish, pasd_state_get and pasd_profile_iterations return
+ * BUSY for it (and do nothing). It is the caller's again once the solve has
+ * retired, at the latest when pasd_poll returns its final status. Errors: BUSY
+ * when the queue is full. */
 pasd_status pasd_submit(pasd_ctx* ctx, pasd_plan_t* plan, const float* T, float* L,
                         float* E, uint64_t* ticket);
 /* PASD_PENDING while the solve is queued or running; otherwise its final

@@ -132,6 +132,7 @@ struct pasd_plan {
     cudaStream_t own_stream = nullptr;   // served path
     cudaEvent_t ev = nullptr;
     bool busy = false;
+    int served = 0;          // served solves queued or running (guarded by ctx->mu)
     int ap_launches = 1;
     // idle-start skip (PASD_F_SKIP_IDLE): armed by pasd_begin, run after the first body
     float* idle_g = nullptr;
@@ -622,8 +623,18 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
     return PASD_OK;
 }
 
+// A plan with served solves queued or running belongs to the served path: the
+// entry points that touch its state refuse it until they have retired.
+static pasd_status check_not_served(pasd_plan_t* pl) {
+    std::unique_lock<std::mutex> lk(pl->ctx->mu);
+    if (pl->served > 0) return fail(PASD_ERR_BUSY, "plan has served solves queued or running");
+    return PASD_OK;
+}
+
 extern "C" pasd_status pasd_plan_destroy(pasd_plan_t* pl) {
     if (!pl) return fail(PASD_ERR_INVALID_ARG, "plan is NULL");
+    pasd_status chk = check_not_served(pl);
+    if (chk != PASD_OK) return chk;
     if (pl->tma) destroy_fused_tma(pl->tma);
     for (int q = 0; q < pl->n_ap_tma; ++q) destroy_apass_tma(pl->ap_tma[q]);
     if (pl->mp_tma) destroy_mpass_tma(pl->mp_tma);
@@ -643,6 +654,8 @@ extern "C" pasd_status pasd_plan_destroy(pasd_plan_t* pl) {
 extern "C" pasd_status pasd_profile_iterations(pasd_plan_t* pl, int32_t iters, double* ms,
                                                void* stream) {
     if (!pl || !ms || iters < 0) return fail(PASD_ERR_INVALID_ARG, "bad argument");
+    pasd_status chk = check_not_served(pl);
+    if (chk != PASD_OK) return chk;
     if (!pl->arena) return fail(PASD_ERR_INVALID_ARG, "pasd_begin has not run");
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t ev[PASD_PROFILE_SLOTS + 1];
@@ -683,8 +696,7 @@ extern "C" int32_t pasd_launches_per_iter(const pasd_plan_t* pl) {
 // ---------------------------------------------------------------------------
 // stepwise solve
 // ---------------------------------------------------------------------------
-extern "C" pasd_status pasd_begin(pasd_plan_t* pl, const float* T, void* stream) {
-    if (!pl || !T) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+static pasd_status begin_impl(pasd_plan_t* pl, const float* T, void* stream) {
     pasd_status st = ensure_allocated(pl);
     if (st != PASD_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -708,8 +720,7 @@ extern "C" pasd_status pasd_begin(pasd_plan_t* pl, const float* T, void* stream)
     return PASD_OK;
 }
 
-extern "C" pasd_status pasd_iterate(pasd_plan_t* pl, int32_t iters, void* stream) {
-    if (!pl || iters < 0) return fail(PASD_ERR_INVALID_ARG, "bad argument");
+static pasd_status iterate_impl(pasd_plan_t* pl, int32_t iters, void* stream) {
     if (!pl->arena) return fail(PASD_ERR_INVALID_ARG, "pasd_begin has not run");
     cudaStream_t s = (cudaStream_t)stream;
     for (int i = 0; i < iters; ++i) {
@@ -745,9 +756,7 @@ static void fill_result(pasd_plan_t* pl, pasd_result* r) {
     r->skipped = h.skipped;
 }
 
-extern "C" pasd_status pasd_finish(pasd_plan_t* pl, float* L, float* E, pasd_result* res,
-                                   void* stream) {
-    if (!pl || !L || !E) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+static pasd_status finish_impl(pasd_plan_t* pl, float* L, float* E, pasd_result* res, void* stream) {
     if (!pl->arena) return fail(PASD_ERR_INVALID_ARG, "pasd_begin has not run");
     cudaStream_t s = (cudaStream_t)stream;
     pasd_status st = read_scalars(pl, s);
@@ -778,7 +787,7 @@ static pasd_status run_loop(pasd_plan_t* pl, cudaStream_t s) {
     const int max_iter = pl->p.max_iter;
     int launched = 0;
     // keep one chunk in flight while the previous chunk's flag is checked
-    pasd_status st = pasd_iterate(pl, std::min(chunk, max_iter), s);
+    pasd_status st = iterate_impl(pl, std::min(chunk, max_iter), s);
     if (st != PASD_OK) return st;
     launched += std::min(chunk, max_iter);
     for (;;) {
@@ -786,7 +795,7 @@ static pasd_status run_loop(pasd_plan_t* pl, cudaStream_t s) {
         CUDA_TRY(cudaEventRecord(pl->ev, s));
         if (launched < max_iter) {
             int n = std::min(chunk, max_iter - launched);
-            st = pasd_iterate(pl, n, s);
+            st = iterate_impl(pl, n, s);
             if (st != PASD_OK) return st;
             launched += n;
         }
@@ -800,20 +809,46 @@ static pasd_status run_loop(pasd_plan_t* pl, cudaStream_t s) {
     return PASD_OK;
 }
 
+extern "C" pasd_status pasd_begin(pasd_plan_t* pl, const float* T, void* stream) {
+    if (!pl || !T) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    pasd_status st = check_not_served(pl);
+    if (st != PASD_OK) return st;
+    return begin_impl(pl, T, stream);
+}
+
+extern "C" pasd_status pasd_iterate(pasd_plan_t* pl, int32_t iters, void* stream) {
+    if (!pl || iters < 0) return fail(PASD_ERR_INVALID_ARG, "bad argument");
+    pasd_status st = check_not_served(pl);
+    if (st != PASD_OK) return st;
+    return iterate_impl(pl, iters, stream);
+}
+
+extern "C" pasd_status pasd_finish(pasd_plan_t* pl, float* L, float* E, pasd_result* res,
+                                   void* stream) {
+    if (!pl || !L || !E) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    pasd_status st = check_not_served(pl);
+    if (st != PASD_OK) return st;
+    return finish_impl(pl, L, E, res, stream);
+}
+
 extern "C" pasd_status pasd_solve(pasd_plan_t* pl, const float* T, float* L, float* E,
                                   pasd_result* res, void* stream) {
     if (!pl || !T || !L || !E) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    pasd_status st = check_not_served(pl);
+    if (st != PASD_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    pasd_status st = pasd_begin(pl, T, stream);
+    st = begin_impl(pl, T, stream);
     if (st != PASD_OK) return st;
     st = run_loop(pl, s);
     if (st != PASD_OK) return st;
-    return pasd_finish(pl, L, E, res, stream);
+    return finish_impl(pl, L, E, res, stream);
 }
 
 extern "C" pasd_status pasd_solve_host(pasd_plan_t* pl, const float* Th, float* Lh, float* Eh,
                                        pasd_result* res, void* stream) {
     if (!pl || !Th || !Lh || !Eh) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    pasd_status chk = check_not_served(pl);
+    if (chk != PASD_OK) return chk;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t Dr = pl->D_real;
     if (!pl->dev_io) CUDA_TRY(cudaMalloc(&pl->dev_io, (size_t)3 * Dr * 4));
@@ -835,6 +870,8 @@ extern "C" pasd_status pasd_solve_host(pasd_plan_t* pl, const float* Th, float* 
 extern "C" pasd_status pasd_state_get(pasd_plan_t* pl, int32_t item, int32_t mode, void* dst,
                                       size_t bytes, void* stream) {
     if (!pl || !dst) return fail(PASD_ERR_INVALID_ARG, "NULL argument");
+    pasd_status chk = check_not_served(pl);
+    if (chk != PASD_OK) return chk;
     if (!pl->arena) return fail(PASD_ERR_INVALID_ARG, "no state yet");
     cudaStream_t s = (cudaStream_t)stream;
     const int N = pl->N;
@@ -936,6 +973,8 @@ extern "C" pasd_status pasd_state_get(pasd_plan_t* pl, int32_t item, int32_t mod
 // ---------------------------------------------------------------------------
 struct Active {
     Job job;
+    size_t footprint = 0;    // the plan's, taken at admission: once a result is
+                             // published the caller may destroy the plan
     int launched = 0;
     bool flag_pending = false;
 };
@@ -959,6 +998,7 @@ static void worker_main(pasd_ctx* c) {
                 if (!pl->busy && in_use + need <= c->hbm_budget) {
                     Active a;
                     a.job = *it;
+                    a.footprint = need;
                     pl->busy = true;
                     in_use += need;
                     c->state[it->ticket] = 1;
@@ -974,7 +1014,7 @@ static void worker_main(pasd_ctx* c) {
             pasd_plan_t* pl = a.job.plan;
             if (a.launched == 0 && !a.flag_pending) {
                 if (!pl->own_stream) cudaStreamCreateWithFlags(&pl->own_stream, cudaStreamNonBlocking);
-                pasd_status st = pasd_begin(pl, a.job.T, pl->own_stream);
+                pasd_status st = begin_impl(pl, a.job.T, pl->own_stream);
                 if (st != PASD_OK) {
                     pasd_result r{};
                     r.status = st;
@@ -982,6 +1022,7 @@ static void worker_main(pasd_ctx* c) {
                     c->done[a.job.ticket] = r;
                     c->state.erase(a.job.ticket);
                     pl->busy = false;
+                    --pl->served;
                     a.launched = -1;
                     continue;
                 }
@@ -993,7 +1034,7 @@ static void worker_main(pasd_ctx* c) {
             pasd_plan_t* pl = a.job.plan;
             int n = std::min(pl->p.check_every, pl->p.max_iter - a.launched);
             if (n > 0) {
-                pasd_iterate(pl, n, pl->own_stream);
+                iterate_impl(pl, n, pl->own_stream);
                 a.launched += n;
             }
             cudaMemcpyAsync(pl->host_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, pl->own_stream);
@@ -1011,7 +1052,7 @@ static void worker_main(pasd_ctx* c) {
             progressed = true;
             if (pl->host_sc->done || a.launched >= pl->p.max_iter) {
                 pasd_result r{};
-                pasd_status st = pasd_finish(pl, a.job.L, a.job.E, &r, pl->own_stream);
+                pasd_status st = finish_impl(pl, a.job.L, a.job.E, &r, pl->own_stream);
                 r.status = st;
                 r.latency_s = std::chrono::duration<double>(std::chrono::steady_clock::now() -
                                                             a.job.t_submit).count();
@@ -1019,12 +1060,13 @@ static void worker_main(pasd_ctx* c) {
                 c->done[a.job.ticket] = r;
                 c->state.erase(a.job.ticket);
                 pl->busy = false;
+                --pl->served;
                 a.launched = -1;
             }
         }
         for (auto it = active.begin(); it != active.end();) {
             if (it->launched < 0) {
-                in_use -= it->job.plan->footprint;
+                in_use -= it->footprint;
                 it = active.erase(it);
             } else {
                 ++it;
@@ -1050,6 +1092,7 @@ extern "C" pasd_status pasd_submit(pasd_ctx* c, pasd_plan_t* pl, const float* T,
     j.t_submit = std::chrono::steady_clock::now();
     c->queue.push_back(j);
     c->state[j.ticket] = 0;
+    ++pl->served;
     *ticket = j.ticket;
     if (!c->worker_started) {
         c->worker_started = true;

@@ -552,6 +552,39 @@ def test_first_solve_on_a_plan_is_ordered_after_its_setup(env):
     P.pasd_plan_destroy(plan)
 
 
+def test_a_plan_belongs_to_the_served_path_until_it_retires(env):
+    # While a served solve of a plan is queued or running, the entry points that
+    # touch the plan's state refuse it with BUSY (destroying it included); once
+    # the ticket has been polled to a final status the plan is the caller's again.
+    torch, P, ctx = env
+    pr = synth.planted((100, 100, 100), (6, 6, 6), 0.1, 50, scale="std", amp=5.0)
+    params = P.make_params(pr.T.shape, (8, 8, 8), stop=P.STOP_FIXED_ITERS, max_iter=1000)
+    plan, _ = P.pasd_plan(ctx, params)
+    Td = torch.from_numpy(pr.T).cuda()
+    L = torch.empty_like(Td); E = torch.empty_like(Td)
+    torch.cuda.synchronize()
+    ticket = P.pasd_submit(ctx, plan, Td, L, E)     # 1000 bodies: tens of milliseconds
+    host = np.zeros(1, np.float64)
+    for call in (lambda: P.pasd_plan_destroy(plan), lambda: P.pasd_solve(plan, Td, L, E),
+                 lambda: P.pasd_begin(plan, Td), lambda: P.pasd_iterate(plan, 1),
+                 lambda: P.pasd_finish(plan, L, E), lambda: P.pasd_state_get(plan, P.STATE_MU, 0, host)):
+        with pytest.raises(P.PasdError) as err:
+            call()
+        assert err.value.status == P.ERR_BUSY
+    import time
+    t0 = time.time()
+    while True:
+        st, r = P.pasd_poll(ctx, ticket)
+        if st != P.PENDING or time.time() - t0 > 60:
+            break
+        time.sleep(0.001)
+    assert st == P.OK and r.iters == 1000
+    served_L = L.clone()
+    res = P.pasd_solve(plan, Td, L, E)
+    assert res.iters == 1000 and torch.equal(L, served_L)
+    P.pasd_plan_destroy(plan)
+
+
 def test_invalid_and_nonfinite_inputs(env):
     torch, P, ctx = env
     with pytest.raises(P.PasdError) as ei:
