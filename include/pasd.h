@@ -118,7 +118,9 @@ typedef struct pasd_plan pasd_plan_t;
  * of the solver state the served path keeps resident (0 -> 90% of free HBM).
  * Creates the served-path scheduler thread lazily on the first pasd_submit. */
 pasd_status pasd_ctx_create(int device, size_t hbm_budget_bytes, pasd_ctx** out);
-/* Waits for served solves still in flight, then frees everything. */
+/* Waits for the served solves still queued or in flight, then frees the
+ * context. Plans made with a context must be destroyed before it (or never):
+ * pasd_plan_destroy reads the plan's context. */
 pasd_status pasd_ctx_destroy(pasd_ctx* ctx);
 
 /* Fills `p` with the paper's defaults (Algorithm 1 initialisation and the
