@@ -134,7 +134,8 @@ pasd_status pasd_params_default(pasd_params* p, int32_t order, const int64_t* di
  * device memory (that happens on first use); `footprint_bytes` (may be NULL)
  * receives the device bytes the state will take. Errors: INVALID_ARG when
  * N < 2, any R_n > I_n (the Stiefel set St(I_n, R_n) is empty) or R_n < 1,
- * a weight <= 0, rho <= 1 or mu_max < mu0; UNSUPPORTED when R_n > PASD_MAX_RANK.
+ * a weight <= 0, rho <= 1 or mu_max < mu0; UNSUPPORTED when R_n > PASD_MAX_RANK
+ * or when I_n x (R_n rounded up to its rank bucket, plus 4) reaches 2^31.
  * Environment, read here (for comparisons and debugging; the same arithmetic up
  * to the grouping of partial sums): PASD_NO_TMA=1 plans the kernels fed by per-thread asynchronous
  * copies instead of bulk tensor copies; PASD_NO_GRAPH=1 launches each loop

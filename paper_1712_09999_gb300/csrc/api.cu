@@ -268,6 +268,11 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
         g.P = g.pre * g.post;
         g.R = p.rank_bound[n];
         g.Rp = rank_bucket(g.R);
+        // the per-mode kernels index I_n x (Rp_n + 4) matrices with 32-bit offsets
+        if (g.I * (int64_t)(g.Rp + 4) >= ((int64_t)1 << 31)) {
+            delete pl;
+            return fail(PASD_ERR_UNSUPPORTED, "mode length times rank bucket reaches 2^31");
+        }
         double lam;
         if (p.lambda > 0) lam = pl->alpha[n] / p.lambda;
         else if (p.lambda_n[n] > 0) lam = p.lambda_n[n];

@@ -307,8 +307,8 @@ __device__ void inv_sqrt_from_eig(const float* D, const float* Q, int n, int ld,
 // dst[i][c] = src[i][c0 + c] for c < w, 0 for w <= c < round4(w); rows x ...
 // (eight elements per thread per pass, loaded before any is stored, so the
 // global reads overlap instead of forming a chain)
-// (32-bit index arithmetic: rows x 64 columns stays below 2^31 for every mode
-// the planner accepts.)
+// (32-bit index arithmetic: the planner accepts a mode only when
+// I_n x (Rp_n + 4) stays below 2^31.)
 __device__ void copy_cols(const float* src, int lds, int c0, int w, int64_t rows, float* dst, int ldd) {
     const int w4 = (w + 3) & ~3;
     const int tot = (int)rows * w4;
