@@ -285,6 +285,18 @@ def test_full_rank_bound_reduces_to_horpca(dims, tucker):
     assert np.allclose(res.E, e_h, rtol=0, atol=1e-9 * np.abs(t).max())
 
 
+def test_zero_tensor_stops_after_one_body_at_zero():
+    # T = 0 is a fixed point of Algorithm 1: G = 0, so A = 0, V = 0, Z = 0, E = 0 and
+    # Y stays 0; the residual is exactly zero, so the stop test holds after one body.
+    for dims, ranks in (((6, 5, 4), (2, 2, 2)), ((7, 3), (3, 3))):
+        res = O.pasd(np.zeros(dims), O.Params(ranks=ranks, lambdas=O.paper_lambdas(dims)))
+        assert res.converged and res.iters == 1
+        assert not res.L.any() and not res.E.any()
+        assert res.trace[0].kept == [0] * len(dims) and res.trace[0].res_inf == 0.0
+        for n, (i_n, r_n) in enumerate(zip(dims, ranks)):
+            assert np.array_equal(res.state.U[n], np.eye(i_n, r_n))
+
+
 def test_scale_equivariance():
     # (T, mu0, mu_max) -> (cT, mu0/c, mu_max/c) maps (L, E, Y) -> (cL, cE, Y): each
     # sub-step of Eq. 10, 13, 15 is homogeneous under this change.
