@@ -285,6 +285,18 @@ def test_full_rank_bound_reduces_to_horpca(dims, tucker):
     assert np.allclose(res.E, e_h, rtol=0, atol=1e-9 * np.abs(t).max())
 
 
+def test_default_weights_are_the_papers_setting():
+    # Sec. 5.1 sets lambda_n = sqrt(max(I_n, prod_{m != n} I_m)) / N. For the 50^3 cube
+    # that is sqrt(2500) / 3 = 50 / 3, the same as the (alpha_n, lambda) form with
+    # alpha_n = 1/3 and lambda = 1/50 (reading 1); for a 4-way 50^4 tensor
+    # sqrt(125000) / 4, and for a matrix sqrt(max(I_1, I_2)) / 2 per mode.
+    assert O.paper_lambdas((50, 50, 50)) == pytest.approx([50 / 3] * 3, rel=1e-15)
+    p = O.Params.from_alpha_lambda((10,) * 3, (1 / 3,) * 3, 1 / 50)
+    assert list(p.lambdas) == pytest.approx(O.paper_lambdas((50, 50, 50)), rel=1e-15)
+    assert O.paper_lambdas((50,) * 4) == pytest.approx([np.sqrt(125000) / 4] * 4, rel=1e-15)
+    assert O.paper_lambdas((9, 400)) == pytest.approx([10.0, 10.0], rel=1e-15)
+
+
 def test_zero_tensor_stops_after_one_body_at_zero():
     # T = 0 is a fixed point of Algorithm 1: G = 0, so A = 0, V = 0, Z = 0, E = 0 and
     # Y stays 0; the residual is exactly zero, so the stop test holds after one body.
