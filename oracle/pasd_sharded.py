@@ -22,7 +22,8 @@ Algorithm 1 is then local to a slab or needs one of these exchanges:
     reduce-scatter followed by an all-gather). V_m is the same on every rank.
   E-step (Eq. 14, Eq. 15), multipliers and Z_n are elementwise on the slab.
   Stop test: an all-reduce (max) of ||T - Z_n - E||_inf and an all-reduce
-    (sum) of the N squared Frobenius norms and ||E||_1.
+    (sum) of the N squared Frobenius norms and ||E||_1 (and, once before the
+    first body, of ||T||_F^2 for the relative residual).
 
 The small factors come from a tall-skinny QR: each rank factors its own rows
 (X_r = Q_r R_r), the R_r are gathered and the stack is factored again, which
