@@ -6,27 +6,26 @@ orthonormal Gaussian-QR factors, 20% of the entries corrupted by
 U[-1,1] * max|L0|), rank bounds R_n = 20, lambda = 1/200, alpha_n = 1/3, run to
 relative residual 1e-6 (max_n ||T - Z_n - E||_F / ||T||_F). Synthetic, seeded.
 
-A step is one ADMM loop body (U-step, V-step, E-step, multipliers, mu) over the
-whole tensor. The timed region replays the solve's own trajectory: it starts a
-new solve (pasd_begin) every `iters_to_converge` steps, so idle, active and
-converging iterations are all in it, inputs resident in HBM. The tensors the
-loop streams (T, E, G_1..G_3: 160 MB) exceed the 129 MB L2, so no L2 flush is
+A step is one whole solve of that workload through pasd_solve with the inputs
+resident in HBM (initialisation, every ADMM loop body until the stop rule, the
+output pass), so every timed step holds the idle, active and converging loop
+bodies of the trajectory; the metric counts loop bodies per second. The tensors
+the loop streams (T, E, G_1..G_3: 160 MB) exceed the 129 MB L2, so no L2 flush is
 added between steps.
 
 Extra keys: roofline of the dominant kernel (algorithmic bytes of the fused
 elementwise pass over its CUDA-event durations, every launch of one solve, with
 the idle and active bodies also reported apart), clocks sampled during the timed
 region, e2e (whole solves through pasd_solve_host with pinned host buffers),
-serving (Poisson arrivals of planted cubes of sides 32-256 through
-pasd_submit / pasd_poll, served with the FP32 path and with mixed precision,
-both with the idle-start skip: solves/s, p50 / p99 latency, against the same
-requests solved one at a time with the plain FP32 path), video (loop bodies/s
-on the 144x176x3x300 colour-video shape, FP32 and mixed), batched (64 uneven
-tensors, 8 of them hyperspectral-shaped, submitted at once), table1 (the
+cpu_baseline (the FP64 oracle on the host cores, a bounded sample), table1 (the
 paper's Table 1 workloads, 100^3 and 50^4, with the paper's own PASD results as
-context) and cpu_baseline (the FP64 oracle on the host cores, a bounded
-sample). Opt-in: --sweep (solve time against cube size) and --phase (the
-phase-transition map of the paper's Fig. 1 setting).
+context), video (whole solves on the 144x176x3x300 colour-video shape, FP32 and
+mixed), batched (64 uneven tensors, 8 of them hyperspectral-shaped, submitted at
+once) and serving (a Poisson trace of distinct requests through pasd_submit /
+pasd_poll: solves/s and p50 / p99 latency, against the same requests solved one
+at a time); the shorter summaries come last on the line. Opt-in: --sweep (solve
+time against cube size) and --phase (the phase-transition map of the paper's
+Fig. 1 setting).
 
 --impl reference times the FP64 oracle (the method as the paper defines it),
 each step one loop body on the same 200^3 workload.
@@ -213,20 +212,24 @@ def _percentile(xs, q):
 
 
 def _serving(P, torch, ctx, args):
-    """Continuous-batching service: Poisson arrivals of planted cubes through
-    pasd_submit / pasd_poll, served once with the FP32 path and once with mixed
-    precision (both with the idle-start skip), against the same requests solved
-    one at a time with the plain FP32 path."""
+    """Continuous-batching service on a Poisson trace of distinct requests: every
+    request is its own planted cube (side log-uniform on 32-256, Tucker ranks
+    3-20, R = floor(1.2 r), 5-30% corruption U[-1,1] max|L0|) with its own
+    precision (FP32 or mixed, Bernoulli(1/2)), served through pasd_submit /
+    pasd_poll with the idle-start skip. Plans are made per request before the
+    trace (a service keeps its plans; plan set-up is not in the latency). The same
+    requests solved one at a time are the baselines: the plain FP32 path, and the
+    FP32 path with the skip (the served flags)."""
     import numpy as np
     from paper_1712_09999_gb300 import synth
     dev = torch.device("cuda", torch.cuda.current_device())
-    specs = synth.serving_mix(args.serve_problems, seed=4)
-    tg = time.perf_counter()
-    probs = [synth.serving_problem(sp) for sp in specs]
-    gen_s = time.perf_counter() - tg
-    Ts = [torch.from_numpy(pr.T).to(dev) for pr in probs]
     n_req = int(args.serve_rate * args.serve_seconds)
-    which = np.random.Generator(np.random.PCG64(6)).integers(0, len(specs), size=n_req)
+    specs = synth.serving_mix(n_req, seed=4)
+    precs = synth.request_precisions(n_req, seed=7)
+    tg = time.perf_counter()
+    Ts = [synth.planted_device(sp.dims, sp.tucker, sp.rho, sp.seed, dev, scale="max")[0] for sp in specs]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - tg
 
     def timed_solve(plan, q, L, E):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -237,28 +240,31 @@ def _serving(P, torch, ctx, args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), r
 
-    # serial baseline: plain FP32 solves, one at a time
-    serial_ms, iters = [], []
-    for q, sp in enumerate(specs):
-        plan, _ = P.pasd_plan(ctx, P.make_params(sp.dims, sp.rank_bounds, max_iter=1000))
-        L = torch.empty_like(Ts[q])
-        E = torch.empty_like(Ts[q])
-        P.pasd_solve(plan, Ts[q], L, E)                  # allocation, graph capture, warm-up
-        ms, r = timed_solve(plan, q, L, E)
-        serial_ms.append(ms)
-        iters.append(int(r.iters))
+    def serial(flags, precision_of):
+        ms_all, iters, plans = [], [], []
+        for q, sp in enumerate(specs):
+            plan, _ = P.pasd_plan(ctx, P.make_params(sp.dims, sp.rank_bounds, max_iter=1000,
+                                                     precision=precision_of(q), flags=flags))
+            L = torch.empty_like(Ts[q])
+            E = torch.empty_like(Ts[q])
+            P.pasd_solve(plan, Ts[q], L, E)              # allocation, graph capture, warm-up
+            ms, r = timed_solve(plan, q, L, E)
+            ms_all.append(ms)
+            iters.append(int(r.iters))
+            plans.append((plan, L, E))
+        return ms_all, iters, plans
+
+    plain_ms, plain_iters, plain_plans = serial(0, lambda q: P.PREC_FP32)
+    for plan, _, _ in plain_plans:
         P.pasd_plan_destroy(plan)
-    serial_s = sum(serial_ms[int(q)] for q in which) / 1000.0
+    skip_ms, _, _tmp = serial(P.F_SKIP_IDLE, lambda q: P.PREC_FP32)
+    for plan, _, _ in _tmp:
+        P.pasd_plan_destroy(plan)
+    # served plans: per-request precision, the skip; warmed by one solve each
+    _, _, slots = serial(P.F_SKIP_IDLE, lambda q: P.PREC_MIXED if precs[q] else P.PREC_FP32)
 
-    def trace(rate):
-        n = int(rate * args.serve_seconds)
+    def run(rate, n):
         arr = synth.poisson_arrivals(rate, n, seed=5)
-        wh = np.random.Generator(np.random.PCG64(6)).integers(0, len(specs), size=n)
-        return n, arr, wh
-
-    def run(slots, rate):
-        n, arr, wh = trace(rate)
-        nxt = [0] * len(specs)
         pending = {}
         lat, finish, bad = [], [], 0
         torch.cuda.synchronize()
@@ -267,10 +273,8 @@ def _serving(P, torch, ctx, args):
         while i < n or pending:
             now = time.perf_counter() - t0
             while i < n and arr[i] <= now:
-                q = int(wh[i])
-                plan, L, E = slots[q][nxt[q]]
-                nxt[q] = (nxt[q] + 1) % len(slots[q])
-                pending[P.pasd_submit(ctx, plan, Ts[q], L, E)] = float(arr[i])
+                plan, L, E = slots[i]
+                pending[P.pasd_submit(ctx, plan, Ts[i], L, E)] = float(arr[i])
                 i += 1
             for tk in list(pending):
                 st, _ = P.pasd_poll(ctx, tk)
@@ -281,47 +285,25 @@ def _serving(P, torch, ctx, args):
                     bad += st not in (P.OK, P.NOT_CONVERGED)
             time.sleep(0.0002)
         span = max(finish) - float(arr[0])
-        return {"offered_rate": rate, "requests": n, "solves_per_s": n / span,
-                "p50_ms": 1000 * _percentile(lat, 50), "p99_ms": 1000 * _percentile(lat, 99), "failed": bad}
+        return {"rate": rate, "n": n, "solves_per_s": round(n / span, 1),
+                "p50_ms": round(1000 * _percentile(lat, 50), 1), "p99_ms": round(1000 * _percentile(lat, 99), 1),
+                "failed": bad}
 
-    def serve(precision):
-        slots, outs, skipped, one_ms = [], [], [], []
-        for q, sp in enumerate(specs):
-            prm = P.make_params(sp.dims, sp.rank_bounds, max_iter=1000, precision=precision, flags=P.F_SKIP_IDLE)
-            row = []
-            for _ in range(args.serve_slots):
-                plan, _ = P.pasd_plan(ctx, prm)
-                L = torch.empty_like(Ts[q])
-                E = torch.empty_like(Ts[q])
-                P.pasd_solve(plan, Ts[q], L, E)          # allocation, graph capture, warm-up
-                row.append((plan, L, E))
-            ms, r = timed_solve(row[0][0], q, row[0][1], row[0][2])
-            one_ms.append(round(ms, 2))
-            skipped.append(int(r.skipped))
-            outs.append(row[0][1].clone())
-            slots.append(row)
-        out = run(slots, args.serve_rate)
-        del out["offered_rate"], out["requests"]
-        out["below_capacity"] = run(slots, args.serve_low_rate)
-        out["skipped_per_solve"] = skipped
-        out["solo_ms_per_solve"] = one_ms
-        for row in slots:
-            for plan, _, _ in row:
-                P.pasd_plan_destroy(plan)
-        return out, outs
-
-    fp32, out32 = serve(P.PREC_FP32)
-    mixed, outmx = serve(P.PREC_MIXED)
-    mixed["L_rel_vs_fp32_max"] = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
-                                     for a, b in zip(outmx, out32))
-    return {"offered_rate": args.serve_rate, "requests": n_req, "fp32": fp32, "mixed": mixed,
-            "serial_plain_fp32_solves_per_s": n_req / serial_s,
-            "mix": f"{len(specs)} planted cubes, side log-uniform 32-256, Tucker 3-20, R=floor(1.2 r), "
-                   f"5-30% corruption (seed 4); {args.serve_slots} plans per problem; Poisson arrivals "
-                   f"(seed 5) for {args.serve_seconds} s; served solves use the idle-start skip; below_capacity: "
-                   f"the same trace at {args.serve_low_rate} requests/s",
-            "sides": [sp.dims[0] for sp in specs], "iters_per_solve": iters,
-            "serial_ms_per_solve": [round(x, 2) for x in serial_ms], "generation_s": round(gen_s, 1)}
+    over = run(args.serve_rate, n_req)
+    low_n = max(1, int(args.serve_low_rate * args.serve_seconds))
+    low = run(args.serve_low_rate, low_n)
+    for plan, _, _ in slots:
+        P.pasd_plan_destroy(plan)
+    serial_plain = n_req / (sum(plain_ms) / 1000.0)
+    serial_skip = n_req / (sum(skip_ms) / 1000.0)
+    return {"trace": f"{n_req} distinct requests, Poisson {args.serve_rate:g}/s for {args.serve_seconds:g} s "
+                     f"(reduced from 60 s), cubes 32-256 log-uniform, Tucker 3-20, R=floor(1.2r), 5-30% "
+                     f"corruption, {int(precs.sum())} mixed / {n_req - int(precs.sum())} FP32, idle-start skip",
+            "served": over, "below_capacity": low,
+            "serial_plain_fp32_solves_per_s": round(serial_plain, 1),
+            "serial_fp32_skip_solves_per_s": round(serial_skip, 1),
+            "served_over_serial_plain": round(over["solves_per_s"] / serial_plain, 2),
+            "iters_mean": round(float(np.mean(plain_iters)), 1), "generation_s": round(gen_s, 1)}
 
 
 def _batched(P, torch, ctx, args):
@@ -330,7 +312,8 @@ def _batched(P, torch, ctx, args):
     pasd_submit (one stream per solve, overlapping on the GPU; one captured graph
     per loop body), with the FP32 path and with mixed precision (both with the
     idle-start skip), against the same solves run one at a time with the plain
-    FP32 path. Recovery error is against the planted low-rank part."""
+    FP32 path and with the FP32 path plus the skip (the batched flags). Recovery
+    error is against the planted low-rank part."""
     import numpy as np
     from paper_1712_09999_gb300 import synth
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -341,20 +324,25 @@ def _batched(P, torch, ctx, args):
     Ts = [torch.from_numpy(pr.T).to(dev) for pr in probs]
     L0s = [torch.from_numpy(pr.L0).to(dev) for pr in probs]
 
-    serial_ms = []
-    for q, sp in enumerate(specs):
-        plan, _ = P.pasd_plan(ctx, P.make_params(sp.dims, sp.rank_bounds, max_iter=1000))
-        L = torch.empty_like(Ts[q])
-        E = torch.empty_like(Ts[q])
-        P.pasd_solve(plan, Ts[q], L, E)              # allocation, graph capture, warm-up
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        P.pasd_solve(plan, Ts[q], L, E)
-        e1.record()
-        torch.cuda.synchronize()
-        serial_ms.append(e0.elapsed_time(e1))
-        P.pasd_plan_destroy(plan)
+    def serial(flags):
+        ms_all = []
+        for q, sp in enumerate(specs):
+            plan, _ = P.pasd_plan(ctx, P.make_params(sp.dims, sp.rank_bounds, max_iter=1000, flags=flags))
+            L = torch.empty_like(Ts[q])
+            E = torch.empty_like(Ts[q])
+            P.pasd_solve(plan, Ts[q], L, E)              # allocation, graph capture, warm-up
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            P.pasd_solve(plan, Ts[q], L, E)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_all.append(e0.elapsed_time(e1))
+            P.pasd_plan_destroy(plan)
+        return len(specs) / (sum(ms_all) / 1000.0)
+
+    serial_plain = serial(0)
+    serial_skip = serial(P.F_SKIP_IDLE)
 
     def batch(precision):
         plans, Ls, Es = [], [], []
@@ -384,19 +372,18 @@ def _batched(P, torch, ctx, args):
                for q in range(len(specs))]
         for plan in plans:
             P.pasd_plan_destroy(plan)
-        return {"solves_per_s": len(specs) / wall, "wall_s": wall, "failed": bad,
-                "rse_median": float(np.median(rse)), "rse_max": max(rse),
-                "iters_total": sum(iters), "skipped_total": sum(skipped)}, Ls
+        return {"solves_per_s": round(len(specs) / wall, 1), "failed": bad,
+                "rse_median": float(np.median(rse)), "iters": sum(iters), "skipped": sum(skipped)}, Ls
 
     fp32, l32 = batch(P.PREC_FP32)
     mixed, lmx = batch(P.PREC_MIXED)
     mixed["L_rel_vs_fp32_max"] = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
                                      for a, b in zip(lmx, l32))
-    return {"workload": "56 planted tensors (sides U{32..160} per mode, Tucker 3-15, R = floor(1.2 r), 5-30% "
-                        "additive corruption) + 8 hyperspectral 128x128x191 (spatial rank 3-15, spectral rank 4, "
-                        "5-30% salt and pepper), seed 3; all submitted at once",
-            "solves": len(specs), "fp32": fp32, "mixed": mixed,
-            "serial_plain_fp32_solves_per_s": len(specs) / (sum(serial_ms) / 1000.0),
+    return {"workload": "64 solves at once: 56 planted (sides U{32..160}, Tucker 3-15, 5-30%) + 8 hyperspectral "
+                        "128x128x191 (salt and pepper), seed 3, idle-start skip",
+            "fp32": fp32, "mixed": mixed,
+            "serial_plain_fp32_solves_per_s": round(serial_plain, 1),
+            "serial_fp32_skip_solves_per_s": round(serial_skip, 1),
             "generation_s": round(gen_s, 1)}
 
 
@@ -433,11 +420,11 @@ def _table1(P, torch, ctx, args):
             P.pasd_plan_destroy(plan)
             rse = float(torch.linalg.vector_norm(L.double() - L0) / torch.linalg.vector_norm(L0))
             prse, psec = PAPER_TABLE1[(name, rho)]
-            rows.append({"size": name, "rho": rho, "iters": int(r.iters), "status": int(r.status),
-                         "ms_per_solve": round(e0.elapsed_time(e1), 2), "rse": rse,
-                         "paper_rse": prse, "paper_s_per_solve": psec})
+            rows.append([name, rho, int(r.iters), int(r.status), round(e0.elapsed_time(e1), 2),
+                         float("%.3g" % rse), prse, psec])
     return {"workload": "Table 1 family: Tucker rank 10, R_n = 12, U[-1,1] additive corruption, paper lambda_n, "
-                        "eps = 1e-5 (seed 7)", "paper_hardware": "Matlab 8.1, Intel Xeon E5-2620 2.0 GHz (context only)",
+                        "eps = 1e-5 (seed 7); paper: Matlab 8.1, Xeon E5-2620 2.0 GHz (context only)",
+            "columns": ["size", "rho", "iters", "status", "ms_per_solve", "rse", "paper_rse", "paper_s_per_solve"],
             "rows": rows}
 
 
@@ -525,32 +512,37 @@ def _phase(P, torch, ctx, args):
 
 def _video(P, torch, ctx, args):
     """Loop bodies per second on the colour-video shape 144x176x3x300, R = (20, 20, 3, 5),
-    the paper's default lambda_n, timed over a fixed number of bodies past the activation."""
+    the paper's default lambda_n, over one whole solve to Algorithm 1's stop rule
+    (eps = 1e-5), FP32 and mixed precision; per-kernel milliseconds per body from
+    CUDA events over the same trajectory."""
+    import numpy as np
     from paper_1712_09999_gb300 import synth
     dev = torch.device("cuda", torch.cuda.current_device())
     pr = synth.video()
     T = torch.from_numpy(pr.T).to(dev)
     stream = torch.cuda.current_stream()
     out = {"workload": "video 144x176x3x300 (rank-1 background, 16 moving rectangles, 5% voxels, seed 2), "
-                       "R=(20,20,3,5), paper-default lambda_n",
-           "bodies_timed": [args.video_pre + 1, args.video_pre + args.video_iters]}
+                       "R=(20,20,3,5), paper lambda_n, whole solve to eps=1e-5"}
     for name, prec in (("fp32", P.PREC_FP32), ("mixed", P.PREC_MIXED)):
-        plan, footprint = P.pasd_plan(ctx, P.make_params(pr.T.shape, (20, 20, 3, 5), stop=P.STOP_FIXED_ITERS,
-                                                         max_iter=10 ** 6, precision=prec))
-        P.pasd_begin(plan, T, stream)
-        P.pasd_iterate(plan, args.video_pre, stream)
-        torch.cuda.synchronize()
+        plan, footprint = P.pasd_plan(ctx, P.make_params(pr.T.shape, (20, 20, 3, 5), max_iter=1000, precision=prec))
+        L = torch.empty_like(T)
+        E = torch.empty_like(T)
+        P.pasd_solve(plan, T, L, E, stream)          # allocation, graph capture, warm-up
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        P.pasd_iterate(plan, args.video_iters, stream)
+        r = P.pasd_solve(plan, T, L, E, stream)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        tr = __import__("numpy").zeros((args.video_pre + args.video_iters, P.TRACE_STRIDE))
-        P.pasd_state_get(plan, P.STATE_TRACE, 0, tr)
+        rse = float(torch.linalg.vector_norm(L.double() - torch.from_numpy(pr.L0).to(dev)) /
+                    float(np.linalg.norm(pr.L0)))
+        P.pasd_begin(plan, T, stream)
+        per = P.pasd_profile_iterations(plan, int(r.iters), stream)
         P.pasd_plan_destroy(plan)
-        out[name] = {"iters_per_s": args.video_iters / (ms / 1000.0), "kept_at_end": tr[-1, 5:9].astype(int).tolist()}
+        out[name] = {"iters_per_s": round(r.iters / (ms / 1000.0), 1), "iters": int(r.iters),
+                     "ms_per_solve": round(ms, 2), "rse": rse, "kept": list(r.kept)[:4],
+                     "kernel_us_per_body": {k: round(1000 * v / r.iters, 1) for k, v in per.items()}}
         out["footprint_bytes"] = footprint
     return out
 
@@ -565,6 +557,20 @@ def _job_time_and_value(ms: float, steps: int, world: int, dist, device):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     return ms, world * steps / (ms / 1000.0)
+
+
+def _bodies_launched(k: int, chunk: int, max_iter: int) -> int:
+    """Loop bodies pasd_solve enqueues for a solve that stops after k bodies: it
+    launches `chunk` bodies, then keeps one chunk in flight while it reads the
+    device stop flag of the previous one, so it sees the flag of body k only
+    after launching the chunk that follows; bodies past the stop return at once."""
+    launched = min(chunk, max_iter)
+    while True:
+        seen = launched
+        if launched < max_iter:
+            launched += min(chunk, max_iter - launched)
+        if seen >= k or launched >= max_iter:
+            return launched
 
 
 def run_ours(args):
@@ -593,29 +599,18 @@ def run_ours(args):
     ctx = P.pasd_ctx_create(torch.cuda.current_device())
     stream = torch.cuda.current_stream()
 
-    # calibration solve: iterations this workload takes to reach the stop rule
+    # A step is one whole solve of the workload (pasd_solve on device buffers:
+    # initialisation, every loop body until the stop rule, the output pass), so
+    # the timed region holds the idle, active and converging bodies of each
+    # trajectory; the metric counts loop bodies.
     sp = P.make_params(DIMS, RANKS, alpha=ALPHA, lam=LAMBDA, stop=P.STOP_FRO_REL, tol=TOL, max_iter=1000)
-    splan, _ = P.pasd_plan(ctx, sp)
+    plan, footprint = P.pasd_plan(ctx, sp)
     L = torch.empty_like(T)
     E = torch.empty_like(T)
-    r = P.pasd_solve(splan, T, L, E, stream)
-    k_conv = r.iters
-
-    # timed loop: one loop body per step, a fresh solve every k_conv steps
-    n_total = args.warmup + args.steps + 64
-    tp = P.make_params(DIMS, RANKS, alpha=ALPHA, lam=LAMBDA, stop=P.STOP_FIXED_ITERS, max_iter=k_conv + 1)
-    plan, footprint = P.pasd_plan(ctx, tp)
-
-    pos = [0]
-
-    def step():
-        if pos[0] % k_conv == 0:
-            P.pasd_begin(plan, T, stream)
-        P.pasd_iterate(plan, 1, stream)
-        pos[0] += 1
-
+    r = P.pasd_solve(plan, T, L, E, stream)          # allocation, graph capture
+    k_conv = int(r.iters)
     for _ in range(args.warmup):
-        step()
+        P.pasd_solve(plan, T, L, E, stream)
     torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device())
     time.sleep(0.15)
@@ -625,17 +620,21 @@ def run_ours(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
+    iters = 0
     for _ in range(args.steps):
-        step()
+        iters += int(P.pasd_solve(plan, T, L, E, stream).iters)
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     clocks = sampler.stop()
-    ms, value = _job_time_and_value(ev0.elapsed_time(ev1), args.steps, world, dist, dev)
+    assert iters == args.steps * k_conv
+    ms, value = _job_time_and_value(ev0.elapsed_time(ev1), iters, world, dist, dev)
+    lpi = P.pasd_launches_per_iter(plan)
+    launches_per_solve = 3 + _bodies_launched(k_conv, 8, 1000) * lpi + 1
 
     # dominant kernel: per-kernel CUDA-event durations for every body of one solve,
-    # i.e. the trajectory the timed region replays (idle and active bodies alike)
+    # the trajectory each timed step runs (idle and active bodies alike)
     P.pasd_begin(plan, T, stream)
     per_body = [P.pasd_profile_iterations(plan, 1, stream) for _ in range(k_conv)]
     D = int(np.prod(DIMS))
@@ -643,8 +642,9 @@ def run_ours(args):
     tr = np.zeros((k_conv, P.TRACE_STRIDE))
     P.pasd_state_get(plan, P.STATE_TRACE, 0, tr)
     kept = tr[:, 5:5 + N]
-    # algorithmic bytes of one fused pass: read T, E, G_1..G_N, write E, G_1..G_N,
-    # read the kept rows of each Vrot_n once (kept counts of that body)
+    # algorithmic bytes of one fused pass: read T, G_1..G_N, write E, G_1..G_N, read
+    # E (the previous iterate, which the multiplier update needs), read the kept rows
+    # of each Vrot_n once (kept counts of that body)
     alg = np.array([(2 * N + 3) * 4 * D + 4 * sum(float(s) * (D // I) for s, I in zip(kept[b], DIMS))
                     for b in range(k_conv)])
     fused = np.array([pb["fused"] for pb in per_body]) / 1000.0        # seconds per launch
@@ -652,100 +652,106 @@ def run_ours(args):
     peak, peak_kind = _peaks()
 
     def phase(mask):
-        return {"bodies": int(mask.sum()), "launch_ms": float(fused[mask].mean() * 1000),
-                "alg_bytes_per_launch": float(alg[mask].mean()),
-                "achieved": float(alg[mask].sum() / fused[mask].sum() / 1e9),
-                "frac": float(alg[mask].sum() / fused[mask].sum() / 1e9 / peak)}
+        return {"bodies": int(mask.sum()), "launch_us": round(float(fused[mask].mean() * 1e6), 1),
+                "frac": round(float(alg[mask].sum() / fused[mask].sum() / 1e9 / peak), 3)}
 
     achieved = float(alg.sum() / fused.sum() / 1e9)
     tr_idle, tr_active = _fused_traffic()
     traffic = None
     if tr_idle is not None and tr_active is not None:
         traffic = (tr_idle * int((~active).sum()) + tr_active * int(active.sum())) / k_conv
-    roofline = {"bound": "hbm", "kernel": "fused elementwise pass (refold Z_n, E-step, multipliers, residuals)",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+    roofline = {"bound": "hbm", "kernel": "fused elementwise pass",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_kind": peak_kind, "traffic": traffic, "alg_bytes_per_launch": float(alg.mean()),
                 "launch_ms": float(fused.mean() * 1000),
-                "averaged_over": f"every launch of one {k_conv}-body solve (the trajectory the timed region replays)",
+                "averaged_over": f"every launch of one {k_conv}-body solve",
                 "phases": {"idle": phase(~active), "active": phase(active)},
-                "kernel_ms_per_iter": {k: float(np.mean([pb[k] for pb in per_body])) for k in per_body[0]}}
+                "kernel_us_per_body": {k: round(1000 * float(np.mean([pb[k] for pb in per_body])), 1)
+                                       for k in per_body[0]}}
 
-    # e2e: whole solves through the public host-buffer entry point
+    # e2e: whole solves through the public host-buffer entry point, pinned host buffers
     Lh = torch.empty(DIMS, dtype=torch.float32).pin_memory()
     Eh = torch.empty(DIMS, dtype=torch.float32).pin_memory()
+    P.pasd_solve_host(plan, T_host, Lh, Eh, stream)       # staging allocation
     it_sum, t_sum = 0, 0.0
     for _ in range(max(1, args.e2e_solves)):
         t0 = time.perf_counter()
-        rr = P.pasd_solve_host(splan, T_host, Lh, Eh, stream)
+        rr = P.pasd_solve_host(plan, T_host, Lh, Eh, stream)
         t_sum += time.perf_counter() - t0
         it_sum += rr.iters
     e2e_v = world * it_sum / t_sum
-    e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 4 * D / k_conv,
-           "d2h_bytes_per_step": 8 * D / k_conv,
-           "note": f"whole solves via pasd_solve_host from pinned host memory ({k_conv} bodies each); "
-                   "one T upload and one L, E download per solve, amortised per body"}
+    e2e = {"value": round(e2e_v, 1), "unit": UNIT, "h2d_bytes_per_step": 4 * D, "d2h_bytes_per_step": 8 * D,
+           "note": f"whole solves via pasd_solve_host from pinned host memory: a step is one solve "
+                   f"({k_conv} bodies) with one T upload and one L, E download"}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU",
-                           iters_to_converge=k_conv, footprint_bytes=footprint),
-            "clocks": clocks, "roofline": roofline, "e2e": e2e,
-            "gpu_launches": args.steps * P.pasd_launches_per_iter(plan) +
-                            3 * sum(1 for q in range(args.warmup, args.warmup + args.steps) if q % k_conv == 0)}
-    if rank == 0 and not args.no_serving:
-        line["serving"] = _serving(P, torch, ctx, args)
-    if rank == 0 and not args.no_video:
-        line["video"] = _video(P, torch, ctx, args)
-    if rank == 0 and not args.no_batched:
-        line["batched"] = _batched(P, torch, ctx, args)
+            "config": dict(CONFIG, step=f"one whole solve ({k_conv} loop bodies)",
+                           ms_per_body=round(ms / iters, 4),
+                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                           footprint_bytes=footprint),
+            "gpu_launches": args.steps * launches_per_solve, "clocks": clocks, "roofline": roofline, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n, el = _oracle_iters_per_s(pr.T, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": round(v, 3), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{n} FP64 loop bodies of the 200^3 workload in {el:.1f} s "
+                                          "(numpy/LAPACK, BLAS threads = all cores)"}
+        one = _oracle_one_core(args.cpu_seconds)
+        if one is not None:
+            line["cpu_baseline"]["single_core"] = {
+                "value": round(one[0], 3), "unit": UNIT, "cores": 1,
+                "sample": f"{one[1]} FP64 loop bodies in {one[2]:.1f} s, one BLAS/OpenMP thread"}
     if rank == 0 and not args.no_table1:
         line["table1"] = _table1(P, torch, ctx, args)
     if rank == 0 and args.sweep:
         line["sweep"] = _sweep(P, torch, ctx, args)
     if rank == 0 and args.phase:
         line["phase"] = _phase(P, torch, ctx, args)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, n, el = _oracle_iters_per_s(pr.T, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"{n} FP64 loop bodies of the 200^3 workload in {el:.1f} s "
-                                          "(numpy/LAPACK, BLAS threads = all cores)"}
-        one = _oracle_one_core(args.cpu_seconds)
-        if one is not None:
-            line["cpu_baseline"]["single_core"] = {
-                "value": one[0], "unit": UNIT, "cores": 1,
-                "sample": f"{one[1]} FP64 loop bodies in {one[2]:.1f} s, BLAS and OpenMP limited to one thread"}
+    if rank == 0 and not args.no_video:
+        line["video"] = _video(P, torch, ctx, args)
+    if rank == 0 and not args.no_batched:
+        line["batched"] = _batched(P, torch, ctx, args)
+    if rank == 0 and not args.no_serving:
+        line["serving"] = _serving(P, torch, ctx, args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     P.pasd_plan_destroy(plan)
-    P.pasd_plan_destroy(splan)
     P.pasd_ctx_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()
 
 
 def run_profile_workload(args):
-    """For ncu: plan the 200^3 workload, run `pre` loop bodies, then `iters` more, exit.
-    Launch order per body: polar, A-pass (one launch per group of modes with the
-    same padded rank), SVT, Vrot, fused pass, M-pass, finalize; pasd_begin
-    launches 3 kernels first. --mixed plans it with mixed precision."""
+    """For ncu: plan a workload, run `pre` loop bodies, then `iters` more, exit.
+    --workload cube200 (default): the 200^3 workload; video: the 144x176x3x300
+    colour-video shape with R = (20, 20, 3, 5). Launch order per body: polar,
+    A-pass (one launch per group of modes with the same padded rank), SVT, Vrot,
+    fused pass, M-pass, finalize; pasd_begin launches 3 kernels first. --mixed
+    plans it with mixed precision."""
     import torch
     import __graft_entry__ as ge
     ge.build()
     from paper_1712_09999_gb300 import pasd as P
     from paper_1712_09999_gb300 import synth
     torch.cuda.set_device(0)
-    pr = synth.cube_200(1)
+    prec = P.PREC_MIXED if args.mixed else P.PREC_FP32
+    if args.workload == "video":
+        pr = synth.video()
+        params = P.make_params(pr.T.shape, (20, 20, 3, 5), stop=P.STOP_FIXED_ITERS,
+                               max_iter=args.pre + args.iters + 1, precision=prec)
+    else:
+        pr = synth.cube_200(1)
+        params = P.make_params(DIMS, RANKS, alpha=ALPHA, lam=LAMBDA, stop=P.STOP_FIXED_ITERS,
+                               max_iter=args.pre + args.iters + 1, precision=prec)
     T = torch.from_numpy(pr.T).cuda()
     ctx = P.pasd_ctx_create(0)
-    plan, _ = P.pasd_plan(ctx, P.make_params(DIMS, RANKS, alpha=ALPHA, lam=LAMBDA,
-                                             stop=P.STOP_FIXED_ITERS, max_iter=args.pre + args.iters + 1,
-                                             precision=P.PREC_MIXED if args.mixed else P.PREC_FP32))
+    plan, _ = P.pasd_plan(ctx, params)
     P.pasd_begin(plan, T)
     P.pasd_iterate(plan, args.pre)
     P.pasd_iterate(plan, args.iters)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_workload": "200^3", "pre": args.pre, "iters": args.iters,
+    print(json.dumps({"profile_workload": args.workload, "pre": args.pre, "iters": args.iters,
                       "launches_per_iter": P.pasd_launches_per_iter(plan)}))
     P.pasd_plan_destroy(plan)
     P.pasd_ctx_destroy(ctx)
@@ -758,20 +764,20 @@ def main():
     ap.add_argument("--pre", type=int, default=120)
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--mixed", action="store_true", help="--profile-workload with mixed precision")
+    ap.add_argument("--workload", default="cube200", choices=["cube200", "video"],
+                    help="--profile-workload: which workload")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20, help="timed whole solves")
+    ap.add_argument("--warmup", type=int, default=3, help="untimed whole solves before the timed ones")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-solves", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-throughput measurement")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate (requests/s)")
-    ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window (s)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window (s)")
     ap.add_argument("--serve-low-rate", type=float, default=40.0,
                     help="second arrival rate, below capacity, for service-time latencies")
-    ap.add_argument("--serve-problems", type=int, default=8)
-    ap.add_argument("--serve-slots", type=int, default=3, help="plans per problem")
     ap.add_argument("--no-video", action="store_true", help="skip the video-shape measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload measurement")
     ap.add_argument("--no-table1", action="store_true", help="skip the paper's Table 1 workloads")
@@ -780,8 +786,6 @@ def main():
     ap.add_argument("--phase", action="store_true", help="phase-transition map on 100^3")
     ap.add_argument("--phase-trials", type=int, default=10)
     ap.add_argument("--phase-slots", type=int, default=16)
-    ap.add_argument("--video-pre", type=int, default=150)
-    ap.add_argument("--video-iters", type=int, default=200)
     ap.add_argument("--oracle-one-core", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_one_core is not None:

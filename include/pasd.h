@@ -70,10 +70,13 @@ typedef struct {
     int32_t order;                        /* N >= 2                                    */
     int64_t dims[PASD_MAX_ORDER];         /* I_1..I_N (C order)                        */
     int32_t rank_bound[PASD_MAX_ORDER];   /* R_n, 1 <= R_n <= min(I_n, PASD_MAX_RANK)   */
-    double alpha[PASD_MAX_ORDER];         /* output weights alpha_n > 0; 0 -> 1/N       */
+    double alpha[PASD_MAX_ORDER];         /* output weights alpha_n: all finite and > 0,
+                                             or all 0 for the default 1/N (a mix of
+                                             zero and nonzero entries is INVALID_ARG)  */
     double lambda;                        /* > 0: lambda_n = alpha_n / lambda          */
     double lambda_n[PASD_MAX_ORDER];      /* used when lambda <= 0: per-mode nuclear
-                                             weights; 0 -> sqrt(max(I_n, D/I_n)) / N   */
+                                             weights, finite and >= 0;
+                                             0 -> sqrt(max(I_n, D/I_n)) / N            */
     double mu0;                           /* 0 -> 1e-4                                  */
     double mu_max;                        /* 0 -> 1e10                                  */
     double rho;                           /* 0 -> 1.1 (must be > 1)                     */
@@ -116,7 +119,10 @@ typedef struct pasd_plan pasd_plan_t;
 
 /* Context on one CUDA device. `hbm_budget_bytes` bounds the summed footprint
  * of the solver state the served path keeps resident (0 -> 90% of free HBM).
- * Creates the served-path scheduler thread lazily on the first pasd_submit. */
+ * Creates the served-path scheduler thread lazily on the first pasd_submit.
+ * The submit queue holds at most 4096 solves that wait for admission; the
+ * environment variable PASD_MAX_QUEUE (an integer >= 1, read here) sets
+ * another bound. */
 pasd_status pasd_ctx_create(int device, size_t hbm_budget_bytes, pasd_ctx** out);
 /* Waits for the served solves still queued or in flight, then frees the
  * context. Plans made with a context must be destroyed before it (or never):
@@ -134,12 +140,17 @@ pasd_status pasd_params_default(pasd_params* p, int32_t order, const int64_t* di
  * device memory (that happens on first use); `footprint_bytes` (may be NULL)
  * receives the device bytes the state will take. Errors: INVALID_ARG when
  * N < 2, any R_n > I_n (the Stiefel set St(I_n, R_n) is empty) or R_n < 1,
- * a weight <= 0, rho <= 1 or mu_max < mu0; UNSUPPORTED when R_n > PASD_MAX_RANK
+ * a weight that is negative, not finite or (for alpha) zero beside nonzero
+ * ones, rho <= 1 or mu_max < mu0; UNSUPPORTED when R_n > PASD_MAX_RANK
  * or when I_n x (R_n rounded up to its rank bucket, plus 4) reaches 2^31.
  * Environment, read here (for comparisons and debugging; the same arithmetic up
  * to the grouping of partial sums): PASD_NO_TMA=1 plans the kernels fed by per-thread asynchronous
  * copies instead of bulk tensor copies; PASD_NO_GRAPH=1 launches each loop
- * body's kernels directly instead of replaying a captured CUDA graph. */
+ * body's kernels directly instead of replaying a captured CUDA graph.
+ * Test hook: PASD_TEST_WAIT_TIMEOUT=1 makes the plan's bulk-copy-fed
+ * elementwise pass issue no copy at all and give up its wait after a few
+ * thousand polls, so the first loop body ends the solve with PASD_ERR_TIMEOUT
+ * (nothing is in flight when the kernels return; the context stays usable). */
 pasd_status pasd_plan(pasd_ctx* ctx, const pasd_params* p, pasd_plan_t** out,
                       size_t* footprint_bytes);
 pasd_status pasd_plan_destroy(pasd_plan_t* plan);
@@ -243,9 +254,11 @@ pasd_status pasd_mode_product(const float* X, int64_t pre, int64_t I, int64_t po
  * (held on every device that loads the library until the process exits), so
  * the call allocates nothing and is asynchronous on `stream`. Limit:
  * ceil(pre*post/256) * R * R <= 1048576, else UNSUPPORTED (outputs untouched).
- * The first call on a device looks up the scratch's device address (with that
- * device current) and clears the scratch's flags on `stream`, waiting for that
- * clear (so that call returns after it); make it before any stream capture. All calls share the
+ * Every call looks up the scratch's device address on the current device (a
+ * host-side lookup, no device work). The first call on a device, and the first
+ * after a cudaDeviceReset of it, also clears the scratch's flags on `stream`,
+ * waiting for that clear (so that call returns after it); make it before any
+ * stream capture. All calls share the
  * scratch and it keeps the last call's contents: calls whose work overlaps on
  * the GPU race on it and must be serialised by the caller. */
 pasd_status pasd_mode_product_noalloc(const float* X, int64_t pre, int64_t I, int64_t post,

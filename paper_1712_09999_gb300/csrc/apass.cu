@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(AP_THREADS) apass_kernel(const ApassMulti mm) 
 template <int RP>
 static void launch_rp(const ApassMulti& mm, cudaStream_t s) {
     size_t smem = std::max(apass_smem_bytes(RP, false), apass_smem_bytes(RP, true));
-    cudaFuncSetAttribute(apass_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_smem_attr((const void*)apass_kernel<RP>, (int)smem);
     apass_kernel<RP><<<mm.cta_start[mm.count], AP_THREADS, smem, s>>>(mm);
 }
 
@@ -482,12 +482,13 @@ __global__ void __launch_bounds__(AtShape<RP>::THREADS) apass_tma_kernel(const _
 #pragma unroll
         for (int r = 0; r < RP; ++r) acc[q][r] = 0.f;
     bool failed = false;
+    int fail_kc = 0;
     for (int kc = 0; kc < nk; ++kc) {
         const int st = kc % AT_STAGES;
         const uint32_t par = (uint32_t)((kc / AT_STAGES) & 1);
         const bool ok = mbar_wait_bounded(&full[st], par, kWaitPolls);
         // also orders every thread's reads of the stage refilled below
-        if (__syncthreads_or(!ok)) { failed = true; break; }
+        if (__syncthreads_or(!ok)) { failed = true; fail_kc = kc; break; }
         if (t == 0 && kc + AT_STAGES - 1 < nk) issue(kc + AT_STAGES - 1);
         const float* gs = smem + st * sst;
         const float* us = gs + gfl;
@@ -545,7 +546,9 @@ __global__ void __launch_bounds__(AtShape<RP>::THREADS) apass_tma_kernel(const _
         // a copy never landed: record it and leave once the copies in flight are
         // accounted for (bounded), so no copy writes into a reassigned CTA's memory
         if (t == 0) {
-            for (int s2 = 0; s2 < AT_STAGES; ++s2) mbar_wait_bounded(&full[s2], 0, kWaitPolls);
+            // chunks fail_kc .. fail_kc + AT_STAGES - 2 were issued, each in its own phase
+            for (int c = fail_kc; c < fail_kc + AT_STAGES - 1 && c < nk; ++c)
+                mbar_wait_bounded(&full[c % AT_STAGES], (uint32_t)((c / AT_STAGES) & 1), kWaitPolls);
             sc->status = -5;   // PASD_ERR_TIMEOUT
             sc->done = 1;
             __threadfence();
@@ -893,13 +896,13 @@ __global__ void __launch_bounds__(TP_THREADS, 1) apass_tc_kernel(const __grid_co
 
 template <int RP>
 static void launch_tma_rp(const ApassTmaPlan& p, cudaStream_t s) {
-    cudaFuncSetAttribute(apass_tma_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    set_smem_attr((const void*)apass_tma_kernel<RP>, (int)p.smem);
     apass_tma_kernel<RP><<<p.args.cta_start[p.args.count], AtShape<RP>::THREADS, p.smem, s>>>(p.maps, p.args);
 }
 
 template <int RP>
 static void launch_tc_rp(const ApassTmaPlan& p, cudaStream_t s) {
-    cudaFuncSetAttribute(apass_tc_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    set_smem_attr((const void*)apass_tc_kernel<RP>, (int)p.smem);
     const int ntask = p.args.cta_start[p.args.count];
     const int grid = ntask < p.grid ? ntask : p.grid;
     apass_tc_kernel<RP><<<grid, TP_THREADS, p.smem, s>>>(p.maps, p.args);

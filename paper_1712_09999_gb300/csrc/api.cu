@@ -29,6 +29,20 @@ static pasd_status fail(pasd_status s, const std::string& msg) {
     return s;
 }
 void pasd_set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace pasd {
+// (kernel, device) -> the largest dynamic shared-memory size set so far
+void set_smem_attr(const void* kernel, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    int& cur = done[std::make_pair(kernel, dev)];
+    if (bytes > cur && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+        cur = bytes;
+}
+}  // namespace pasd
 #define CUDA_TRY(call)                                                                   \
     do {                                                                                 \
         cudaError_t e_ = (call);                                                         \
@@ -138,6 +152,9 @@ struct pasd_plan {
     float* idle_g = nullptr;
     IdleSkipArgs idle{};
     bool skip_pending = false;
+    // test hook (PASD_TEST_WAIT_TIMEOUT=1 at plan time): the fused pass issues no
+    // bulk copy and waits a few thousand polls, so its bounded wait runs out
+    bool test_wait_timeout = false;
 };
 
 // ---------------------------------------------------------------------------
@@ -160,6 +177,10 @@ extern "C" pasd_status pasd_ctx_create(int device, size_t hbm_budget_bytes, pasd
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     c->hbm_budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+    if (const char* q = std::getenv("PASD_MAX_QUEUE")) {
+        const long v = std::strtol(q, nullptr, 10);
+        if (v >= 1) c->max_queue = (size_t)v;
+    }
     *out = c;
     return PASD_OK;
 }
@@ -234,14 +255,27 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     pl->ctx = c;
     pl->N = N;
     pl->D = D;
-    double asum = 0;
-    for (int n = 0; n < N; ++n) {
-        double a = p.alpha[n];
-        if (a < 0) { delete pl; return fail(PASD_ERR_INVALID_ARG, "alpha_n must be > 0"); }
-        if (a == 0) a = 1.0 / N;
-        pl->alpha[n] = a;
-        asum += a;
+    // weights: all alpha_n zero selects the default 1/N; otherwise every one must be
+    // finite and > 0 (a partly filled weight vector is an error, not a mix)
+    {
+        int zeros = 0;
+        for (int n = 0; n < N; ++n) {
+            const double a = p.alpha[n];
+            if (!std::isfinite(a) || a < 0) { delete pl; return fail(PASD_ERR_INVALID_ARG, "alpha_n must be finite and > 0"); }
+            zeros += a == 0;
+        }
+        if (zeros != 0 && zeros != N) {
+            delete pl;
+            return fail(PASD_ERR_INVALID_ARG, "alpha_n must all be > 0, or all 0 for the default 1/N");
+        }
+        for (int n = 0; n < N; ++n) pl->alpha[n] = zeros ? 1.0 / N : p.alpha[n];
     }
+    if (std::isnan(p.lambda) || std::isinf(p.lambda)) { delete pl; return fail(PASD_ERR_INVALID_ARG, "lambda must be finite"); }
+    for (int n = 0; n < N; ++n)
+        if (p.lambda <= 0 && !(p.lambda_n[n] >= 0 && std::isfinite(p.lambda_n[n]))) {
+            delete pl;
+            return fail(PASD_ERR_INVALID_ARG, "lambda_n must be finite and > 0 (0 selects the default)");
+        }
     int64_t dint[PASD_MAXN];
     for (int n = 0; n < N; ++n) dint[n] = p.dims[n];
     pl->D_real = D;
@@ -276,7 +310,6 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
         double lam;
         if (p.lambda > 0) lam = pl->alpha[n] / p.lambda;
         else if (p.lambda_n[n] > 0) lam = p.lambda_n[n];
-        else if (p.lambda_n[n] < 0) { delete pl; return fail(PASD_ERR_INVALID_ARG, "lambda_n must be > 0"); }
         else lam = std::sqrt((double)std::max<int64_t>(p.dims[n], preR * postR)) / N;
         pl->lam[n] = lam;
     }
@@ -410,6 +443,8 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     if (footprint_bytes) *footprint_bytes = f;
     const char* ng = std::getenv("PASD_NO_GRAPH");
     pl->use_graph = !(ng && ng[0] == '1');
+    const char* tw = std::getenv("PASD_TEST_WAIT_TIMEOUT");
+    pl->test_wait_timeout = tw && tw[0] == '1';
     *out = pl;
     return PASD_OK;
 }
@@ -526,6 +561,8 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
     fu.mu_max = pl->p.mu_max;
     fu.output = 0;
     fu.L = nullptr;
+    fu.test_no_copy = pl->test_wait_timeout ? 1 : 0;
+    fu.wait_polls = pl->test_wait_timeout ? 4096u : 0u;   // 0: the kernels' default bound
     VrotArgs& va = pl->vr;
     va.N = N;
     va.sc = pl->sc;
@@ -770,7 +807,9 @@ static pasd_status finish_impl(pasd_plan_t* pl, float* L, float* E, pasd_result*
     fill_result(pl, &r);
     if (res) *res = r;
     if (r.status != PASD_OK && r.status != PASD_NOT_CONVERGED) {
-        return fail((pasd_status)r.status, "solve failed: non-finite values in the iterate");
+        return fail((pasd_status)r.status, r.status == PASD_ERR_TIMEOUT
+                                               ? "solve failed: a bounded wait for a bulk copy ran out on the device"
+                                               : "solve failed: non-finite values in the iterate");
     }
     // output: L = sum_n alpha_n Z_n / sum alpha_n, E (Algorithm 1, Output)
     if (pl->pad) {

@@ -512,10 +512,10 @@ static void launch_n(const FusedArgs& a, cudaStream_t s) {
     bool vec = (a.g.I[N - 1] % 4) == 0;
     size_t smem = (size_t)a.g.smem_floats * 4;
     if (vec) {
-        cudaFuncSetAttribute(fused_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        set_smem_attr((const void*)fused_kernel<N, true>, (int)smem);
         fused_kernel<N, true><<<a.g.nregions, FU_THREADS, smem, s>>>(a);
     } else {
-        cudaFuncSetAttribute(fused_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        set_smem_attr((const void*)fused_kernel<N, false>, (int)smem);
         fused_kernel<N, false><<<a.g.nregions, FU_THREADS, smem, s>>>(a);
     }
 }

@@ -154,7 +154,9 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
     }
     __syncthreads();
 
+    const uint32_t polls = fa.wait_polls ? fa.wait_polls : kWaitPolls;
     auto issue = [&](int st) {
+        if (fa.test_no_copy) return;   // test hook: no arrival, no copy in flight
         int o[N];
 #pragma unroll
         for (int n = 0; n < N; ++n) { o[n] = tc[n] * g.b[n]; tile_o[st][n] = o[n]; }
@@ -186,14 +188,15 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
     };
 
     bool failed = false;
+    int64_t fail_it = 0;     // the tile whose copy did not land
     if (t == 0)
         for (int i = 0; i < (early ? nst - 1 : 1) && i < ntile; ++i) issue(i);
     for (int64_t it = 0; it < ntile; ++it) {
         const int st = (int)(it % nst);
         const uint32_t par = (uint32_t)((it / nst) & 1);
         if (early && t == 0 && it + nst - 1 < ntile) issue((int)((it + nst - 1) % nst));
-        bool ok = mbar_wait_bounded(&full_bar[st], par, kWaitPolls);
-        if (__syncthreads_or(!ok)) { failed = true; break; }
+        bool ok = mbar_wait_bounded(&full_bar[st], par, polls);
+        if (__syncthreads_or(!ok)) { failed = true; fail_it = it; break; }
         if (!early && t == 0 && it + 1 < ntile) issue(st ^ 1);
         float* stg = sm + st * sstride;
         float* Xs = stg + g.xs_off;
@@ -365,10 +368,13 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         if (early) __syncthreads();   // stage st fully read: the next iteration refills it first
     }
     if (failed) {
-        // a copy never arrived: record it and leave (the stage may still be written
-        // by a straggling copy, so wait on both barriers once more, bounded)
+        // a copy never arrived: record it and leave once every tile issued from the
+        // failed one on (early: nst - 1 ahead, else none ahead) has been waited for
+        // in its own phase, bounded, so no copy lands after the CTA has exited
         if (t == 0) {
-            for (int i = 0; i < nst; ++i) mbar_wait_bounded(&full_bar[i], 0, kWaitPolls);
+            const int64_t last = early ? fail_it + nst - 1 : fail_it;
+            for (int64_t c = fail_it; c <= last && c < ntile; ++c)
+                mbar_wait_bounded(&full_bar[c % nst], (uint32_t)((c / nst) & 1), polls);
             sc->status = -5;   // PASD_ERR_TIMEOUT
             sc->done = 1;
             __threadfence();
@@ -520,7 +526,7 @@ template <int N>
 static void launch_tma_n(FusedTmaPlan* p, int output, float* L, cudaStream_t s) {
     const FusedGeom& g = p->base.g;
     size_t smem = (size_t)g.smem_floats * 4 + 1024;
-    cudaFuncSetAttribute(fused_tma_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_smem_attr((const void*)fused_tma_kernel<N>, (int)smem);
     fused_tma_kernel<N><<<g.nregions, g.nthreads, smem, s>>>(p->maps, p->base, output, L);
 }
 

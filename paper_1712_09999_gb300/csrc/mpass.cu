@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(MP_THREADS) mpass_kernel(const MpassArgs ma) {
 }
 
 int mpass_ctas_per_sm(size_t smem) {
-    cudaFuncSetAttribute(mpass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_smem_attr((const void*)mpass_kernel, (int)smem);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mpass_kernel, MP_THREADS, smem) != cudaSuccess || n < 1)
         n = 1;
@@ -282,7 +282,7 @@ int mpass_ctas_per_sm(size_t smem) {
 }
 
 void launch_mpass(const MpassArgs& a, size_t smem, cudaStream_t s) {
-    cudaFuncSetAttribute(mpass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_smem_attr((const void*)mpass_kernel, (int)smem);
     mpass_kernel<<<a.cta_start[a.N], MP_THREADS, smem, s>>>(a);
 }
 
@@ -387,11 +387,12 @@ __global__ void __launch_bounds__(MP_THREADS) mpass_tma_kernel(const __grid_cons
         for (int r = 0; r < 4; ++r) acc[kk][r] = 0.f;
     const int nq8 = nq;
     bool failed = false;
+    int fail_kc = 0;
     for (int kc = 0; kc < nk; ++kc) {
         const int st = kc % MT_STAGES;
         const uint32_t par = (uint32_t)((kc / MT_STAGES) & 1);
         const bool ok = mbar_wait_bounded(&full[st], par, kWaitPolls);
-        if (__syncthreads_or(!ok)) { failed = true; break; }
+        if (__syncthreads_or(!ok)) { failed = true; fail_kc = kc; break; }
         if (t == 0 && kc + MT_STAGES - 1 < nk) issue(kc + MT_STAGES - 1);
         const float* gs = smem + st * sst;
         const float* vs = gs + gfl;
@@ -437,7 +438,9 @@ __global__ void __launch_bounds__(MP_THREADS) mpass_tma_kernel(const __grid_cons
     }
     if (failed) {
         if (t == 0) {
-            for (int s2 = 0; s2 < MT_STAGES; ++s2) mbar_wait_bounded(&full[s2], 0, kWaitPolls);
+            // chunks fail_kc .. fail_kc + MT_STAGES - 2 were issued, each in its own phase
+            for (int c = fail_kc; c < fail_kc + MT_STAGES - 1 && c < nk; ++c)
+                mbar_wait_bounded(&full[c % MT_STAGES], (uint32_t)((c / MT_STAGES) & 1), kWaitPolls);
             sc->status = -5;   // PASD_ERR_TIMEOUT
             sc->done = 1;
             __threadfence();
@@ -496,7 +499,7 @@ size_t mpass_tma_smem_bytes(int IS, int Rp) {
 }
 
 int mpass_tma_ctas_per_sm(size_t smem) {
-    cudaFuncSetAttribute(mpass_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_smem_attr((const void*)mpass_tma_kernel, (int)smem);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mpass_tma_kernel, MP_THREADS, smem) != cudaSuccess || n < 1)
         n = 1;
@@ -533,7 +536,7 @@ MpassTmaPlan* make_mpass_tma(const MpassTmaArgs& a, const float* const* G, const
 }
 
 void launch_mpass_tma(const MpassTmaPlan* p, cudaStream_t s) {
-    cudaFuncSetAttribute(mpass_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+    set_smem_attr((const void*)mpass_tma_kernel, (int)p->smem);
     mpass_tma_kernel<<<p->args.cta_start[p->args.N], MP_THREADS, p->smem, s>>>(p->maps, p->args);
 }
 

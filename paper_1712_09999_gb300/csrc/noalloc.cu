@@ -12,8 +12,10 @@
 // (4 MiB). Every GPU that loads the library holds it until the process exits.
 // In host code the array's name is only a host-side stand-in, not a device
 // address, so the address handed to the kernels is taken with
-// cudaGetSymbolAddress once per device, with that device current, on the first
-// call made on that device; make that first call before any stream capture.
+// cudaGetSymbolAddress with that device current, on every call (a host-side
+// lookup); the first call on a device (and the first after a cudaDeviceReset)
+// also clears the flags and waits for that clear, so make it before any stream
+// capture.
 // Every call shares the one array and it keeps the last call's contents: two
 // calls whose work overlaps on the GPU (different streams, or different host
 // threads) race on it and must be serialised by the caller.
@@ -47,8 +49,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 DeviceScratch g_scratch[kMaxDevices];
 
-// Device addresses of the scratch on the current device (set up once per device;
-// the setup clears the flags on `stream` and waits for that clear).
+// Device addresses of the scratch on the current device. The addresses are
+// looked up on every call (a host-side table lookup in the runtime) and compared
+// with the cached ones: after a cudaDeviceReset the module is loaded again,
+// possibly elsewhere, and the set-up (the flags clear) is then redone, so no call
+// ever launches on a stale address. The set-up clears the flags on `stream` and
+// waits for that clear.
 pasd_status scratch_for_current_device(DeviceScratch** out, cudaStream_t stream) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -62,22 +68,18 @@ pasd_status scratch_for_current_device(DeviceScratch** out, cudaStream_t stream)
     }
     std::lock_guard<std::mutex> lk(g_setup_mu);
     DeviceScratch& d = g_scratch[dev];
-    if (!d.ready) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_mode_product_scratch);
-        if (e != cudaSuccess) {
-            pasd_set_error(std::string("pasd_mode_product_noalloc: cudaGetSymbolAddress: ") +
-                           cudaGetErrorString(e));
-            return PASD_ERR_CUDA;
-        }
-        d.part = static_cast<float*>(p);
-        e = cudaGetSymbolAddress(&p, g_mode_product_flags);
-        if (e != cudaSuccess) {
-            pasd_set_error(std::string("pasd_mode_product_noalloc: cudaGetSymbolAddress: ") +
-                           cudaGetErrorString(e));
-            return PASD_ERR_CUDA;
-        }
-        d.flags = static_cast<DevScalars*>(p);
+    void* part = nullptr;
+    void* flags = nullptr;
+    e = cudaGetSymbolAddress(&part, g_mode_product_scratch);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&flags, g_mode_product_flags);
+    if (e != cudaSuccess) {
+        pasd_set_error(std::string("pasd_mode_product_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return PASD_ERR_CUDA;
+    }
+    if (!d.ready || d.part != part || d.flags != flags) {
+        d.ready = false;
+        d.part = static_cast<float*>(part);
+        d.flags = static_cast<DevScalars*>(flags);
         // the product kernel returns early when flags->done is set: clear it once,
         // complete before any product is launched (on whatever stream)
         e = cudaMemsetAsync(d.flags, 0, sizeof(DevScalars), stream);

@@ -24,6 +24,11 @@
 
 namespace pasd {
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device. The attribute is set once per (kernel, device, size) and
+// remembered, so launches on the hot path make no driver call for it.
+void set_smem_attr(const void* kernel, int bytes);
+
 // Scalars that live on the device so that a captured iteration graph can be
 // replayed without host involvement.
 struct DevScalars {
@@ -292,6 +297,10 @@ struct FusedArgs {
     int output;
     float* L;
     float alpha_w[PASD_MAXN];
+    // test hook of the TMA pass: issue no bulk copy (nothing is ever in flight),
+    // and give up a wait after wait_polls polls (0: kWaitPolls)
+    int test_no_copy;
+    uint32_t wait_polls;
 };
 
 bool plan_fused_geom(FusedGeom& g, int N, const int64_t* I, const int* Rp, int num_sms,

@@ -589,7 +589,7 @@ void launch_svt(const SmallArgs& a, cudaStream_t s) {
     int maxRp = 4;
     for (int n = 0; n < a.N; ++n) maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
     size_t smem = svt_smem_bytes(maxRp);
-    cudaFuncSetAttribute(svt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_smem_attr((const void*)svt_kernel, (int)smem);
     svt_kernel<<<a.N, SM_THREADS, smem, s>>>(a);
 }
 
@@ -602,7 +602,7 @@ void launch_polar(const SmallArgs& a, cudaStream_t s) {
         if (a.m[n].polar_in_smem) { any_smem = true; maxI = a.m[n].I > maxI ? a.m[n].I : maxI; }
     }
     size_t smem = any_smem ? polar_smem_bytes(maxRp, maxI) : 4 * small_base_floats(maxRp);
-    cudaFuncSetAttribute(polar_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_smem_attr((const void*)polar_kernel, (int)smem);
     polar_kernel<<<a.N, SM_THREADS, smem, s>>>(a);
 }
 

@@ -184,6 +184,12 @@ def batch_mix(seed: int = 3, n_random: int = 56, n_hyper: int = 8) -> list:
     return out
 
 
+def request_precisions(count: int, seed: int = 7) -> np.ndarray:
+    """Per-request precision of the serving workload: Bernoulli(1/2), 1 = mixed."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.integers(0, 2, size=count)
+
+
 def poisson_arrivals(rate: float, count: int, seed: int = 5) -> np.ndarray:
     """Arrival times (seconds from 0) of `count` requests at Poisson rate `rate`."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -239,12 +245,14 @@ def video(height: int = 144, width: int = 176, frames: int = 300, seed: int = 2,
     return Problem(T=t.astype(np.float32), L0=l0, E0=e0, support=support, desc=desc)
 
 
-def planted_device(dims, tucker_ranks, rho: float, seed: int, device, amp: float = 1.0):
-    """planted(..., scale="none") generated on a CUDA device with torch (for sizes and
+def planted_device(dims, tucker_ranks, rho: float, seed: int, device, amp: float = 1.0,
+                   scale: str = "none"):
+    """planted(..., scale=scale) generated on a CUDA device with torch (for sizes and
     counts the host generator is too slow for): Haar factors (QR of a Gaussian matrix,
     columns times sign(diag R)), N(0,1) core, exactly floor(rho D) positions drawn
-    without replacement carrying U[-amp, amp]. Returns (T float32, L0 float32) on
-    `device`; a different random stream from planted() for the same seed."""
+    without replacement carrying U[-amp, amp] ("none") or U[-amp, amp] max|L0|
+    ("max"). Returns (T float32, L0 float32) on `device`; a different random stream
+    from planted() for the same seed."""
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
@@ -259,6 +267,10 @@ def planted_device(dims, tucker_ranks, rho: float, seed: int, device, amp: float
     total = l0.numel()
     count = int(rho * total)
     t = l0.clone().reshape(-1)
+    if scale == "max":
+        amp = amp * float(l0.abs().max())
+    elif scale != "none":
+        raise ValueError(scale)
     if count:
         idx = torch.randperm(total, generator=g, device=device)[:count]
         t[idx] += (torch.rand(count, generator=g, device=device) * 2 - 1) * amp

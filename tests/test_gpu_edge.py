@@ -1,0 +1,251 @@
+"""GPU parity on the edge cases of Algorithm 1, and the C ABI's failure paths.
+
+Parity bar as in test_gpu_parity.py: kept counts identical per mode and per
+loop body, the same stopping body, rel-Fro(L), rel-Fro(E) <= 1e-5 on the FP32
+path and <= 1e-3 with mixed precision. Every oracle trajectory also reports its
+tie margin min |sigma - tau| / tau (tests/parity_util.py).
+"""
+import numpy as np
+import pytest
+
+from oracle import pasd_oracle as O
+from paper_1712_09999_gb300 import synth
+from parity_util import rel, tie_margin
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+MIXED_TOL = 1e-3
+STOPS = {0: "inf", 1: "fro_rel", 2: "fixed"}
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1712_09999_gb300 import pasd as P
+    ctx = P.pasd_ctx_create(0)
+    yield torch, P, ctx
+    P.pasd_ctx_destroy(ctx)
+
+
+def _gpu(env, T, ranks, **kw):
+    torch, P, ctx = env
+    plan, _ = P.pasd_plan(ctx, P.make_params(T.shape, ranks, **kw))
+    Td = torch.from_numpy(np.ascontiguousarray(T)).cuda()
+    L = torch.empty_like(Td)
+    E = torch.empty_like(Td)
+    res = P.pasd_solve(plan, Td, L, E)
+    trace = np.zeros((res.iters, P.TRACE_STRIDE))
+    P.pasd_state_get(plan, P.STATE_TRACE, 0, trace)
+    P.pasd_plan_destroy(plan)
+    return dict(res=res, L=L.cpu().numpy(), E=E.cpu().numpy(), trace=trace)
+
+
+def _check(g, ref, n_modes, tol=TOL):
+    gk = g["trace"][:, 5:5 + n_modes].astype(int).tolist()
+    rk = [s.kept for s in ref.trace]
+    assert g["res"].iters == ref.iters
+    assert gk == rk, "kept counts differ first at body %s" % next(
+        i + 1 for i, (a, b) in enumerate(zip(gk, rk)) if a != b)
+    assert rel(g["L"], ref.L) <= tol
+    assert rel(g["E"], ref.E) <= tol
+
+
+# --- Algorithm 1's output with unequal weights ---------------------------------
+
+@pytest.mark.parametrize("form", ["lambda_n", "alpha_lambda"])
+@pytest.mark.parametrize("stop,iters", [(2, 150), (0, 1000)])
+def test_unequal_alpha_output_matches_oracle(env, form, stop, iters):
+    # X = sum_n alpha_n Z_n / sum_n alpha_n with alpha = (0.5, 0.3, 0.2): with the
+    # nuclear weights given per mode (alpha_n weights the output only), and in the
+    # (alpha_n, lambda) form (lambda_n = alpha_n / lambda weights the modes as well)
+    _, P, _ = env
+    pr = synth.planted((24, 20, 16), (3, 3, 2), 0.1, 7, scale="std", amp=5.0)
+    ranks, alpha = (4, 4, 3), (0.5, 0.3, 0.2)
+    if form == "lambda_n":
+        lam = O.paper_lambdas(pr.T.shape)
+        ref = O.pasd(pr.T, O.Params(ranks=ranks, lambdas=lam, alpha=alpha, stop=STOPS[stop], max_iter=iters))
+        g = _gpu(env, pr.T, ranks, alpha=alpha, lambda_n=lam, stop=stop, max_iter=iters)
+        g_eq = _gpu(env, pr.T, ranks, lambda_n=lam, stop=stop, max_iter=iters)
+        # the same trajectory as the equal-weight solve, another output
+        assert np.array_equal(g["E"], g_eq["E"])
+        if stop == 2:
+            assert rel(g["L"], g_eq["L"]) > 1e-4
+    else:
+        ref = O.pasd(pr.T, O.Params.from_alpha_lambda(ranks, alpha, 1 / 12, stop=STOPS[stop], max_iter=iters))
+        g = _gpu(env, pr.T, ranks, alpha=alpha, lam=1 / 12, stop=stop, max_iter=iters)
+    tie_margin(ref.trace, ref_lambdas(ref, ranks, alpha, form, pr.T.shape), f"alpha {form} stop {stop}")
+    _check(g, ref, 3)
+
+
+def ref_lambdas(ref, ranks, alpha, form, dims):
+    if form == "lambda_n":
+        return O.paper_lambdas(dims)
+    return [a * 12 for a in alpha]
+
+
+# --- degenerate inputs ------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,ranks", [((24, 20, 16), (4, 4, 3)), ((37, 29, 23), (5, 4, 3)),
+                                        ((12, 10, 3, 20), (3, 3, 2, 4))])
+@pytest.mark.parametrize("stop", [0, 1])
+@pytest.mark.parametrize("flags", [0, 1])
+def test_zero_tensor_stops_after_one_body_at_zero(env, dims, ranks, stop, flags):
+    # T = 0 is a fixed point of Algorithm 1 (the oracle pins it): one body, every
+    # residual exactly zero, L = E = 0 exactly, nothing kept
+    torch, P, ctx = env
+    g = _gpu(env, np.zeros(dims, np.float32), ranks, stop=stop, max_iter=1000, flags=flags)
+    assert g["res"].status == P.OK and g["res"].iters == 1
+    assert not g["L"].any() and not g["E"].any()
+    assert g["trace"][0, 1] == 0.0 and g["trace"][0, 2] == 0.0
+    assert not g["trace"][0, 5:5 + len(dims)].any()
+    ref = O.pasd(np.zeros(dims), O.Params(ranks=ranks, lambdas=O.paper_lambdas(dims), stop=STOPS[stop]))
+    assert ref.iters == 1
+
+
+@pytest.mark.parametrize("dims,tucker,ranks", [
+    ((1, 20, 16), (1, 3, 2), (1, 4, 3)),         # leading singleton mode, I_0 = R_0 = 1
+    ((20, 1, 16), (3, 1, 2), (4, 1, 3)),         # middle singleton mode
+    ((20, 16, 1), (3, 2, 1), (4, 3, 1)),         # contiguous singleton mode (padded to 4)
+    ((12, 1, 10, 8), (2, 1, 2, 2), (3, 1, 3, 3)),  # 4-way with a singleton
+])
+def test_singleton_modes_match_oracle(env, dims, tucker, ranks):
+    pr = synth.planted(dims, tucker, 0.1, 5, scale="std", amp=5.0)
+    ref = O.pasd(pr.T, O.Params(ranks=ranks, lambdas=O.paper_lambdas(dims), stop="inf", max_iter=1000))
+    tie_margin(ref.trace, O.paper_lambdas(dims), f"singleton {dims}")
+    g = _gpu(env, pr.T, ranks, stop=0, max_iter=1000)
+    _check(g, ref, len(dims))
+
+
+@pytest.mark.parametrize("r,rho,stop,iters", [
+    (34, 0.02, 0, 1000),     # R = 40: a phase-map cell that recovers
+    (40, 0.02, 2, 250),      # R = 48
+    (50, 0.02, 2, 250),      # R = 60, rank bucket 64
+])
+def test_rank_buckets_40_to_64_match_oracle(env, r, rho, stop, iters):
+    # the phase map's high-rank cells: 100^3, Tucker rank r, R = floor(1.2 r),
+    # U[-1,1] additive corruption (Table 1 family), paper-default lambda_n
+    dims = (100, 100, 100)
+    R = int(1.2 * r)
+    pr = synth.table1(dims, rho, seed=900 + r, r=r)
+    lam = O.paper_lambdas(dims)
+    ref = O.pasd(pr.T, O.Params(ranks=(R,) * 3, lambdas=lam, stop=STOPS[stop], max_iter=iters))
+    tie_margin(ref.trace, lam, f"100^3 r={r} R={R}")
+    g = _gpu(env, pr.T, (R,) * 3, stop=stop, max_iter=iters)
+    _check(g, ref, 3)
+
+
+def test_mixed_video_shape_matches_oracle(env):
+    # the colour-video shape at reduced size (36 x 44 x 3 x 40, R = (10, 10, 3, 5))
+    # with mixed precision: kept counts per body and the stopping body identical,
+    # L and E within 1e-3, recovery error within 1e-4 of the oracle's
+    _, P, _ = env
+    pr = synth.video(height=36, width=44, frames=40, n_rect=4, seed=3)
+    ranks = (10, 10, 3, 5)
+    lam = O.paper_lambdas(pr.T.shape)
+    for stop, iters in ((2, 150), (0, 1000)):
+        ref = O.pasd(pr.T, O.Params(ranks=ranks, lambdas=lam, stop=STOPS[stop], max_iter=iters))
+        g = _gpu(env, pr.T, ranks, stop=stop, max_iter=iters, precision=P.PREC_MIXED)
+        if g["res"].iters != ref.iters:
+            # a stopping tie (the residual within FP32 rounding of eps): compare
+            # with the oracle run to the GPU's stopping body
+            k = min(g["res"].iters, ref.iters)
+            assert abs(g["res"].iters - ref.iters) == 1
+            assert abs(ref.trace[k - 1].res_inf - 1e-5) <= 4 * 2.0 ** -24 * float(np.abs(pr.T).max())
+            ref = O.pasd(pr.T, O.Params(ranks=ranks, lambdas=lam, stop="fixed", max_iter=g["res"].iters))
+        tie_margin(ref.trace, lam, f"video mixed stop {stop}")
+        _check(g, ref, 4, tol=MIXED_TOL)
+    assert abs(O.rse(g["L"], pr.L0) - O.rse(ref.L, pr.L0)) <= 1e-4
+
+
+# --- failure paths of the ABI -------------------------------------------------------
+
+def test_invalid_weights_are_rejected(env):
+    torch, P, ctx = env
+    for kw in (dict(alpha=(1.0, 0.0, 0.0)), dict(alpha=(float("nan"), 0.3, 0.2)),
+               dict(alpha=(0.5, -0.3, 0.2)), dict(lam=float("nan")),
+               dict(lambda_n=(1.0, -2.0, 1.0)), dict(lambda_n=(1.0, float("inf"), 1.0))):
+        with pytest.raises(P.PasdError) as ei:
+            P.pasd_plan(ctx, P.make_params((10, 8, 6), (4, 4, 2), **kw))
+        assert ei.value.status == P.ERR_INVALID_ARG, kw
+
+
+def test_submit_beyond_the_hbm_budget_is_oom(env):
+    torch, P, _ = env
+    small = P.pasd_ctx_create(0, 1 << 20)            # a 1 MiB budget
+    plan, footprint = P.pasd_plan(small, P.make_params((64, 60, 56), (4, 4, 4)))
+    assert footprint > 4 << 20
+    T = torch.zeros((64, 60, 56), device="cuda")
+    L, E = torch.empty_like(T), torch.empty_like(T)
+    with pytest.raises(P.PasdError) as ei:
+        P.pasd_submit(small, plan, T, L, E)
+    assert ei.value.status == P.ERR_OOM
+    P.pasd_plan_destroy(plan)
+    P.pasd_ctx_destroy(small)
+
+
+def test_full_queue_is_busy_and_tickets_are_polled_once(env, monkeypatch):
+    # one plan serves one solve at a time, so with a queue bound of 3 at most four
+    # submits of the same plan are accepted (one running, three queued) while its
+    # first solve (1000 loop bodies of a 100^3 tensor) runs
+    torch, P, _ = env
+    monkeypatch.setenv("PASD_MAX_QUEUE", "3")
+    ctx = P.pasd_ctx_create(0)
+    monkeypatch.delenv("PASD_MAX_QUEUE")
+    pr = synth.planted((100, 100, 100), (4, 4, 4), 0.1, 61, scale="std", amp=5.0)
+    plan, _ = P.pasd_plan(ctx, P.make_params(pr.T.shape, (5, 5, 5), stop=P.STOP_FIXED_ITERS, max_iter=1000))
+    T = torch.from_numpy(pr.T).cuda()
+    L, E = torch.empty_like(T), torch.empty_like(T)
+    torch.cuda.synchronize()
+    tickets, busy = [], False
+    for _ in range(6):
+        try:
+            tickets.append(P.pasd_submit(ctx, plan, T, L, E))
+        except P.PasdError as err:
+            assert err.status == P.ERR_BUSY
+            busy = True
+            break
+    assert busy and 3 <= len(tickets) <= 4
+    import time
+    t0 = time.time()
+    left = set(tickets)
+    while left and time.time() - t0 < 120:
+        for tk in list(left):
+            st, r = P.pasd_poll(ctx, tk)
+            if st != P.PENDING:
+                assert st == P.OK and r.iters == 1000
+                left.discard(tk)
+        time.sleep(0.001)
+    assert not left
+    for tk in (tickets[0], 10 ** 12):            # polled to completion once / never issued
+        with pytest.raises(P.PasdError) as ei:
+            P.pasd_poll(ctx, tk)
+        assert ei.value.status == P.ERR_UNKNOWN_TICKET
+    P.pasd_plan_destroy(plan)
+    P.pasd_ctx_destroy(ctx)
+
+
+def test_bounded_wait_that_runs_out_returns_timeout(env, monkeypatch):
+    # The test hook makes the bulk-copy-fed elementwise pass issue no copy at all,
+    # so its mbarrier wait can only run out (nothing is in flight): the kernel
+    # records PASD_ERR_TIMEOUT and returns, the solve reports it, the outputs stay
+    # untouched, and the context still solves a normal plan afterwards.
+    torch, P, ctx = env
+    pr = synth.planted((24, 20, 16), (3, 3, 2), 0.1, 7, scale="std", amp=5.0)
+    monkeypatch.setenv("PASD_TEST_WAIT_TIMEOUT", "1")
+    bad, _ = P.pasd_plan(ctx, P.make_params(pr.T.shape, (4, 4, 3), max_iter=100))
+    monkeypatch.delenv("PASD_TEST_WAIT_TIMEOUT")
+    T = torch.from_numpy(pr.T).cuda()
+    L, E = torch.full_like(T, 7.0), torch.full_like(T, 7.0)
+    with pytest.raises(P.PasdError) as ei:
+        P.pasd_solve(bad, T, L, E)
+    assert ei.value.status == P.ERR_TIMEOUT
+    assert bool(torch.all(L == 7.0)) and bool(torch.all(E == 7.0))
+    P.pasd_plan_destroy(bad)
+    good = _gpu(env, pr.T, (4, 4, 3), stop=2, max_iter=150)
+    ref = O.pasd(pr.T, O.Params(ranks=(4, 4, 3), lambdas=O.paper_lambdas(pr.T.shape), stop="fixed", max_iter=150))
+    _check(good, ref, 3)

@@ -10,6 +10,7 @@ import pytest
 
 from oracle import pasd_oracle as O
 from paper_1712_09999_gb300 import synth
+from parity_util import tie_margin
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +56,10 @@ def _oracle(T, ranks, stop, max_iter, lam_pair=None):
     else:
         alpha, lam = lam_pair
         p = O.Params.from_alpha_lambda(ranks, alpha, lam, stop=STOPS[stop], max_iter=max_iter)
-    return O.pasd(T, p)
+    res = O.pasd(T, p)
+    # the evidence that identical kept counts are not luck: no singular value on tau
+    tie_margin(res.trace, p.lambdas, f"{T.shape} R={tuple(ranks)} stop={STOPS[stop]} iters={res.iters}")
+    return res
 
 
 def _stop_tie(ref, g_iters, tol, tmax):

@@ -79,14 +79,17 @@ PINS = [
     ("eqS3", pins.test_dual_spectral_bound_eqS3),
     ("idle", pins.test_idle_phase_matches_closed_form),
     ("svt_tie", pins.test_svt_drops_a_singular_value_equal_to_tau),
+    ("alpha_output", pins.test_output_is_the_alpha_weighted_mean_of_the_refolds),
 ]
 
 
-def _failing_pins(monkeypatch, step=None, svt=None, stop_at_first=True):
+def _failing_pins(monkeypatch, step=None, svt=None, output=None, stop_at_first=True):
     if step is not None:
         monkeypatch.setattr(O, "step", step)
     if svt is not None:
         monkeypatch.setattr(O, "svt", svt)
+    if output is not None:
+        monkeypatch.setattr(O, "output_low_rank", output)
     failed = []
     for name, pin in PINS:
         try:
@@ -110,3 +113,19 @@ def test_a_planted_mistake_in_the_body_fails_a_pin(monkeypatch, kind):
 
 def test_keeping_svt_ties_fails_a_pin(monkeypatch):
     assert _failing_pins(monkeypatch, svt=_svt_keeping_ties)
+
+
+def _output_ignoring_alpha(zs, alpha):
+    """Algorithm 1's output with the weights dropped: the plain mean of the Z_n."""
+    return sum(zs) / len(zs)
+
+
+def _output_unnormalised(zs, alpha):
+    """Algorithm 1's output without the division by sum_n alpha_n."""
+    alpha = [1.0 / len(zs)] * len(zs) if alpha is None else alpha
+    return sum(a * z for a, z in zip(alpha, zs))
+
+
+@pytest.mark.parametrize("output", [_output_ignoring_alpha, _output_unnormalised])
+def test_a_planted_mistake_in_the_output_fails_a_pin(monkeypatch, output):
+    assert _failing_pins(monkeypatch, output=output)

@@ -297,6 +297,66 @@ def test_default_weights_are_the_papers_setting():
     assert O.paper_lambdas((9, 400)) == pytest.approx([10.0, 10.0], rel=1e-15)
 
 
+def _fold_by_index(m, n, dims):
+    """fold_n written out entry by entry: Z[x] = M[x_n, j] with j the C-order index
+    of x over the modes other than n (Sec. 2.1 with the column order of reading 7)."""
+    z = np.empty(dims)
+    for x in np.ndindex(*dims):
+        j = 0
+        for k, i_k in enumerate(dims):
+            if k != n:
+                j = j * i_k + x[k]
+        z[x] = m[x[n], j]
+    return z
+
+
+def test_output_is_the_alpha_weighted_mean_of_the_refolds():
+    # Algorithm 1's output X = sum_n alpha_n Z_n / sum_n alpha_n with unequal alpha_n,
+    # against Z_n = fold_n(U_n V_n) rebuilt from the final state entry by entry. With
+    # the nuclear weights lambda_n given per mode, alpha_n enters the output only: the
+    # whole trajectory equals the equal-weight run bit for bit. The unweighted mean of
+    # the Z_n is far from X at this (unconverged) body, so a kernel or an oracle that
+    # ignored alpha would fail.
+    pr = _small_problem(seed=17)
+    t = pr.T.astype(np.float64)
+    lam = O.paper_lambdas(t.shape)
+    alpha = (0.5, 0.3, 0.2)
+    iters = 120
+    r_eq = O.pasd(t, O.Params(ranks=(3, 3, 3), lambdas=lam, stop="fixed", max_iter=iters))
+    r_al = O.pasd(t, O.Params(ranks=(3, 3, 3), lambdas=lam, alpha=alpha, stop="fixed", max_iter=iters))
+    assert max(r_al.trace[-1].kept) > 0
+    for n in range(3):
+        assert np.array_equal(r_al.state.U[n], r_eq.state.U[n])
+        assert np.array_equal(r_al.state.V[n], r_eq.state.V[n])
+    assert np.array_equal(r_al.E, r_eq.E)
+    zs = [_fold_by_index(r_al.state.U[n] @ r_al.state.V[n], n, t.shape) for n in range(3)]
+    want = (alpha[0] * zs[0] + alpha[1] * zs[1] + alpha[2] * zs[2]) / (alpha[0] + alpha[1] + alpha[2])
+    assert np.allclose(r_al.L, want, rtol=0, atol=1e-13 * np.abs(want).max())
+    mean = (zs[0] + zs[1] + zs[2]) / 3
+    assert np.allclose(r_eq.L, mean, rtol=0, atol=1e-13 * np.abs(mean).max())
+    assert np.linalg.norm(r_al.L - mean) > 1e-4 * np.linalg.norm(mean)
+    # scaling every alpha_n by a power of two leaves X unchanged, bit for bit
+    r_4 = O.pasd(t, O.Params(ranks=(3, 3, 3), lambdas=lam, alpha=tuple(4 * a for a in alpha),
+                             stop="fixed", max_iter=iters))
+    assert np.array_equal(r_4.L, r_al.L)
+
+
+def test_alpha_lambda_form_depends_on_the_ratios_only():
+    # In the (alpha_n, lambda) form lambda_n = alpha_n / lambda, so (c alpha, c lambda)
+    # is the same problem: with c a power of two every lambda_n is the same double and
+    # the run is the same bit for bit; unequal alpha_n change the trajectory itself.
+    pr = _small_problem(seed=18)
+    t = pr.T.astype(np.float64)
+    alpha = (0.5, 0.3, 0.2)
+    p1 = O.Params.from_alpha_lambda((3, 3, 3), alpha, 1 / 12, stop="fixed", max_iter=140)
+    p2 = O.Params.from_alpha_lambda((3, 3, 3), tuple(2 * a for a in alpha), 2 / 12, stop="fixed", max_iter=140)
+    assert list(p1.lambdas) == list(p2.lambdas)
+    r1, r2 = O.pasd(t, p1), O.pasd(t, p2)
+    assert np.array_equal(r1.L, r2.L) and np.array_equal(r1.E, r2.E)
+    r_eq = O.pasd(t, O.Params.from_alpha_lambda((3, 3, 3), (1 / 3,) * 3, 1 / 12, stop="fixed", max_iter=140))
+    assert [s.kept for s in r1.trace] != [s.kept for s in r_eq.trace] or not np.allclose(r1.E, r_eq.E)
+
+
 def test_zero_tensor_stops_after_one_body_at_zero():
     # T = 0 is a fixed point of Algorithm 1: G = 0, so A = 0, V = 0, Z = 0, E = 0 and
     # Y stays 0; the residual is exactly zero, so the stop test holds after one body.
