@@ -691,7 +691,8 @@ def run_ours(args):
                            ms_per_body=round(ms / iters, 4),
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                            footprint_bytes=footprint),
-            "gpu_launches": args.steps * launches_per_solve, "clocks": clocks, "roofline": roofline, "e2e": e2e}
+            "gpu_launches": args.steps * launches_per_solve, "clocks": clocks, "roofline": roofline, "e2e": e2e,
+            "plan": P.pasd_plan_info(plan)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, el = _oracle_iters_per_s(pr.T, args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(v, 3), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",

@@ -146,7 +146,9 @@ pasd_status pasd_params_default(pasd_params* p, int32_t order, const int64_t* di
  * Environment, read here (for comparisons and debugging; the same arithmetic up
  * to the grouping of partial sums): PASD_NO_TMA=1 plans the kernels fed by per-thread asynchronous
  * copies instead of bulk tensor copies; PASD_NO_GRAPH=1 launches each loop
- * body's kernels directly instead of replaying a captured CUDA graph.
+ * body's kernels directly instead of replaying a captured CUDA graph;
+ * PASD_NO_FEWROW=1 runs modes of at most 8 rows on the general streaming
+ * products instead of their few-row kernels.
  * Test hook: PASD_TEST_WAIT_TIMEOUT=1 makes the plan's bulk-copy-fed
  * elementwise pass issue no copy at all and give up its wait after a few
  * thousand polls, so the first loop body ends the solve with PASD_ERR_TIMEOUT
@@ -230,6 +232,25 @@ pasd_status pasd_state_get(pasd_plan_t* plan, int32_t item, int32_t mode, void* 
 
 /* Number of kernel launches pasd_iterate enqueues per loop body. */
 int32_t pasd_launches_per_iter(const pasd_plan_t* plan);
+
+/* The plan's kernel configuration as a one-line JSON object written to `buf`
+ * (`len` bytes, NUL-terminated; INVALID_ARG if it does not fit): the fused
+ * pass's tile box per mode, regions, threads and resident CTAs per SM, the
+ * M-pass's CTAs and waves, the modes on the few-row kernels, launches per body,
+ * and the autotuner's state ("pending" before the first pasd_begin, then
+ * "timed", "cached" or "off"). The paper has no counterpart (a
+ * measurement aid). Tile autotuning: at the first pasd_begin of a plan the
+ * library times the fused pass with 1, 2 and 3 resident CTAs per SM (each with
+ * the largest tile that fits that share of shared memory, in an idle and an
+ * active body), the M-pass with one and two waves of CTAs and the FP32 A-pass
+ * with its default and half its default columns per thread, on the plan's own
+ * buffers, and keeps a candidate only if it beats the planner's default by more
+ * than 3%; the choice is cached per device and problem shape for the life of the
+ * process, so plans of one shape share it (and their results agree bit for
+ * bit). The choice changes only how partial sums are grouped, i.e. results in
+ * their last bits. PASD_NO_TUNE=1 (read at that first pasd_begin) keeps the
+ * planner's default. */
+pasd_status pasd_plan_info(const pasd_plan_t* plan, char* buf, size_t len);
 
 /* The mode-n product of the V-step (Eq. 13) as a standalone operation: for a
  * C-order float32 tensor X viewed as [pre][I][post] (the mode-n unfolding X_(n)

@@ -406,6 +406,8 @@ struct ApassTmaPlan {
     size_t smem;
     int kind;      // ApassKind
     int grid;      // persistent grid of the tensor-core kernel (one CTA per SM)
+    int nc;        // FMA kernel: columns per thread
+    size_t pipe_floats, epi_base_floats;   // shared-memory parts independent of nc
 };
 
 // Stage stride in floats: 512-byte multiples, the period of the 64-byte swizzle,
@@ -414,14 +416,17 @@ static inline __host__ __device__ int at_stage_floats(int BN, int RP) {
     return (AP_BK * BN + AP_BK * RP + 127) / 128 * 128;
 }
 
-// Columns per thread: four while the 4 x RP accumulators fit in registers, two beyond.
+// Columns per thread: by default four while the 4 x RP accumulators fit in
+// registers, two beyond; the autotuner may halve it (twice the warps per CTA,
+// half the accumulators per thread: more latency hiding, less reuse of each
+// broadcast U row).
 template <int RP> struct AtShape {
     static constexpr int COLS = RP <= 40 ? 4 : 2;
     static constexpr int THREADS = AP_BN / COLS;
 };
 
-template <int RP>
-__global__ void __launch_bounds__(AtShape<RP>::THREADS) apass_tma_kernel(const __grid_constant__ ApassTmaMaps maps,
+template <int RP, int NC>
+__global__ void __launch_bounds__(AP_BN / NC) apass_tma_kernel(const __grid_constant__ ApassTmaMaps maps,
                                                                const ApassTmaArgs aa) {
     extern __shared__ __align__(16) float sm_raw[];
     float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 511) & ~uintptr_t(511));
@@ -430,7 +435,7 @@ __global__ void __launch_bounds__(AtShape<RP>::THREADS) apass_tma_kernel(const _
     while (k + 1 < aa.count && (int)blockIdx.x >= aa.cta_start[k + 1]) ++k;
     const ApassTmaMode& m = aa.m[k];
     DevScalars* sc = aa.sc;
-    constexpr int NT = AtShape<RP>::THREADS, NC = AtShape<RP>::COLS;
+    constexpr int NT = AP_BN / NC;
     if (sc->done) return;
     const int task = blockIdx.x - aa.cta_start[k];
     const int t = threadIdx.x;
@@ -894,10 +899,16 @@ __global__ void __launch_bounds__(TP_THREADS, 1) apass_tc_kernel(const __grid_co
     if (warp == 1) tmem_dealloc(tm, S::TMEM_COLS);
 }
 
+template <int RP, int NC>
+static void launch_tma_rp_nc(const ApassTmaPlan& p, cudaStream_t s) {
+    set_smem_attr((const void*)apass_tma_kernel<RP, NC>, (int)p.smem);
+    apass_tma_kernel<RP, NC><<<p.args.cta_start[p.args.count], AP_BN / NC, p.smem, s>>>(p.maps, p.args);
+}
 template <int RP>
 static void launch_tma_rp(const ApassTmaPlan& p, cudaStream_t s) {
-    set_smem_attr((const void*)apass_tma_kernel<RP>, (int)p.smem);
-    apass_tma_kernel<RP><<<p.args.cta_start[p.args.count], AtShape<RP>::THREADS, p.smem, s>>>(p.maps, p.args);
+    constexpr int C = AtShape<RP>::COLS;
+    if (p.nc == C) launch_tma_rp_nc<RP, C>(p, s);
+    else launch_tma_rp_nc<RP, C / 2>(p, s);
 }
 
 template <int RP>
@@ -1023,6 +1034,8 @@ ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, in
         if (!ok) { delete p; return nullptr; }
         if (kind == APASS_FFMA) {
             const size_t pipe = (size_t)AT_STAGES * at_stage_floats(mm.BN, Rp);
+            p->pipe_floats = std::max(p->pipe_floats, pipe);
+            p->epi_base_floats = std::max(p->epi_base_floats, (size_t)AP_BN * (Rp + 4));
             const size_t epi = (size_t)AP_BN * (Rp + 4) + gram_red_floats(Rp, Rp <= 40 ? AP_BN / 4 : AP_BN / 2);
             smem = std::max(smem, 4 * std::max(pipe, epi) + 512);
         } else {
@@ -1031,7 +1044,20 @@ ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, in
     }
     p->args.cta_start[count] = start;
     p->smem = smem;
+    p->nc = p->args.Rp <= 40 ? 4 : 2;
     return p;
+}
+
+int apass_tma_cols(const ApassTmaPlan* p) { return p->kind == APASS_FFMA ? p->nc : 0; }
+
+// Columns per thread of the FMA kernel: its default or half of it.
+void apass_tma_set_cols(ApassTmaPlan* p, int nc) {
+    if (p->kind != APASS_FFMA) return;
+    const int def = p->args.Rp <= 40 ? 4 : 2;
+    if (nc != def && nc != def / 2) return;
+    p->nc = nc;
+    const size_t epi = p->epi_base_floats + gram_red_floats(p->args.Rp, AP_BN / nc);
+    p->smem = 4 * std::max(p->pipe_floats, epi) + 512;
 }
 
 void destroy_apass_tma(ApassTmaPlan* p) { delete p; }

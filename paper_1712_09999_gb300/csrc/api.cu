@@ -110,6 +110,7 @@ struct pasd_plan {
     // device arena
     char* arena = nullptr;
     DevScalars* sc = nullptr;
+    DevScalars* tune_sc = nullptr;       // scalars the autotuner's timing launches read
     float *E = nullptr, *G[PASD_MAXN], *A[PASD_MAXN], *U[PASD_MAXN], *Urot[PASD_MAXN], *Vr[PASD_MAXN];
     float *W[PASD_MAXN], *F[PASD_MAXN], *sigma[PASD_MAXN];
     float *gram[PASD_MAXN], *mp[PASD_MAXN], *scratch[PASD_MAXN], *Mred[PASD_MAXN];
@@ -127,10 +128,27 @@ struct pasd_plan {
     MpassArgs mpa{};
     size_t mp_smem = 0;
     bool mp_use_tma = false;
+    MpassSmallArgs mp_small[PASD_MAXN];  // few-row modes' M-pass (fewrow.cu)
+    int n_mp_big = 0;                    // modes on the shared M-pass launch
     MpassTmaArgs mpt{};
     size_t mpt_smem = 0;
+    int mpt_slots = 0;                   // TMA M-pass CTAs resident at once
+    int64_t mpt_tot = 0, mpt_work[PASD_MAXN];
+    // autotuner candidates of the fused pass (k CTAs per SM) and its choices
+    FusedGeom fcand[3];
+    int fcand_k[3];
+    int n_fcand = 0;
+    int default_fused_k = 0;             // CTAs per SM of the planner's default geometry
+    int tuned_fused_k = 0;               // CTAs per SM of the geometry in use
+    int tuned_mp_waves = 1;
+    int tuned_ap_half = 0;
+    int ap_tma_default_nc[PASD_MAXN];
+    bool tuned = false;
+    const char* tune_mode = "pending";   // pending (no pasd_begin yet), timed, cached, off
     MpassTmaPlan* mp_tma = nullptr;
     // A-pass: TMA plans (one per padded rank) and the modes on the cp.async kernel
+    bool ap_small[PASD_MAXN];            // modes on the few-row kernel (apass_small.cu)
+    int ap_small_grid[PASD_MAXN];
     bool ap_use_tma[PASD_MAXN];
     int ap_kind = APASS_FFMA;            // arithmetic of the TMA-fed A-pass (ApassKind)
     ApassTmaPlan* ap_tma[PASD_MAXN];
@@ -147,7 +165,9 @@ struct pasd_plan {
     cudaEvent_t ev = nullptr;
     bool busy = false;
     int served = 0;          // served solves queued or running (guarded by ctx->mu)
+    int nparts_max = 0;                  // residual partials: room for every fused geometry
     int ap_launches = 1;
+    int mp_launches = 1;
     // idle-start skip (PASD_F_SKIP_IDLE): armed by pasd_begin, run after the first body
     float* idle_g = nullptr;
     IdleSkipArgs idle{};
@@ -221,6 +241,8 @@ static int rank_bucket(int R) {
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static MpassTmaArgs mpass_tma_layout(const pasd_plan_t* pl, int waves);
 
 extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_t** out,
                                  size_t* footprint_bytes) {
@@ -331,8 +353,20 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
         const size_t half = c->smem_per_sm / 2 > 2048 ? c->smem_per_sm / 2 - 1024 : 0;
         const bool ok1 = plan_fused_tma(one, N, Is, Rps, c->num_sms, c->smem_optin);
         const bool ok2 = plan_fused_tma(two, N, Is, Rps, 2 * c->num_sms, std::min(half, c->smem_optin));
-        if (ok2 && (!ok1 || 2 * two.nthreads >= one.nthreads)) { pl->fg = two; pl->want_tma = true; }
-        else if (ok1) { pl->fg = one; pl->want_tma = true; }
+        if (ok2 && (!ok1 || 2 * two.nthreads >= one.nthreads)) { pl->fg = two; pl->want_tma = true; pl->default_fused_k = 2; }
+        else if (ok1) { pl->fg = one; pl->want_tma = true; pl->default_fused_k = 1; }
+        // the autotuner's candidates: k = 1, 2, 3 resident CTAs per SM, each with
+        // the largest tile that fits 1/k of the SM's shared memory
+        for (int k = 1; k <= 3; ++k) {
+            FusedGeom gk{};
+            const size_t share = c->smem_per_sm / k > 2048 ? c->smem_per_sm / k - 1024 : 0;
+            const size_t lim = k == 1 ? c->smem_optin : std::min(share, c->smem_optin);
+            if (plan_fused_tma(gk, N, Is, Rps, k * c->num_sms, lim)) {
+                pl->fcand[pl->n_fcand] = gk;
+                pl->fcand_k[pl->n_fcand] = k;
+                ++pl->n_fcand;
+            }
+        }
     }
     if (!pl->want_tma) pl->fg = pl->fg_plain;
     const bool tma_ok = !(nt && nt[0] == '1');
@@ -342,11 +376,17 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     // converting each stage into split operands costs more than the FMAs, so the
     // FP32 path keeps the FMA kernel.
     pl->ap_kind = p.precision == PASD_PREC_MIXED ? APASS_TC : APASS_FFMA;
+    const char* nf = std::getenv("PASD_NO_FEWROW");
+    const bool no_fewrow = nf && nf[0] == '1';
     for (int n = 0; n < N; ++n) {
         const ModeGeom& g = pl->m[n];
-        pl->ap_use_tma[n] = tma_ok && apass_tma_supported(g.I, g.post);
-        // Gram partials: room for either kernel's CTA count (the TMA plan may be refused later)
-        pl->ncta_ap[n] = std::max(apass_ncta(g.P), apass_tma_tasks(g.I, g.pre, g.post, pl->ap_kind));
+        pl->ap_small[n] = !no_fewrow && apass_small_supported(g.I, g.Rp);
+        pl->ap_small_grid[n] = apass_small_grid(c->num_sms, g.P);
+        pl->ap_use_tma[n] = !pl->ap_small[n] && tma_ok && apass_tma_supported(g.I, g.post);
+        // Gram partials: room for the CTA count of the kernel in use (the TMA plan
+        // may be refused later, leaving the cp.async kernel)
+        pl->ncta_ap[n] = pl->ap_small[n] ? pl->ap_small_grid[n]
+                                         : std::max(apass_ncta(g.P), apass_tma_tasks(g.I, g.pre, g.post, pl->ap_kind));
     }
     // M-pass: row strips x column ranges, as many CTAs as fit on the device at
     // once (one wave), split over the modes in proportion to their columns
@@ -360,7 +400,8 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
             mm.variant = mpass_variant(g.I, g.post);
             mm.IS = mpass_strip_rows(g.I, g.Rp);
             mm.nstrips = (int)((g.I + mm.IS - 1) / mm.IS);
-            work[n] = (int64_t)mm.nstrips * ((g.P + MP_CB - 1) / MP_CB);
+            // few-row modes run their own kernel (no CTAs here)
+            work[n] = pl->ap_small[n] ? 0 : (int64_t)mm.nstrips * ((g.P + MP_CB - 1) / MP_CB);
             tot += work[n];
             smem = std::max(smem, mpass_smem_bytes(mm.IS, g.Rp, mm.variant));
         }
@@ -368,14 +409,20 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
         int start = 0;
         for (int n = 0; n < N; ++n) {
             MpassMode& mm = pl->mpa.m[n];
-            int64_t target = (int64_t)((double)slots * (double)work[n] / (double)tot);
+            pl->mpa.cta_start[n] = start;
+            if (pl->ap_small[n]) {
+                mm.ncg = 0;
+                mm.cols_per_cg = MP_CB;
+                pl->n_mp[n] = pl->ap_small_grid[n];
+                continue;
+            }
+            int64_t target = (int64_t)((double)slots * (double)work[n] / (double)std::max<int64_t>(tot, 1));
             int64_t ncg = std::max<int64_t>(1, target / mm.nstrips);
             int64_t cols = (mm.P + ncg - 1) / ncg;
             cols = (cols + MP_CB - 1) / MP_CB * MP_CB;
             mm.cols_per_cg = cols;
             mm.ncg = (int)((mm.P + cols - 1) / cols);
             pl->n_mp[n] = mm.ncg;
-            pl->mpa.cta_start[n] = start;
             start += mm.nstrips * mm.ncg;
         }
         pl->mpa.cta_start[N] = start;
@@ -385,7 +432,8 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     // TMA-fed M-pass when every mode's layout allows it: CTAs = row strips x
     // ranges of whole chunks, one wave, split over the modes by work
     pl->mp_use_tma = tma_ok;
-    for (int n = 0; n < N; ++n) pl->mp_use_tma = pl->mp_use_tma && mpass_tma_supported(pl->m[n].I, pl->m[n].post);
+    for (int n = 0; n < N; ++n)
+        pl->mp_use_tma = pl->mp_use_tma && (pl->ap_small[n] || mpass_tma_supported(pl->m[n].I, pl->m[n].post));
     if (pl->mp_use_tma) {
         int64_t work[PASD_MAXN], tot = 0;
         size_t smem = 0;
@@ -398,27 +446,25 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
             mm.nstrips = (int)((g.I + mm.IS - 1) / mm.IS);
             mm.nch = mpass_tma_chunks(g.pre, g.post);
             mm.nbb = mm.rowmajor ? 1 : (int)((g.post + MP_CB - 1) / MP_CB);
-            work[n] = (int64_t)mm.nstrips * mm.nch;
+            work[n] = pl->ap_small[n] ? 0 : (int64_t)mm.nstrips * mm.nch;
             tot += work[n];
-            smem = std::max(smem, mpass_tma_smem_bytes(mm.IS, g.Rp));
+            if (!pl->ap_small[n]) smem = std::max(smem, mpass_tma_smem_bytes(mm.IS, g.Rp));
         }
-        const int slots = c->num_sms * mpass_tma_ctas_per_sm(smem);
-        int start = 0;
-        for (int n = 0; n < N; ++n) {
-            MpassTmaMode& mm = pl->mpt.m[n];
-            int64_t target = (int64_t)((double)slots * (double)work[n] / (double)tot);
-            int64_t ncg = std::max<int64_t>(1, target / mm.nstrips);
-            mm.cpr = (int)((mm.nch + ncg - 1) / ncg);
-            mm.ncg = (mm.nch + mm.cpr - 1) / mm.cpr;
-            pl->n_mp[n] = std::max(pl->n_mp[n], mm.ncg);
-            pl->mpt.cta_start[n] = start;
-            start += mm.nstrips * mm.ncg;
-        }
-        pl->mpt.cta_start[N] = start;
         pl->mpt.N = N;
         pl->mpt_smem = smem;
+        pl->mpt_slots = c->num_sms * mpass_tma_ctas_per_sm(smem);
+        pl->mpt_tot = tot;
+        for (int n = 0; n < N; ++n) pl->mpt_work[n] = work[n];
+        // the autotuner's candidates: one or two waves of CTAs (column ranges)
+        for (int waves = 2; waves >= 1; --waves) {
+            MpassTmaArgs a = mpass_tma_layout(pl, waves);
+            for (int n = 0; n < N; ++n) pl->n_mp[n] = std::max(pl->n_mp[n], a.m[n].ncg);
+        }
+        pl->mpt = mpass_tma_layout(pl, 1);
     }
     int nparts = std::max(pl->fg.nregions, pl->fg_plain.nregions);
+    for (int q = 0; q < pl->n_fcand; ++q) nparts = std::max(nparts, pl->fcand[q].nregions);
+    pl->nparts_max = nparts;
     // footprint (padded sizes)
     const int64_t Dp = pl->D;
     size_t f = align256(sizeof(DevScalars));
@@ -437,6 +483,7 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     }
     f += align256((size_t)nparts * (3 + N) * 4);
     f += align256(1024 * 4) + align256(PASD_MAXN * 4) + align256(4);   // + idle-skip factor
+    f += align256(sizeof(DevScalars));                     // autotuner scalars
     f += align256((size_t)p.max_iter * PASD_TRACE_STRIDE * 8);
     if (pl->pad) f += align256(Dp * 4);                    // output-pass target
     pl->footprint = f;
@@ -447,6 +494,26 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     pl->test_wait_timeout = tw && tw[0] == '1';
     *out = pl;
     return PASD_OK;
+}
+
+// TMA M-pass CTAs: row strips x column ranges, `waves` times as many as fit on
+// the device at once, split over the (non few-row) modes in proportion to their work
+static MpassTmaArgs mpass_tma_layout(const pasd_plan_t* pl, int waves) {
+    MpassTmaArgs a = pl->mpt;
+    const int slots = waves * pl->mpt_slots;
+    int start = 0;
+    for (int n = 0; n < pl->N; ++n) {
+        MpassTmaMode& mm = a.m[n];
+        a.cta_start[n] = start;
+        if (pl->ap_small[n]) { mm.ncg = 0; mm.cpr = 1; continue; }
+        int64_t target = (int64_t)((double)slots * (double)pl->mpt_work[n] / (double)std::max<int64_t>(pl->mpt_tot, 1));
+        int64_t ncg = std::max<int64_t>(1, target / mm.nstrips);
+        mm.cpr = (int)((mm.nch + ncg - 1) / ncg);
+        mm.ncg = (mm.nch + mm.cpr - 1) / mm.cpr;
+        start += mm.nstrips * mm.ncg;
+    }
+    a.cta_start[pl->N] = start;
+    return a;
 }
 
 static void launch_fused_pass(pasd_plan_t* pl, int output, float* L, cudaStream_t s) {
@@ -462,14 +529,21 @@ static void launch_fused_pass(pasd_plan_t* pl, int output, float* L, cudaStream_
 
 static int launch_apass_all(pasd_plan_t* pl, cudaStream_t s) {
     int launches = 0;
+    for (int n = 0; n < pl->N; ++n)
+        if (pl->ap_small[n]) { launch_apass_small(pl->ap[n], pl->ap_small_grid[n], s); ++launches; }
     for (int q = 0; q < pl->n_ap_tma; ++q) { launch_apass_tma(pl->ap_tma[q], s); ++launches; }
     if (pl->n_ap_plain > 0) launches += launch_apass_modes(pl->ap_plain, pl->n_ap_plain, s);
     return launches;
 }
 
-static void launch_mpass_any(pasd_plan_t* pl, cudaStream_t s) {
+static int launch_mpass_any(pasd_plan_t* pl, cudaStream_t s) {
+    int launches = 0;
+    for (int n = 0; n < pl->N; ++n)
+        if (pl->ap_small[n]) { launch_mpass_small(pl->mp_small[n], pl->ap_small_grid[n], s); ++launches; }
+    if (pl->n_mp_big == 0) return launches;
     if (pl->mp_use_tma) launch_mpass_tma(pl->mp_tma, s);
     else launch_mpass(pl->mpa, pl->mp_smem, s);
+    return launches + 1;
 }
 
 static void enqueue_iteration(pasd_plan_t* pl, cudaStream_t s) {
@@ -478,8 +552,189 @@ static void enqueue_iteration(pasd_plan_t* pl, cudaStream_t s) {
     launch_svt(pl->small, s);
     launch_vrot(pl->vr, s);
     launch_fused_pass(pl, 0, nullptr, s);
-    launch_mpass_any(pl, s);
+    pl->mp_launches = launch_mpass_any(pl, s);
     launch_finalize(pl->fin, s);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: tile shapes per problem shape, timed on the plan's own buffers at
+// its first use and cached for the process
+// ---------------------------------------------------------------------------
+struct TuneChoice {
+    int fused_k;     // resident CTAs per SM of the fused pass's geometry
+    int mp_waves;    // waves of M-pass CTAs
+    int ap_half;     // 1: the A-pass FMA kernel with half its default columns per thread
+};
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneChoice> g_tune_cache;
+
+static std::string tune_key(const pasd_plan_t* pl) {
+    std::string k = std::to_string(pl->ctx->device) + "|" + std::to_string(pl->want_tma) + "|" +
+                    std::to_string(pl->ap_kind);
+    for (int n = 0; n < pl->N; ++n)
+        k += "|" + std::to_string(pl->m[n].I) + "x" + std::to_string(pl->m[n].Rp) + (pl->ap_small[n] ? "s" : "");
+    return k;
+}
+
+// mean milliseconds of `reps` launches after one untimed launch (nan on error)
+template <class F>
+static float time_launches(cudaStream_t s, F f, int reps) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return NAN;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return NAN; }
+    f();
+    cudaEventRecord(a, s);
+    for (int i = 0; i < reps; ++i) f();
+    cudaEventRecord(b, s);
+    float ms = NAN;
+    if (cudaEventSynchronize(b) == cudaSuccess && cudaGetLastError() == cudaSuccess) {
+        cudaEventElapsedTime(&ms, a, b);
+        ms /= reps;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+// Tuning state: the launches read only these scalars (nothing has been solved:
+// the arena is zero, so every value the timed kernels read or write stays zero).
+static void set_tune_scalars(pasd_plan_t* pl, bool active) {
+    DevScalars h{};
+    h.mu = 1.0;
+    h.t_norm_fro = 1.0;
+    for (int n = 0; n < pl->N; ++n) h.kept[n] = active ? std::max(1, pl->m[n].R / 2) : 0;
+    cudaMemcpyAsync(pl->tune_sc, &h, sizeof(h), cudaMemcpyHostToDevice, pl->cap_stream);
+}
+
+static MpassTmaArgs mpass_candidate(const pasd_plan_t* pl, int waves, DevScalars* sc) {
+    MpassTmaArgs a = mpass_tma_layout(pl, waves);
+    a.sc = sc;
+    for (int n = 0; n < pl->N; ++n) a.m[n].part = pl->mp[n];
+    return a;
+}
+
+static MpassTmaPlan* make_mpass_candidate(const pasd_plan_t* pl, const MpassTmaArgs& a) {
+    const float* gp[PASD_MAXN];
+    const float* vp[PASD_MAXN];
+    for (int n = 0; n < pl->N; ++n) { gp[n] = pl->G[n]; vp[n] = pl->Vr[n]; }
+    char err[256];
+    return make_mpass_tma(a, gp, vp, pl->mpt_smem, err, sizeof(err));
+}
+
+// Switches the plan's kernels to the choice `c` (fused geometry, M-pass layout,
+// A-pass columns per thread); a shape whose maps the driver refuses stays as it was.
+static void apply_tune(pasd_plan_t* pl, const TuneChoice& c) {
+    char err[256];
+    if (pl->tma && c.fused_k != pl->tuned_fused_k) {
+        for (int q = 0; q < pl->n_fcand; ++q) {
+            if (pl->fcand_k[q] != c.fused_k) continue;
+            FusedArgs fu2 = pl->fu;
+            fu2.g = pl->fcand[q];
+            FusedTmaPlan* tp = make_fused_tma(fu2, pl->Tc, err, sizeof(err));
+            if (!tp) break;
+            destroy_fused_tma(pl->tma);
+            pl->tma = tp;
+            pl->fg = pl->fcand[q];
+            pl->fu.g = pl->fg;
+            pl->fin.nparts = pl->fg.nregions;
+            pl->tuned_fused_k = c.fused_k;
+            break;
+        }
+    }
+    if (pl->mp_tma && c.mp_waves != pl->tuned_mp_waves) {
+        MpassTmaArgs a = mpass_candidate(pl, c.mp_waves, pl->sc);
+        MpassTmaPlan* mp = make_mpass_candidate(pl, a);
+        if (mp) {
+            destroy_mpass_tma(pl->mp_tma);
+            pl->mp_tma = mp;
+            pl->mpt = a;
+            for (int n = 0; n < pl->N; ++n)
+                if (!pl->ap_small[n]) pl->fin.n_mp[n] = a.m[n].ncg;
+            pl->tuned_mp_waves = c.mp_waves;
+        }
+    }
+    for (int q = 0; q < pl->n_ap_tma; ++q) {
+        const int cur = apass_tma_cols(pl->ap_tma[q]);
+        if (cur == 0) continue;
+        const int def = pl->ap_tma_default_nc[q];
+        apass_tma_set_cols(pl->ap_tma[q], c.ap_half ? def / 2 : def);
+    }
+    pl->tuned_ap_half = c.ap_half;
+}
+
+// Times the candidates on the plan's own buffers (before its first pasd_begin
+// fills them) and keeps one only if it beats the planner's default by more than
+// 3%, so timing noise between near-equal shapes does not flip the choice; the
+// choice is cached per device and problem shape.
+static void autotune(pasd_plan_t* pl) {
+    pl->tuned = true;
+    pl->tuned_fused_k = pl->default_fused_k;
+    pl->tuned_mp_waves = 1;
+    for (int q = 0; q < pl->n_ap_tma; ++q) pl->ap_tma_default_nc[q] = apass_tma_cols(pl->ap_tma[q]);
+    const char* nt = std::getenv("PASD_NO_TUNE");
+    if (nt && nt[0] == '1') { pl->tune_mode = "off"; return; }
+    const std::string key = tune_key(pl);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { apply_tune(pl, it->second); pl->tune_mode = "cached"; return; }
+    }
+    pl->tune_mode = "timed";
+    cudaStream_t s = pl->cap_stream;
+    TuneChoice choice{pl->default_fused_k, 1, 0};
+    char err[256];
+    if (pl->tma && pl->n_fcand > 1) {
+        float t_def = NAN, best = INFINITY;
+        int best_k = pl->default_fused_k;
+        for (int q = 0; q < pl->n_fcand; ++q) {
+            FusedArgs fc = pl->fu;
+            fc.g = pl->fcand[q];
+            fc.sc = pl->tune_sc;
+            FusedTmaPlan* tp = make_fused_tma(fc, pl->Tc, err, sizeof(err));
+            if (!tp) continue;
+            float t = 0.f;
+            for (int active = 0; active < 2; ++active) {
+                set_tune_scalars(pl, active != 0);
+                t += time_launches(s, [&] { launch_fused_tma(tp, 0, nullptr, s); }, 3);
+            }
+            destroy_fused_tma(tp);
+            if (!(t == t)) continue;
+            if (pl->fcand_k[q] == pl->default_fused_k) t_def = t;
+            if (t < best) { best = t; best_k = pl->fcand_k[q]; }
+        }
+        if (t_def == t_def && best < 0.97f * t_def) choice.fused_k = best_k;
+    }
+    if (pl->mp_tma) {
+        set_tune_scalars(pl, true);
+        float tw[3] = {NAN, NAN, NAN};
+        for (int waves = 1; waves <= 2; ++waves) {
+            MpassTmaPlan* mp = make_mpass_candidate(pl, mpass_candidate(pl, waves, pl->tune_sc));
+            if (!mp) continue;
+            tw[waves] = time_launches(s, [&] { launch_mpass_tma(mp, s); }, 3);
+            destroy_mpass_tma(mp);
+        }
+        if (tw[1] == tw[1] && tw[2] == tw[2] && tw[2] < 0.97f * tw[1]) choice.mp_waves = 2;
+    }
+    if (pl->n_ap_tma > 0 && pl->ap_kind == APASS_FFMA) {
+        // the A-pass reads only the done flag, which is clear before the first pasd_begin
+        float th[2] = {NAN, NAN};
+        for (int half = 0; half < 2; ++half) {
+            for (int q = 0; q < pl->n_ap_tma; ++q) {
+                const int def = pl->ap_tma_default_nc[q];
+                apass_tma_set_cols(pl->ap_tma[q], half ? def / 2 : def);
+            }
+            th[half] = time_launches(s, [&] { launch_apass_all(pl, s); }, 3);
+        }
+        for (int q = 0; q < pl->n_ap_tma; ++q) apass_tma_set_cols(pl->ap_tma[q], pl->ap_tma_default_nc[q]);
+        if (th[0] == th[0] && th[1] == th[1] && th[1] < 0.97f * th[0]) choice.ap_half = 1;
+    }
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache.emplace(key, choice);
+    }
+    apply_tune(pl, choice);
 }
 
 static pasd_status ensure_allocated(pasd_plan_t* pl) {
@@ -510,7 +765,8 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
         pl->scratch[n] = reinterpret_cast<float*>(take((size_t)4 * g.I * g.Rp * 4));
         pl->Mred[n] = reinterpret_cast<float*>(take((size_t)g.I * g.Rp * 4));
     }
-    pl->part = reinterpret_cast<float*>(take((size_t)std::max(pl->fg.nregions, pl->fg_plain.nregions) * (3 + N) * 4));
+    pl->part = reinterpret_cast<float*>(take((size_t)pl->nparts_max * (3 + N) * 4));
+    pl->tune_sc = reinterpret_cast<DevScalars*>(take(sizeof(DevScalars)));
     pl->sq_part = reinterpret_cast<float*>(take(1024 * 4));
     pl->kept = reinterpret_cast<int32_t*>(take(PASD_MAXN * 4));
     pl->idle_g = reinterpret_cast<float*>(take(4));
@@ -567,12 +823,14 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
     va.N = N;
     va.sc = pl->sc;
     va.cta_start[0] = 0;
+    int vr_maxRp = 4;
+    for (int n = 0; n < N; ++n) vr_maxRp = std::max(vr_maxRp, pl->m[n].Rp);
     for (int n = 0; n < N; ++n) {
         const ModeGeom& g = pl->m[n];
         VrotMode& vm = va.m[n];
         vm.A = pl->A[n]; vm.V = pl->Vr[n]; vm.W = pl->W[n]; vm.F = pl->F[n];
         vm.P = g.P; vm.post = g.post; vm.R = g.R; vm.Rp = g.Rp;
-        va.cta_start[n + 1] = va.cta_start[n] + (int)((g.P + 255) / 256);
+        va.cta_start[n + 1] = va.cta_start[n] + vrot_ctas(g.P, g.post, vr_maxRp);
     }
     pl->mpa.sc = pl->sc;
     for (int n = 0; n < N; ++n) {
@@ -631,7 +889,19 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
         pl->mp_tma = make_mpass_tma(pl->mpt, gp, vp, pl->mpt_smem, err, sizeof(err));
         if (!pl->mp_tma) pl->mp_use_tma = false;
     }
-    for (int n = 0; n < N; ++n) fi.n_mp[n] = pl->mp_use_tma ? pl->mpt.m[n].ncg : pl->mpa.m[n].ncg;
+    pl->n_mp_big = 0;
+    for (int n = 0; n < N; ++n) {
+        const ModeGeom& g = pl->m[n];
+        if (pl->ap_small[n]) {
+            MpassSmallArgs& ms = pl->mp_small[n];
+            ms.G = pl->G[n]; ms.V = pl->Vr[n]; ms.part = pl->mp[n]; ms.sc = pl->sc;
+            ms.I = g.I; ms.pre = g.pre; ms.post = g.post; ms.P = g.P; ms.Rp = g.Rp; ms.mode = n;
+            fi.n_mp[n] = pl->ap_small_grid[n];
+        } else {
+            ++pl->n_mp_big;
+            fi.n_mp[n] = pl->mp_use_tma ? pl->mpt.m[n].ncg : pl->mpa.m[n].ncg;
+        }
+    }
 
     // A-pass: TMA plans for the modes whose layout allows them (grouped by padded
     // rank), the cp.async kernel for the rest or when a tensor map is refused
@@ -651,10 +921,13 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
         }
         for (int n = 0; n < N; ++n) {
             const ModeGeom& g = pl->m[n];
+            if (pl->ap_small[n]) { sa.m[n].n_gram = pl->ap_small_grid[n]; continue; }
             if (!pl->ap_use_tma[n]) pl->ap_plain[pl->n_ap_plain++] = pl->ap[n];
             sa.m[n].n_gram = pl->ap_use_tma[n] ? apass_tma_tasks(g.I, g.pre, g.post, pl->ap_kind) : apass_ncta(g.P);
         }
     }
+
+    autotune(pl);
 
     if (pl->use_graph) {
         CUDA_TRY(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -731,8 +1004,33 @@ extern "C" pasd_status pasd_profile_iterations(pasd_plan_t* pl, int32_t iters, d
     return PASD_OK;
 }
 
+extern "C" pasd_status pasd_plan_info(const pasd_plan_t* pl, char* buf, size_t len) {
+    if (!pl || !buf || len == 0) return fail(PASD_ERR_INVALID_ARG, "bad argument");
+    const FusedGeom& g = pl->fg;
+    std::string box, few;
+    for (int n = 0; n < pl->N; ++n) {
+        box += (n ? "," : "") + std::to_string(g.b[n]);
+        if (pl->ap_small[n]) few += (few.empty() ? "" : ",") + std::to_string(n);
+    }
+    int mp_ctas = pl->mp_use_tma ? pl->mpt.cta_start[pl->N] : pl->mpa.cta_start[pl->N];
+    std::string apc;
+    for (int q = 0; q < pl->n_ap_tma; ++q) apc += (q ? "," : "") + std::to_string(apass_tma_cols(pl->ap_tma[q]));
+    char tmp[1024];
+    snprintf(tmp, sizeof(tmp),
+             "{\"autotune\": \"%s\", \"fused\": {\"tma\": %d, \"ctas_per_sm\": %d, \"box\": [%s], \"regions\": %d, "
+             "\"threads\": %d, \"candidates\": %d}, \"mpass\": {\"tma\": %d, \"waves\": %d, \"ctas\": %d}, "
+             "\"apass_cols_per_thread\": [%s], \"fewrow_modes\": [%s], \"launches_per_iter\": %d}",
+             pl->tune_mode, pl->tma != nullptr || (!pl->arena && pl->want_tma) ? 1 : 0,
+             pl->tuned ? pl->tuned_fused_k : pl->default_fused_k, box.c_str(), g.nregions,
+             g.tma ? g.nthreads : FU_THREADS, pl->n_fcand, pl->mp_use_tma ? 1 : 0, pl->tuned_mp_waves, mp_ctas,
+             apc.c_str(), few.c_str(), pl->ap_launches + pl->mp_launches + 5);
+    if (std::strlen(tmp) + 1 > len) return fail(PASD_ERR_INVALID_ARG, "buffer too small");
+    std::memcpy(buf, tmp, std::strlen(tmp) + 1);
+    return PASD_OK;
+}
+
 extern "C" int32_t pasd_launches_per_iter(const pasd_plan_t* pl) {
-    return pl ? pl->ap_launches + 6 : 0;
+    return pl ? pl->ap_launches + pl->mp_launches + 5 : 0;
 }
 
 // ---------------------------------------------------------------------------

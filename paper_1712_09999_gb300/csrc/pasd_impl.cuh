@@ -99,12 +99,31 @@ int apass_tma_tasks(int64_t I, int64_t pre, int64_t post, int kind);
 ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, int kind, int num_sms, char* err,
                              size_t errlen);
 void launch_apass_tma(const ApassTmaPlan* p, cudaStream_t s);
+// FMA kernel's columns per thread (0 for the tensor-core kernel); the setter
+// accepts the default or half of it (an autotuner candidate)
+int apass_tma_cols(const ApassTmaPlan* p);
+void apass_tma_set_cols(ApassTmaPlan* p, int nc);
 void destroy_apass_tma(ApassTmaPlan* p);
 // All modes in as few launches as possible (one per distinct padded rank);
 // returns the number of launches.
 int launch_apass_modes(const ApassArgs* a, int N, cudaStream_t s);
 size_t apass_smem_bytes(int Rp, bool rowmajor);
 int apass_ncta(int64_t P);
+// Modes with I_n <= 8 and Rp <= 8 (fewrow.cu): one thread per four columns, a
+// fixed grid, one Gram partial (A-pass) or one G_n Vrot_n^T partial (M-pass)
+// per CTA.
+bool apass_small_supported(int64_t I, int Rp);
+int apass_small_grid(int num_sms, int64_t P);
+void launch_apass_small(const ApassArgs& a, int grid, cudaStream_t s);
+struct MpassSmallArgs {
+    const float* G;        // G_n (D floats)
+    const float* V;        // Vrot_n, [pre][Rp][post]
+    float* part;           // [grid][I][Rp]
+    const DevScalars* sc;
+    int64_t I, pre, post, P;
+    int Rp, mode;
+};
+void launch_mpass_small(const MpassSmallArgs& m, int grid, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // Small per-mode kernels (one CTA per mode): polar (U-step), SVT, finalize
@@ -188,6 +207,8 @@ struct VrotArgs {
     int cta_start[PASD_MAXN + 1];
 };
 void launch_vrot(const VrotArgs& a, cudaStream_t s);
+// CTAs the Vrot launch gives a mode of P columns (maxRp: the largest Rp of the plan)
+int vrot_ctas(int64_t P, int64_t post, int maxRp);
 void launch_norm_fro(const float* T, int64_t D, float* part, int nparts, DevScalars* sc,
                      cudaStream_t s);
 void launch_export_y(const float* G, const float* T, const float* E, const DevScalars* sc,

@@ -50,6 +50,10 @@ constexpr int TILE_SCRATCH = 4096;   // floats of split partial sums for tile_At
 // update is evaluated in an order that is symmetric in (i, j) with explicit
 // rounding, so A stays exactly symmetric.
 // ---------------------------------------------------------------------------
+struct JacobiBufs {
+    float *A, *V, *A2, *V2, *cs;
+    int* pc;
+};
 // Buffers holding the eigenvalues (diagonal) and eigenvectors (columns) on return.
 struct EigBufs {
     float* A;
@@ -73,22 +77,33 @@ __device__ __forceinline__ int rr_partner(int i, int round, int m) {
 // (a Jacobi round is a chain of dependent steps; the correctly rounded forms
 // made it about a quarter slower); c and s come from the same t, so the
 // rotation is orthogonal to rounding whatever t's last bits are.
+// With `exact` the tangent and the cosine use correctly rounded division and
+// square root instead: about a quarter of the error of each rotation, which a
+// rank above 24 needs (there the many rotations of each entry add their
+// rounding to the eigenvector directions; see sym_eig_orth).
 __device__ __forceinline__ int pair_rotation(const float* A, int ld, int i, int pi, float tol, float& ci,
-                                             float& si) {
+                                             float& si, bool exact = false) {
     const int p = min(i, pi), q = max(i, pi);
     const float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
     float c = 1.f, s = 0.f;
     int rot = 0;
     if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq))) {
-        const float theta = __fdividef(aqq - app, 2.f * apq);
         float tt;
-        if (fabsf(theta) > 1e18f) {
-            tt = __fdividef(0.5f, theta);
+        if (exact) {
+            const float theta = (aqq - app) / (2.f * apq);
+            if (fabsf(theta) > 1e18f) tt = 0.5f / theta;
+            else tt = copysignf(1.f / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f))), theta);
+            c = 1.f / sqrtf(fmaf(tt, tt, 1.f));
         } else {
-            const float r = fmaf(theta, theta, 1.f);
-            tt = copysignf(__fdividef(1.f, fabsf(theta) + r * rsqrtf(r)), theta);
+            const float theta = __fdividef(aqq - app, 2.f * apq);
+            if (fabsf(theta) > 1e18f) {
+                tt = __fdividef(0.5f, theta);
+            } else {
+                const float r = fmaf(theta, theta, 1.f);
+                tt = copysignf(__fdividef(1.f, fabsf(theta) + r * rsqrtf(r)), theta);
+            }
+            c = rsqrtf(fmaf(tt, tt, 1.f));
         }
-        c = rsqrtf(fmaf(tt, tt, 1.f));
         s = tt * c;
         rot = 1;
     }
@@ -124,7 +139,7 @@ __device__ EigBufs block_jacobi(float* A, float* V, float* A2, float* V2, int* p
                 if (t < m) {
                     const int pi = rr_partner(t, round, m);
                     float ci, si;
-                    rot = pair_rotation(A, ld, t, pi, tol, ci, si);
+                    rot = pair_rotation(A, ld, t, pi, tol, ci, si, n > 24);
                     pc[t] = pi;
                     cs[2 * t] = ci;
                     cs[2 * t + 1] = si;
@@ -285,6 +300,19 @@ __device__ void tile_AB(const float* X, int ldx, int inner, const float* S, int 
     }
 }
 
+// Symmetric eigen-solve whose eigenvector matrix, above kOrthMinN, is
+// re-orthonormalised by one Newton-Schulz step V (3 I - V^T V) / 2. Each Jacobi
+// rotation is orthogonal only to the rounding of its approximate reciprocal
+// square root, and a high-rank Gram matrix formed in FP32 needs many sweeps of
+// rotations, so V^T V drifts from I (by about 1e-6 at rank 60, enough to move L
+// by 5e-5 over a few hundred loop bodies: the refold and the U-step are
+// sensitive to that drift rather than to the last bits of the directions). At
+// low rank the drift is far below that and the step is skipped. With no
+// rotation at all V = I and the step returns I exactly. `scratch` holds
+// TILE_SCRATCH floats.
+constexpr int kOrthMinN = 24;
+__device__ EigBufs sym_eig_orth(JacobiBufs& jb, int n, int ld, float tol, int max_sweeps, float* scratch);
+
 // Z = Q diag(w^{-1/2}) Q^T for the n x n eigen-system (Q columns, eigenvalues w
 // on the diagonal of D); entries up to the next multiple of 4 are zero.
 // Nonpositive eigenvalues (rank loss) map to 0. Ends with a barrier.
@@ -329,10 +357,7 @@ __device__ void copy_cols(const float* src, int lds, int c0, int w, int64_t rows
     }
 }
 
-struct JacobiBufs {
-    float *A, *V, *A2, *V2, *cs;
-    int* pc;
-};
+
 
 __device__ JacobiBufs carve_jacobi(float* base, int ld) {
     JacobiBufs b;
@@ -347,6 +372,24 @@ __device__ JacobiBufs carve_jacobi(float* base, int ld) {
 // (a multiple of 4 floats, so what follows stays 16-byte aligned)
 __host__ __device__ constexpr int jacobi_floats(int ld) { return 4 * ld * ld + 4 * ld; }
 
+__device__ EigBufs sym_eig_orth(JacobiBufs& jb, int n, int ld, float tol, int max_sweeps, float* scratch) {
+    const EigBufs eb = block_jacobi(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, n, ld, tol, max_sweeps);
+    if (n <= kOrthMinN) return eb;
+    // the pair of buffers the last round did not leave its result in
+    float* K = eb.A == jb.A ? jb.A2 : jb.A;
+    float* out = eb.V == jb.V ? jb.V2 : jb.V;
+    const int n4 = (n + 3) & ~3;
+    tile_AtB(eb.V, ld, n, eb.V, ld, n, n, K, ld, true, scratch);    // K = V^T V (zero padded to n4)
+    for (int idx = threadIdx.x; idx < n4 * n4; idx += blockDim.x) {
+        const int i = idx / n4, j = idx % n4;
+        K[i * ld + j] = (i < n && j < n) ? ((i == j) ? 1.5f : 0.f) - 0.5f * K[i * ld + j] : 0.f;
+    }
+    __syncthreads();
+    tile_AB(eb.V, ld, n, K, ld, n4, n, out, ld, false);            // rows < n, columns < n4
+    __syncthreads();
+    return EigBufs{eb.A, out};
+}
+
 // Row stride of the I x R matrices of the U-step in shared memory: a multiple of
 // 4 with (stride / 4) odd, so float4 rows of consecutive rows hit distinct banks.
 __host__ __device__ inline int polar_ld(int Rp) { return ((Rp / 4) & 1) ? Rp : Rp + 4; }
@@ -354,7 +397,8 @@ __host__ __device__ inline int polar_ld(int Rp) { return ((Rp / 4) & 1) ? Rp : R
 // ---------------------------------------------------------------------------
 // SVT (Eq. 13 and the SVT definition after it), one CTA per mode.
 // ---------------------------------------------------------------------------
-__host__ __device__ inline int svt_red_floats(int Rp) { return Rp * Rp > 2048 ? Rp * Rp : 2048; }
+// (also the scratch of the eigenvector re-orthonormalisation: TILE_SCRATCH floats)
+__host__ __device__ inline int svt_red_floats(int Rp) { return Rp * Rp > TILE_SCRATCH ? Rp * Rp : TILE_SCRATCH; }
 
 __global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
     DevScalars* sc = sa.sc;
@@ -408,7 +452,7 @@ __global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
         __syncthreads();
     }
     // 2. eigen-decomposition
-    const EigBufs eb = sym_eig(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, R, ld, 1e-6f, 30);
+    const EigBufs eb = sym_eig_orth(jb, R, ld, 1e-6f, 30, red);
     const float* Ae = eb.A;
     const float* Ve = eb.V;
     sort_desc(Ae, R, ld, perm);
@@ -531,7 +575,7 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
         __syncthreads();
         // B1 = M^T M, Z1 = B1^{-1/2}, P1 = M Z1
         tile_AtB(Pw, LD, s, Pw, LD, s, I, jb.A, ld, true, tsc);
-        const EigBufs eb = sym_eig(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, s, ld, 1e-6f, 30);
+        const EigBufs eb = sym_eig_orth(jb, s, ld, 1e-6f, 30, tsc);
         const float* Ae = eb.A;
         const float* Ve = eb.V;
         inv_sqrt_from_eig(Ae, Ve, s, ld, Z);
@@ -549,7 +593,7 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
             __syncthreads();
         }
         tile_AtB(Bw, LD, q, Bw, LD, q, I, jb.A, ld, true, tsc);
-        const EigBufs eb = sym_eig(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, q, ld, 1e-6f, 30);
+        const EigBufs eb = sym_eig_orth(jb, q, ld, 1e-6f, 30, tsc);
         const float* Ae = eb.A;
         const float* Ve = eb.V;
         inv_sqrt_from_eig(Ae, Ve, q, ld, Z);
@@ -757,9 +801,18 @@ void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Vrot_n = diag(F) W^T A_n: the small factor V_n of Eq. 13 in the eigenbasis of
 // the SVT, stored like A_n ([pre][Rp][post]); rows at and beyond the kept
-// count are zero. One thread per unfolding column, all modes in one launch.
+// count are zero. All modes in one launch. A thread owns four consecutive
+// columns b .. b + 3 of one a-row when post % 4 == 0 (one 16-byte load per row
+// of A and one 16-byte store per row of Vrot), else one column (post == 1: the
+// Rp contiguous floats of the column, as float4 moves).
 // ---------------------------------------------------------------------------
-template <int RB>
+// (four columns a thread only where there are enough columns to fill the GPU
+// with the fatter threads)
+__host__ __device__ inline int vrot_cols(int64_t P, int64_t post, int RB) {
+    return (post % 4 == 0 && post > 1 && RB <= 32 && P >= (1 << 18)) ? 4 : 1;
+}
+
+template <int RB, bool V4>
 __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     const DevScalars* sc = va.sc;
     if (sc->done) return;
@@ -773,16 +826,52 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     const int s4 = (s + 3) & ~3;
     if (s4 == 0) return;
     // Wt[i][r] = F_i W[r][i] with row stride RB, zero for R <= r < RB: the
-    // product below runs over all RB entries of a row as float4 broadcasts, and
-    // the padding terms are exact zeros added last, so each sum is the same as
-    // over r < R
+    // product below runs over the float4 groups r < Rp of a row as broadcasts,
+    // and the padding terms are exact zeros, so each sum is the same as over r < R
     __shared__ __align__(16) float Wt[PASD_MAXR * PASD_MAXR];
     for (int idx = threadIdx.x; idx < s * RB; idx += blockDim.x) {
         const int i = idx / RB, r = idx % RB;
         Wt[idx] = r < R ? m.F[i] * m.W[r * Rp + i] : 0.f;
     }
     __syncthreads();
-    const int64_t j = (int64_t)(blockIdx.x - va.cta_start[k]) * blockDim.x + threadIdx.x;
+    const int64_t u = (int64_t)(blockIdx.x - va.cta_start[k]) * blockDim.x + threadIdx.x;
+    if (V4 && vrot_cols(m.P, m.post, RB) == 4) {
+        const int64_t per_row = m.post / 4;
+        if (u >= m.P / 4) return;
+        const int64_t a = u / per_row, b = 4 * (u - a * per_row);
+        const float* src = m.A + a * Rp * m.post + b;
+        float* dst = m.V + a * Rp * m.post + b;
+        float av[RB][4];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < R) v = *reinterpret_cast<const float4*>(src + (int64_t)r * m.post);
+            av[r][0] = v.x; av[r][1] = v.y; av[r][2] = v.z; av[r][3] = v.w;
+        }
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            if (i < s4) {
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                if (i < s) {
+                    const float4* w4 = reinterpret_cast<const float4*>(Wt + i * RB);
+#pragma unroll
+                    for (int r4 = 0; r4 < RB / 4; ++r4) {
+                        if (4 * r4 < Rp) {
+                            const float4 w = w4[r4];
+                            const float ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) acc[c] = fmaf(ws[q], av[4 * r4 + q][c], acc[c]);
+                        }
+                    }
+                }
+                *reinterpret_cast<float4*>(dst + (int64_t)i * m.post) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            }
+        }
+        return;
+    }
+    const int64_t j = u;
     if (j >= m.P) return;
     const int64_t a = j / m.post, b = j % m.post;
     const float* src = m.A + a * Rp * m.post + b;
@@ -813,11 +902,13 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
             const float4* w4 = reinterpret_cast<const float4*>(Wt + i * RB);
 #pragma unroll
             for (int r4 = 0; r4 < RB / 4; ++r4) {
-                const float4 w = w4[r4];
-                acc = fmaf(w.x, av[4 * r4], acc);
-                acc = fmaf(w.y, av[4 * r4 + 1], acc);
-                acc = fmaf(w.z, av[4 * r4 + 2], acc);
-                acc = fmaf(w.w, av[4 * r4 + 3], acc);
+                if (4 * r4 < Rp) {
+                    const float4 w = w4[r4];
+                    acc = fmaf(w.x, av[4 * r4], acc);
+                    acc = fmaf(w.y, av[4 * r4 + 1], acc);
+                    acc = fmaf(w.z, av[4 * r4 + 2], acc);
+                    acc = fmaf(w.w, av[4 * r4 + 3], acc);
+                }
             }
         }
         out[i] = acc;
@@ -834,16 +925,38 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     }
 }
 
+int vrot_rb(int maxRp) {
+    return maxRp <= 8 ? 8 : maxRp <= 16 ? 16 : maxRp <= 24 ? 24 : maxRp <= 32 ? 32 : maxRp <= 48 ? 48 : 64;
+}
+
+// CTAs of mode n's part of the launch (256 threads, one or four columns each)
+int vrot_ctas(int64_t P, int64_t post, int maxRp) {
+    const int cols = vrot_cols(P, post, vrot_rb(maxRp));
+    return (int)((P / cols + 255) / 256);
+}
+
+// The four-column path is compiled into the launch only when some mode takes it:
+// its registers would otherwise slow every mode's one-column path.
+template <int RB>
+static void launch_vrot_rb(const VrotArgs& a, cudaStream_t s) {
+    bool v4 = false;
+    for (int n = 0; n < a.N; ++n) v4 = v4 || vrot_cols(a.m[n].P, a.m[n].post, RB) == 4;
+    const int grid = a.cta_start[a.N];
+    if (v4) vrot_kernel<RB, true><<<grid, 256, 0, s>>>(a);
+    else vrot_kernel<RB, false><<<grid, 256, 0, s>>>(a);
+}
+
 void launch_vrot(const VrotArgs& a, cudaStream_t s) {
     int maxRp = 4;
     for (int n = 0; n < a.N; ++n) maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
-    const int grid = a.cta_start[a.N];
-    if (maxRp <= 8) vrot_kernel<8><<<grid, 256, 0, s>>>(a);
-    else if (maxRp <= 16) vrot_kernel<16><<<grid, 256, 0, s>>>(a);
-    else if (maxRp <= 24) vrot_kernel<24><<<grid, 256, 0, s>>>(a);
-    else if (maxRp <= 32) vrot_kernel<32><<<grid, 256, 0, s>>>(a);
-    else if (maxRp <= 48) vrot_kernel<48><<<grid, 256, 0, s>>>(a);
-    else vrot_kernel<64><<<grid, 256, 0, s>>>(a);
+    switch (vrot_rb(maxRp)) {
+        case 8: launch_vrot_rb<8>(a, s); break;
+        case 16: launch_vrot_rb<16>(a, s); break;
+        case 24: launch_vrot_rb<24>(a, s); break;
+        case 32: launch_vrot_rb<32>(a, s); break;
+        case 48: launch_vrot_rb<48>(a, s); break;
+        default: launch_vrot_rb<64>(a, s); break;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -89,6 +89,7 @@ _SIGS = {
     "pasd_state_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_size_t, ctypes.c_void_p]),
     "pasd_launches_per_iter": (ctypes.c_int32, [ctypes.c_void_p]),
+    "pasd_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "pasd_profile_iterations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "pasd_mode_product": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
@@ -241,6 +242,14 @@ def pasd_state_get(plan: int, item: int, mode: int, out, stream=None) -> None:
 
 def pasd_launches_per_iter(plan: int) -> int:
     return int(lib().pasd_launches_per_iter(plan))
+
+
+def pasd_plan_info(plan: int) -> dict:
+    """The plan's kernel configuration (tile boxes, CTAs, autotuner choice)."""
+    import json
+    buf = ctypes.create_string_buffer(1024)
+    _check(lib().pasd_plan_info(plan, buf, len(buf)), "pasd_plan_info")
+    return json.loads(buf.value.decode())
 
 
 def pasd_mode_product(X, pre: int, I: int, post: int, U, R: int, A, gram=None, stream=None) -> None:

@@ -162,6 +162,41 @@ def test_mixed_video_shape_matches_oracle(env):
     assert abs(O.rse(g["L"], pr.L0) - O.rse(ref.L, pr.L0)) <= 1e-4
 
 
+# --- autotuner -------------------------------------------------------------------------
+
+def test_autotuner_choice_is_cached_reported_and_harmless(env, monkeypatch):
+    # Two plans of one shape: the first times the candidates at its first use, the
+    # second takes the cached choice; both report it and agree bit for bit. A plan
+    # with tuning off keeps the planner's default and agrees to rounding.
+    torch, P, ctx = env
+    pr = synth.planted((64, 48, 40), (4, 4, 4), 0.1, 3, scale="std", amp=5.0)
+    params = P.make_params(pr.T.shape, (8, 8, 8), stop=P.STOP_FIXED_ITERS, max_iter=150)
+    T = torch.from_numpy(pr.T).cuda()
+    outs, infos = [], []
+    for _ in range(2):
+        plan, _ = P.pasd_plan(ctx, params)
+        assert P.pasd_plan_info(plan)["autotune"] == "pending"
+        L, E = torch.empty_like(T), torch.empty_like(T)
+        P.pasd_solve(plan, T, L, E)
+        infos.append(P.pasd_plan_info(plan))
+        outs.append((L, E))
+        P.pasd_plan_destroy(plan)
+    assert infos[0]["autotune"] in ("timed", "cached") and infos[1]["autotune"] == "cached"
+    for k in ("fused", "mpass", "fewrow_modes", "launches_per_iter"):
+        assert infos[0][k] == infos[1][k]
+    assert infos[0]["fused"]["ctas_per_sm"] in (1, 2, 3) and infos[0]["mpass"]["waves"] in (1, 2)
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    monkeypatch.setenv("PASD_NO_TUNE", "1")
+    plan, _ = P.pasd_plan(ctx, params)
+    L, E = torch.empty_like(T), torch.empty_like(T)
+    P.pasd_solve(plan, T, L, E)
+    monkeypatch.delenv("PASD_NO_TUNE")
+    assert P.pasd_plan_info(plan)["autotune"] == "off"
+    P.pasd_plan_destroy(plan)
+    assert rel(L.cpu().numpy(), outs[0][0].cpu().numpy()) <= 1e-6
+    assert rel(E.cpu().numpy(), outs[0][1].cpu().numpy()) <= 1e-6
+
+
 # --- failure paths of the ABI -------------------------------------------------------
 
 def test_invalid_weights_are_rejected(env):
