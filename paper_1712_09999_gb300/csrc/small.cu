@@ -123,6 +123,8 @@ __device__ EigBufs block_jacobi(float* A, float* V, float* A2, float* V2, int* p
         if (i >= n || j >= n) A[idx] = 0.f;
     }
     __syncthreads();
+    // this thread's first entry (i, j) of the m x m update, fixed for the solve
+    const int fi = t / (m > 0 ? m : 1), fj = t - fi * (m > 0 ? m : 1);
     if (m >= 2) {
         for (int sweep = 0; sweep < max_sweeps; ++sweep) {
             int need = 0;
@@ -140,14 +142,15 @@ __device__ EigBufs block_jacobi(float* A, float* V, float* A2, float* V2, int* p
                     const int pi = rr_partner(t, round, m);
                     float ci, si;
                     rot = pair_rotation(A, ld, t, pi, tol, ci, si, n > 24);
-                    pc[t] = pi;
                     cs[2 * t] = ci;
                     cs[2 * t + 1] = si;
                 }
                 if (!__syncthreads_or(rot)) continue;
+                // the partners come from the round-robin formula, not from pc[], so
+                // the loads below do not wait on another shared-memory load
                 for (int idx = t; idx < m * m; idx += nt) {
-                    const int i = idx / m, j = idx % m;
-                    const int pi = pc[i], pj = pc[j];
+                    const int i = idx < nt ? fi : idx / m, j = idx < nt ? fj : idx % m;
+                    const int pi = rr_partner(i, round, m), pj = rr_partner(j, round, m);
                     const float ci = cs[2 * i], si = cs[2 * i + 1], cj = cs[2 * j], sj = cs[2 * j + 1];
                     const float t1 = __fmul_rn(__fmul_rn(ci, cj), A[i * ld + j]);
                     const float t2 = __fmul_rn(__fmul_rn(ci, sj), A[i * ld + pj]);
@@ -569,10 +572,12 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
         // (not near-orthonormal: the general path below)
     }
 
+    // both global inputs at once: M in the W basis (G_n Vrot^T, summed over
+    // regions by the finalize kernel) and (U W)[:, s:] from the last SVT
+    if (s > 0) copy_cols(m.Mred, Rp, 0, s, I, Pw, LD);
+    if (q > 0) copy_cols(m.Urot, Rp, s, q, I, Bw, LD);
+    __syncthreads();
     if (s > 0) {
-        // M in the W basis: G_n Vrot^T, summed over regions by the finalize kernel
-        copy_cols(m.Mred, Rp, 0, s, I, Pw, LD);
-        __syncthreads();
         // B1 = M^T M, Z1 = B1^{-1/2}, P1 = M Z1
         tile_AtB(Pw, LD, s, Pw, LD, s, I, jb.A, ld, true, tsc);
         const EigBufs eb = sym_eig_orth(jb, s, ld, 1e-6f, 30, tsc);
@@ -583,9 +588,7 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
         __syncthreads();
     }
     if (q > 0) {
-        // (U W)[:, s:], from the SVT of the previous loop body (eye at k = 0)
-        copy_cols(m.Urot, Rp, s, q, I, Bw, LD);
-        __syncthreads();
+        // B = (U W)[:, s:] (eye at k = 0), less its part on the range of P1
         if (s > 0) {
             // K = P1^T Ur (s x q);  B = Ur - P1 K
             tile_AtB(Mw, LD, s, Bw, LD, q, I, K, ld, false, tsc);
