@@ -344,11 +344,11 @@ def _batched(P, torch, ctx, args):
     serial_plain = serial(0)
     serial_skip = serial(P.F_SKIP_IDLE)
 
-    def batch(precision):
+    def batch(precision, cx):
         plans, Ls, Es = [], [], []
         for q, sp in enumerate(specs):
-            plan, _ = P.pasd_plan(ctx, P.make_params(sp.dims, sp.rank_bounds, max_iter=1000,
-                                                     precision=precision, flags=P.F_SKIP_IDLE))
+            plan, _ = P.pasd_plan(cx, P.make_params(sp.dims, sp.rank_bounds, max_iter=1000,
+                                                    precision=precision, flags=P.F_SKIP_IDLE))
             L = torch.empty_like(Ts[q])
             E = torch.empty_like(Ts[q])
             P.pasd_solve(plan, Ts[q], L, E)          # allocation, graph capture, warm-up
@@ -357,31 +357,38 @@ def _batched(P, torch, ctx, args):
             Es.append(E)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pending = {P.pasd_submit(ctx, plans[q], Ts[q], Ls[q], Es[q]): q for q in range(len(specs))}
-        bad, iters, skipped = 0, [0] * len(specs), [0] * len(specs)
+        pending = {P.pasd_submit(cx, plans[q], Ts[q], Ls[q], Es[q]): q for q in range(len(specs))}
+        bad, iters, skipped, batched = 0, [0] * len(specs), [0] * len(specs), 0
         while pending:
             for tk in list(pending):
-                st, r = P.pasd_poll(ctx, tk)
+                st, r = P.pasd_poll(cx, tk)
                 if st != P.PENDING:
                     q = pending.pop(tk)
                     bad += st not in (P.OK, P.NOT_CONVERGED)
                     iters[q], skipped[q] = int(r.iters), int(r.skipped)
+                    batched += int(r.batched)
             time.sleep(0.0002)
         wall = time.perf_counter() - t0
         rse = [float(torch.linalg.vector_norm(Ls[q].double() - L0s[q]) / torch.linalg.vector_norm(L0s[q]))
                for q in range(len(specs))]
         for plan in plans:
             P.pasd_plan_destroy(plan)
-        return {"solves_per_s": round(len(specs) / wall, 1), "failed": bad,
+        return {"solves_per_s": round(len(specs) / wall, 1), "failed": bad, "in_batched_executor": batched,
                 "rse_median": float(np.median(rse)), "iters": sum(iters), "skipped": sum(skipped)}, Ls
 
-    fp32, l32 = batch(P.PREC_FP32)
-    mixed, lmx = batch(P.PREC_MIXED)
+    fp32, l32 = batch(P.PREC_FP32, ctx)
+    mixed, lmx = batch(P.PREC_MIXED, ctx)
+    # the same FP32 solves with every solve on a stream of its own (no batched executor)
+    os.environ["PASD_NO_BATCH"] = "1"
+    ctx_streams = P.pasd_ctx_create(torch.cuda.current_device())
+    del os.environ["PASD_NO_BATCH"]
+    fp32_streams, _ = batch(P.PREC_FP32, ctx_streams)
+    P.pasd_ctx_destroy(ctx_streams)
     mixed["L_rel_vs_fp32_max"] = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
                                      for a, b in zip(lmx, l32))
     return {"workload": "64 solves at once: 56 planted (sides U{32..160}, Tucker 3-15, 5-30%) + 8 hyperspectral "
                         "128x128x191 (salt and pepper), seed 3, idle-start skip",
-            "fp32": fp32, "mixed": mixed,
+            "fp32": fp32, "fp32_own_streams": fp32_streams, "mixed": mixed,
             "serial_plain_fp32_solves_per_s": round(serial_plain, 1),
             "serial_fp32_skip_solves_per_s": round(serial_skip, 1),
             "generation_s": round(gen_s, 1)}

@@ -112,6 +112,8 @@ typedef struct {
     int32_t skipped;                      /* loop bodies replaced by the idle-start
                                              closed form (PASD_F_SKIP_IDLE), included
                                              in iters                                  */
+    int32_t batched;                      /* served solves: 1 if it advanced in the
+                                             batched executor, 0 on a stream of its own */
 } pasd_result;
 
 typedef struct pasd_ctx pasd_ctx;
@@ -174,7 +176,15 @@ pasd_status pasd_solve_host(pasd_plan_t* plan, const float* T_host, float* L_hos
  * tensors T, L, E; the caller keeps them alive and untouched until pasd_poll
  * returns something other than PASD_PENDING. A solve is admitted when its
  * plan's footprint fits the context's HBM budget; admitted solves advance
- * together, each on its own stream, and retire as they converge. The solve's
+ * together and retire as they converge. Solves whose kernels all have batched
+ * forms (the FP32 path on bulk-copy kernels) join one batch: each loop body is
+ * one launch per kernel for all of them (grouped by the kernels' template
+ * parameters: rank bucket, tile threads, tensor order), replayed as one
+ * captured CUDA graph per body that is rebuilt when solves join or leave at
+ * the boundaries of 8-body chunks. The others (mixed precision, layouts on the
+ * fallback kernels) run each on a stream of its own. Results are the same bit
+ * for bit either way. PASD_NO_BATCH=1 (read by pasd_ctx_create) puts every
+ * served solve on its own stream. The solve's
  * stream is not ordered after any stream of the caller: T must be fully
  * written (its producing stream synchronised) before pasd_submit is called.
  * One plan serves one solve at a time (further submits of it wait in the

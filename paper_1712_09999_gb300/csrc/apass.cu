@@ -426,18 +426,17 @@ template <int RP> struct AtShape {
 };
 
 template <int RP, int NC>
-__global__ void __launch_bounds__(AP_BN / NC) apass_tma_kernel(const __grid_constant__ ApassTmaMaps maps,
-                                                               const ApassTmaArgs aa) {
+__device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const ApassTmaArgs& aa, const int block) {
     extern __shared__ __align__(16) float sm_raw[];
     float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 511) & ~uintptr_t(511));
     __shared__ __align__(8) uint64_t full[AT_STAGES];
     int k = 0;
-    while (k + 1 < aa.count && (int)blockIdx.x >= aa.cta_start[k + 1]) ++k;
+    while (k + 1 < aa.count && (int)block >= aa.cta_start[k + 1]) ++k;
     const ApassTmaMode& m = aa.m[k];
     DevScalars* sc = aa.sc;
     constexpr int NT = AP_BN / NC;
     if (sc->done) return;
-    const int task = blockIdx.x - aa.cta_start[k];
+    const int task = block - aa.cta_start[k];
     const int t = threadIdx.x;
     const int64_t I = m.I, post = m.post;
     const int BN = m.BN;
@@ -586,6 +585,34 @@ __global__ void __launch_bounds__(AP_BN / NC) apass_tma_kernel(const __grid_cons
         }
     }
     gram_epilogue<RP, NT, NC>(acc, smem, m.gram_part + (size_t)task * RP * RP);
+}
+
+template <int RP, int NC>
+__global__ void __launch_bounds__(AP_BN / NC) apass_tma_kernel(const __grid_constant__ ApassTmaMaps maps,
+                                                               const ApassTmaArgs aa) {
+    apass_tma_body<RP, NC>(maps, aa, blockIdx.x);
+}
+
+// Batched: CTAs [start, start + tasks) of an entry run one solve's A-pass group
+// (modes with one padded rank); maps from global memory, arguments from shared.
+struct ApassBatchEntry {
+    ApassTmaMaps maps;
+    ApassTmaArgs args;
+    int start;
+};
+template <int RP, int NC>
+__global__ void __launch_bounds__(AP_BN / NC) apass_tma_kernel_batched(const ApassBatchEntry* e, const int* block_entry) {
+    const ApassBatchEntry& x = e[block_entry[blockIdx.x]];
+    __shared__ __align__(16) ApassTmaArgs s_aa;
+    load_args_to_smem(&s_aa, &x.args);
+    const int block = blockIdx.x - x.start;
+    if (threadIdx.x == 0) {
+        int k = 0;
+        while (k + 1 < s_aa.count && block >= s_aa.cta_start[k + 1]) ++k;
+        tensormap_acquire(&x.maps.g[k]);
+        tensormap_acquire(&x.maps.u[k]);
+    }
+    apass_tma_body<RP, NC>(x.maps, s_aa, block);
 }
 
 // ---------------------------------------------------------------------------
@@ -1046,6 +1073,53 @@ ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, in
     p->smem = smem;
     p->nc = p->args.Rp <= 40 ? 4 : 2;
     return p;
+}
+
+size_t apass_batch_entry_bytes() { return sizeof(ApassBatchEntry); }
+int apass_batch_rp(const ApassTmaPlan* p) { return p->args.Rp; }
+int apass_batch_ctas(const ApassTmaPlan* p) { return p->kind == APASS_FFMA ? p->args.cta_start[p->args.count] : -1; }
+size_t apass_batch_smem(const ApassTmaPlan* p) { return p->smem; }
+void apass_batch_fill(void* entry, const ApassTmaPlan* p, int start) {
+    // built in an aligned local and copied: `entry` points into a byte staging
+    // buffer that need not meet the tensor maps' 64-byte alignment
+    ApassBatchEntry e;
+    std::memset(&e, 0, sizeof(e));
+    e.maps = p->maps;
+    e.args = p->args;
+    e.start = start;
+    std::memcpy(entry, &e, sizeof(e));
+}
+template <int RP, int NC>
+static void launch_batched_rp_nc(const void* entries, const int* block_entry, int grid, size_t smem, cudaStream_t s) {
+    set_smem_attr((const void*)apass_tma_kernel_batched<RP, NC>, (int)smem);
+    apass_tma_kernel_batched<RP, NC><<<grid, AP_BN / NC, smem, s>>>(static_cast<const ApassBatchEntry*>(entries),
+                                                                   block_entry);
+}
+template <int RP>
+static void launch_batched_rp(int nc, const void* entries, const int* block_entry, int grid, size_t smem,
+                              cudaStream_t s) {
+    constexpr int C = AtShape<RP>::COLS;
+    if (nc == C) launch_batched_rp_nc<RP, C>(entries, block_entry, grid, smem, s);
+    else launch_batched_rp_nc<RP, C / 2>(entries, block_entry, grid, smem, s);
+}
+// every entry of one launch has padded rank Rp and nc columns per thread
+void launch_apass_batched(int Rp, int nc, const void* entries, const int* block_entry, int grid, size_t smem,
+                          cudaStream_t s) {
+    switch (Rp) {
+        case 4: launch_batched_rp<4>(nc, entries, block_entry, grid, smem, s); break;
+        case 8: launch_batched_rp<8>(nc, entries, block_entry, grid, smem, s); break;
+        case 12: launch_batched_rp<12>(nc, entries, block_entry, grid, smem, s); break;
+        case 16: launch_batched_rp<16>(nc, entries, block_entry, grid, smem, s); break;
+        case 20: launch_batched_rp<20>(nc, entries, block_entry, grid, smem, s); break;
+        case 24: launch_batched_rp<24>(nc, entries, block_entry, grid, smem, s); break;
+        case 28: launch_batched_rp<28>(nc, entries, block_entry, grid, smem, s); break;
+        case 32: launch_batched_rp<32>(nc, entries, block_entry, grid, smem, s); break;
+        case 40: launch_batched_rp<40>(nc, entries, block_entry, grid, smem, s); break;
+        case 48: launch_batched_rp<48>(nc, entries, block_entry, grid, smem, s); break;
+        case 56: launch_batched_rp<56>(nc, entries, block_entry, grid, smem, s); break;
+        case 64: launch_batched_rp<64>(nc, entries, block_entry, grid, smem, s); break;
+        default: break;
+    }
 }
 
 int apass_tma_cols(const ApassTmaPlan* p) { return p->kind == APASS_FFMA ? p->nc : 0; }

@@ -4,6 +4,7 @@
 #include "../../include/pasd.h"
 #include "pasd_impl.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -80,6 +81,9 @@ struct pasd_ctx {
     bool stop = false;
     uint64_t next_ticket = 1;
     size_t max_queue = 4096;
+    bool no_batch = false;    // PASD_NO_BATCH=1 at creation: every served solve on its own stream
+    int n_batches = 4;        // batches of the served path (PASD_BATCHES, 1..16)
+    int batch_chunk = 8;      // loop bodies between a batch's flag reads (PASD_BATCH_CHUNK, 1..64)
 };
 
 struct pasd_plan {
@@ -197,6 +201,15 @@ extern "C" pasd_status pasd_ctx_create(int device, size_t hbm_budget_bytes, pasd
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     c->hbm_budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+    if (const char* nb = std::getenv("PASD_NO_BATCH")) c->no_batch = nb[0] == '1';
+    if (const char* q = std::getenv("PASD_BATCHES")) {
+        const long v = std::strtol(q, nullptr, 10);
+        if (v >= 1 && v <= 16) c->n_batches = (int)v;
+    }
+    if (const char* q = std::getenv("PASD_BATCH_CHUNK")) {
+        const long v = std::strtol(q, nullptr, 10);
+        if (v >= 1 && v <= 64) c->batch_chunk = (int)v;
+    }
     if (const char* q = std::getenv("PASD_MAX_QUEUE")) {
         const long v = std::strtol(q, nullptr, 10);
         if (v >= 1) c->max_queue = (size_t)v;
@@ -1313,23 +1326,258 @@ extern "C" pasd_status pasd_state_get(pasd_plan_t* pl, int32_t item, int32_t mod
 // ---------------------------------------------------------------------------
 // served path: continuous batching over per-solve streams
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// batched executor: the served path advances its batchable solves together, one
+// launch per kernel of a loop body (grouped by the kernels' template
+// parameters) for all of them, replayed as one captured graph per body
+// ---------------------------------------------------------------------------
+// A plan can join a batch when all its streaming kernels are the bulk-copy FP32
+// ones that have batched forms (few-row modes run as their own launches).
+static bool batchable(const pasd_plan_t* pl) {
+    if (!pl->arena || !pl->tma || pl->n_ap_plain > 0) return false;
+    for (int q = 0; q < pl->n_ap_tma; ++q)
+        if (apass_batch_ctas(pl->ap_tma[q]) < 0) return false;
+    return true;
+}
+
+struct BatchLaunch {
+    int k1 = 0, k2 = 0;          // A-pass: Rp, columns per thread; Vrot: RB, four-column path; fused: N, threads
+    size_t ent = 0, map = 0;     // byte offsets of the entries and of the CTA -> entry map
+    int grid = 0;
+    size_t smem = 0;
+};
+
+struct BatchExec {
+    std::vector<pasd_plan_t*> members;
+    std::vector<char> host;      // staging of the device tables
+    char* dev = nullptr;
+    size_t dev_bytes = 0;
+    size_t small_ent = 0;
+    int n_small = 0;
+    size_t polar_smem = 0, svt_smem = 0;
+    std::vector<BatchLaunch> apass, vrot, fused, mpass, mplain, fin;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int num_sms = 0;
+};
+
+static size_t stage_bytes(std::vector<char>& h, size_t bytes, size_t align = 256) {
+    size_t off = (h.size() + align - 1) / align * align;
+    h.resize(off + bytes);
+    return off;
+}
+
+// Groups entries by key; for each group lays out [entries][CTA -> entry map].
+template <class Key, class Item>
+static void layout_groups(BatchExec& b, std::vector<BatchLaunch>& out, const std::map<Key, std::vector<Item>>& groups,
+                          size_t entry_bytes, int (*ctas)(const Item&), void (*fill)(void*, const Item&, int),
+                          size_t (*smem)(const Item&), void (*keys)(const Key&, BatchLaunch&)) {
+    out.clear();
+    for (const auto& kv : groups) {
+        BatchLaunch L;
+        keys(kv.first, L);
+        const size_t ent = stage_bytes(b.host, entry_bytes * kv.second.size(), 256);
+        int start = 0;
+        std::vector<int> owner;
+        for (size_t e = 0; e < kv.second.size(); ++e) {
+            const Item& it = kv.second[e];
+            const int c = ctas(it);
+            fill(b.host.data() + ent + e * entry_bytes, it, start);
+            for (int q = 0; q < c; ++q) owner.push_back((int)e);
+            start += c;
+            L.smem = std::max(L.smem, smem(it));
+        }
+        if (start == 0) continue;
+        const size_t map = stage_bytes(b.host, owner.size() * sizeof(int), 256);
+        std::memcpy(b.host.data() + map, owner.data(), owner.size() * sizeof(int));
+        L.ent = ent;
+        L.map = map;
+        L.grid = start;
+        out.push_back(L);
+    }
+}
+
+struct ApItem { const ApassTmaPlan* p; };
+struct VrItem { const pasd_plan_t* pl; };
+struct FuItem { const FusedTmaPlan* p; };
+struct MpItem { const MpassTmaPlan* p; };
+struct MqItem { const pasd_plan_t* pl; };
+struct FiItem { const pasd_plan_t* pl; };
+
+static void launch_batch_body(BatchExec& b, cudaStream_t s) {
+    const char* d = b.dev;
+    auto ent = [&](size_t off) { return static_cast<const void*>(d + off); };
+    auto map = [&](size_t off) { return reinterpret_cast<const int*>(d + off); };
+    launch_polar_batched(reinterpret_cast<const SmallBatchEntry*>(d + b.small_ent), b.n_small, b.polar_smem, s);
+    for (const BatchLaunch& L : b.apass) launch_apass_batched(L.k1, L.k2, ent(L.ent), map(L.map), L.grid, L.smem, s);
+    for (pasd_plan_t* pl : b.members)
+        for (int n = 0; n < pl->N; ++n)
+            if (pl->ap_small[n]) launch_apass_small(pl->ap[n], pl->ap_small_grid[n], s);
+    launch_svt_batched(reinterpret_cast<const SmallBatchEntry*>(d + b.small_ent), b.n_small, b.svt_smem, s);
+    for (const BatchLaunch& L : b.vrot)
+        launch_vrot_batched(L.k1, L.k2 != 0, reinterpret_cast<const VrotBatchEntry*>(d + L.ent), map(L.map), L.grid, s);
+    for (const BatchLaunch& L : b.fused) launch_fused_batched(L.k1, ent(L.ent), map(L.map), L.grid, L.k2, L.smem, s);
+    for (pasd_plan_t* pl : b.members)
+        for (int n = 0; n < pl->N; ++n)
+            if (pl->ap_small[n]) launch_mpass_small(pl->mp_small[n], pl->ap_small_grid[n], s);
+    for (const BatchLaunch& L : b.mpass) launch_mpass_batched(ent(L.ent), map(L.map), L.grid, L.smem, s);
+    for (const BatchLaunch& L : b.mplain)
+        launch_mpass_plain_batched(reinterpret_cast<const MpassPlainBatchEntry*>(d + L.ent), map(L.map), L.grid, L.smem,
+                                   s);
+    for (const BatchLaunch& L : b.fin)
+        launch_finalize_batched(reinterpret_cast<const FinBatchEntry*>(d + L.ent), map(L.map), L.grid, s);
+}
+
+static void batch_release(BatchExec& b) {
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    if (b.graph) cudaGraphDestroy(b.graph);
+    b.exec = nullptr;
+    b.graph = nullptr;
+}
+
+// Rebuilds the device tables and the body graph for the current members.
+static bool batch_build(BatchExec& b, cudaStream_t s) {
+    batch_release(b);
+    b.host.clear();
+    if (b.members.empty()) return true;
+    // polar / SVT: one CTA per (solve, mode)
+    {
+        std::vector<SmallBatchEntry> e;
+        b.polar_smem = b.svt_smem = 0;
+        for (pasd_plan_t* pl : b.members) {
+            for (int n = 0; n < pl->N; ++n) e.push_back(SmallBatchEntry{pl->small.m[n], pl->sc, n});
+            b.polar_smem = std::max(b.polar_smem, polar_launch_smem(pl->small));
+            b.svt_smem = std::max(b.svt_smem, svt_launch_smem(pl->small));
+        }
+        b.n_small = (int)e.size();
+        b.small_ent = stage_bytes(b.host, e.size() * sizeof(SmallBatchEntry));
+        std::memcpy(b.host.data() + b.small_ent, e.data(), e.size() * sizeof(SmallBatchEntry));
+    }
+    std::map<std::pair<int, int>, std::vector<ApItem>> ap;
+    std::map<std::pair<int, int>, std::vector<VrItem>> vr;
+    std::map<std::pair<int, int>, std::vector<FuItem>> fu;
+    std::map<int, std::vector<MpItem>> mp;
+    std::map<int, std::vector<MqItem>> mq;
+    std::map<int, std::vector<FiItem>> fi;
+    for (pasd_plan_t* pl : b.members) {
+        for (int q = 0; q < pl->n_ap_tma; ++q)
+            ap[{apass_batch_rp(pl->ap_tma[q]), apass_tma_cols(pl->ap_tma[q])}].push_back(ApItem{pl->ap_tma[q]});
+        vr[{vrot_launch_rb(pl->vr), vrot_launch_v4(pl->vr) ? 1 : 0}].push_back(VrItem{pl});
+        fu[{fused_batch_order(pl->tma), fused_batch_threads(pl->tma)}].push_back(FuItem{pl->tma});
+        if (pl->n_mp_big > 0) {
+            if (pl->mp_tma) mp[0].push_back(MpItem{pl->mp_tma});
+            else mq[0].push_back(MqItem{pl});
+        }
+        fi[0].push_back(FiItem{pl});
+    }
+    auto pair_keys = [](const std::pair<int, int>& k, BatchLaunch& L) { L.k1 = k.first; L.k2 = k.second; };
+    layout_groups<std::pair<int, int>, ApItem>(
+        b, b.apass, ap, apass_batch_entry_bytes(), [](const ApItem& i) { return apass_batch_ctas(i.p); },
+        [](void* e, const ApItem& i, int st) { apass_batch_fill(e, i.p, st); },
+        [](const ApItem& i) { return apass_batch_smem(i.p); }, pair_keys);
+    layout_groups<std::pair<int, int>, VrItem>(
+        b, b.vrot, vr, sizeof(VrotBatchEntry), [](const VrItem& i) { return i.pl->vr.cta_start[i.pl->N]; },
+        [](void* e, const VrItem& i, int st) {
+            VrotBatchEntry v{i.pl->vr, st};
+            std::memcpy(e, &v, sizeof(v));
+        },
+        [](const VrItem&) { return (size_t)0; }, pair_keys);
+    layout_groups<std::pair<int, int>, FuItem>(
+        b, b.fused, fu, fused_batch_entry_bytes(), [](const FuItem& i) { return fused_batch_ctas(i.p); },
+        [](void* e, const FuItem& i, int st) { fused_batch_fill(e, i.p, st); },
+        [](const FuItem& i) { return fused_batch_smem(i.p); }, pair_keys);
+    layout_groups<int, MpItem>(
+        b, b.mpass, mp, mpass_batch_entry_bytes(), [](const MpItem& i) { return mpass_batch_ctas(i.p); },
+        [](void* e, const MpItem& i, int st) { mpass_batch_fill(e, i.p, st); },
+        [](const MpItem& i) { return mpass_batch_smem(i.p); }, [](const int&, BatchLaunch&) {});
+    layout_groups<int, MqItem>(
+        b, b.mplain, mq, sizeof(MpassPlainBatchEntry), [](const MqItem& i) { return i.pl->mpa.cta_start[i.pl->N]; },
+        [](void* e, const MqItem& i, int st) {
+            MpassPlainBatchEntry m{i.pl->mpa, st};
+            std::memcpy(e, &m, sizeof(m));
+        },
+        [](const MqItem& i) { return i.pl->mp_smem; }, [](const int&, BatchLaunch&) {});
+    layout_groups<int, FiItem>(
+        b, b.fin, fi, sizeof(FinBatchEntry), [](const FiItem& i) { return finalize_ctas(i.pl->fin); },
+        [](void* e, const FiItem& i, int st) {
+            FinBatchEntry f{i.pl->fin, st};
+            std::memcpy(e, &f, sizeof(f));
+        },
+        [](const FiItem&) { return (size_t)0; }, [](const int&, BatchLaunch&) {});
+    if (b.host.size() > b.dev_bytes) {
+        if (b.dev) cudaFree(b.dev);
+        b.dev = nullptr;
+        b.dev_bytes = 0;
+        if (cudaMalloc(&b.dev, b.host.size()) != cudaSuccess) return false;
+        b.dev_bytes = b.host.size();
+    }
+    if (cudaMemcpyAsync(b.dev, b.host.data(), b.host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) return false;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return false;
+    launch_batch_body(b, s);
+    if (cudaStreamEndCapture(s, &b.graph) != cudaSuccess) return false;
+    return cudaGraphInstantiate(&b.exec, b.graph, 0) == cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// served path: continuous batching (one batch of the batchable solves on one
+// stream, the others on a stream each)
+// ---------------------------------------------------------------------------
 struct Active {
     Job job;
     size_t footprint = 0;    // the plan's, taken at admission: once a result is
                              // published the caller may destroy the plan
     int launched = 0;
     bool flag_pending = false;
+    bool started = false;
+    bool batched = false;
+    int batch = 0;           // which batch, when batched
+    bool in_chunk = false;   // part of its batch's chunk in flight
+};
+
+static void publish(pasd_ctx* c, Active& a, pasd_result r) {
+    r.latency_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - a.job.t_submit).count();
+    r.batched = a.batched ? 1 : 0;
+    pasd_plan_t* pl = a.job.plan;
+    std::unique_lock<std::mutex> lk(c->mu);
+    c->done[a.job.ticket] = r;
+    c->state.erase(a.job.ticket);
+    pl->busy = false;
+    --pl->served;
+    a.launched = -1;
+}
+
+// One batch of the served path: its members advance together on its stream, a
+// chunk of loop bodies at a time; the tables are rebuilt (between chunks, with the
+// stream idle) when members join or leave.
+struct SubBatch {
+    BatchExec b;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;        // a chunk is in flight
+    bool rebuild = false;
+    int size() const { return (int)b.members.size(); }
 };
 
 static void worker_main(pasd_ctx* c) {
     cudaSetDevice(c->device);
     std::vector<Active> active;
     size_t in_use = 0;
+    const bool use_batch = !c->no_batch;
+    // A few batches on streams of their own: one batch would serialise the loop
+    // body's phases, leaving the GPU to the one-CTA-per-mode kernels of all solves
+    // at once; batches on separate streams overlap one's small kernels with
+    // another's streaming passes, and the host waits on none of them.
+    constexpr int kMaxBatches = 16;
+    const int kBatches = c->n_batches;
+    const int kBatchChunk = c->batch_chunk;
+    SubBatch subs[kMaxBatches];
     for (;;) {
         // admission
         {
             std::unique_lock<std::mutex> lk(c->mu);
-            if (active.empty() && c->queue.empty()) {
+            bool idle = active.empty();
+            if (idle && c->queue.empty()) {
                 if (c->stop) break;
                 c->cv.wait_for(lk, std::chrono::milliseconds(2));
                 if (c->stop && c->queue.empty()) break;
@@ -1351,28 +1599,87 @@ static void worker_main(pasd_ctx* c) {
                 }
             }
         }
-        // start newly admitted solves
+        // start newly admitted solves: into the smallest batch when their kernels allow it
         for (auto& a : active) {
+            if (a.started || a.launched < 0) continue;
+            a.started = true;
             pasd_plan_t* pl = a.job.plan;
-            if (a.launched == 0 && !a.flag_pending) {
-                if (!pl->own_stream) cudaStreamCreateWithFlags(&pl->own_stream, cudaStreamNonBlocking);
-                pasd_status st = begin_impl(pl, a.job.T, pl->own_stream);
-                if (st != PASD_OK) {
-                    pasd_result r{};
-                    r.status = st;
-                    std::unique_lock<std::mutex> lk(c->mu);
-                    c->done[a.job.ticket] = r;
-                    c->state.erase(a.job.ticket);
-                    pl->busy = false;
-                    --pl->served;
-                    a.launched = -1;
+            pasd_status st = ensure_allocated(pl);
+            cudaStream_t s = nullptr;
+            if (st == PASD_OK) {
+                a.batched = use_batch && batchable(pl);
+                if (a.batched) {
+                    int j = 0;
+                    for (int q = 1; q < kBatches; ++q)
+                        if (subs[q].size() < subs[j].size()) j = q;
+                    SubBatch& sb = subs[j];
+                    if (!sb.s) {
+                        cudaStreamCreateWithFlags(&sb.s, cudaStreamNonBlocking);
+                        cudaEventCreateWithFlags(&sb.ev, cudaEventDisableTiming);
+                    }
+                    a.batch = j;
+                    s = sb.s;
+                } else {
+                    if (!pl->own_stream) cudaStreamCreateWithFlags(&pl->own_stream, cudaStreamNonBlocking);
+                    s = pl->own_stream;
+                }
+                st = begin_impl(pl, a.job.T, s);   // after the batch's chunk in flight, if any
+            }
+            if (st != PASD_OK) {
+                pasd_result r{};
+                r.status = st;
+                publish(c, a, r);
+                continue;
+            }
+            if (a.batched) {
+                subs[a.batch].b.members.push_back(pl);
+                subs[a.batch].rebuild = true;
+            }
+        }
+        bool progressed = false;
+        // batches whose stream is idle: rebuild if needed, then the next chunk
+        for (int j = 0; j < kBatches; ++j) {
+            SubBatch& sb = subs[j];
+            if (sb.pending || sb.b.members.empty()) continue;
+            if (sb.rebuild) {
+                sb.rebuild = false;
+                if (!batch_build(sb.b, sb.s)) {
+                    // no tables: the members continue on streams of their own
+                    cudaStreamSynchronize(sb.s);
+                    for (auto& a : active)
+                        if (a.batched && a.batch == j && a.launched >= 0) {
+                            a.batched = false;
+                            pasd_plan_t* pl = a.job.plan;
+                            if (!pl->own_stream) cudaStreamCreateWithFlags(&pl->own_stream, cudaStreamNonBlocking);
+                        }
+                    sb.b.members.clear();
+                    batch_release(sb.b);
                     continue;
                 }
             }
+            for (int i = 0; i < kBatchChunk; ++i) {
+                cudaGraphLaunch(sb.b.exec, sb.s);
+                if (i == 0)
+                    for (pasd_plan_t* pl : sb.b.members)
+                        if (pl->skip_pending) {
+                            // first body after pasd_begin: replace the provably idle bodies that follow
+                            launch_idle_skip(pl->idle, pl->ctx->num_sms, sb.s);
+                            pl->skip_pending = false;
+                        }
+            }
+            for (pasd_plan_t* pl : sb.b.members)
+                cudaMemcpyAsync(pl->host_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, sb.s);
+            cudaEventRecord(sb.ev, sb.s);
+            sb.pending = true;
+            for (auto& a : active)
+                if (a.batched && a.batch == j && a.launched >= 0) {
+                    a.launched += kBatchChunk;
+                    a.in_chunk = true;
+                }
         }
-        // advance every active solve by one chunk, one stream each
+        // the others: one chunk each, on their own streams
         for (auto& a : active) {
-            if (a.launched < 0 || a.flag_pending) continue;
+            if (a.launched < 0 || a.batched || a.flag_pending) continue;
             pasd_plan_t* pl = a.job.plan;
             int n = std::min(pl->p.check_every, pl->p.max_iter - a.launched);
             if (n > 0) {
@@ -1383,10 +1690,31 @@ static void worker_main(pasd_ctx* c) {
             cudaEventRecord(pl->ev, pl->own_stream);
             a.flag_pending = true;
         }
-        // retire finished ones
-        bool progressed = false;
+        // retire finished batch members once their batch's chunk has completed
+        for (int j = 0; j < kBatches; ++j) {
+            SubBatch& sb = subs[j];
+            if (!sb.pending || cudaEventQuery(sb.ev) != cudaSuccess) continue;
+            sb.pending = false;
+            progressed = true;
+            for (auto& a : active) {
+                // only the members of the completed chunk have fresh flags (a solve
+                // that joined meanwhile has not run a body yet)
+                if (!a.batched || a.batch != j || a.launched < 0 || !a.in_chunk) continue;
+                a.in_chunk = false;
+                pasd_plan_t* pl = a.job.plan;
+                if (pl->host_sc->done || a.launched >= pl->p.max_iter) {
+                    pasd_result r{};
+                    r.status = finish_impl(pl, a.job.L, a.job.E, &r, sb.s);
+                    auto it = std::find(sb.b.members.begin(), sb.b.members.end(), pl);
+                    if (it != sb.b.members.end()) sb.b.members.erase(it);
+                    sb.rebuild = true;
+                    publish(c, a, r);
+                }
+            }
+        }
+        // retire finished solo solves
         for (auto& a : active) {
-            if (a.launched < 0) continue;
+            if (a.launched < 0 || a.batched) continue;
             pasd_plan_t* pl = a.job.plan;
             if (!a.flag_pending) continue;
             if (cudaEventQuery(pl->ev) != cudaSuccess) continue;
@@ -1394,16 +1722,8 @@ static void worker_main(pasd_ctx* c) {
             progressed = true;
             if (pl->host_sc->done || a.launched >= pl->p.max_iter) {
                 pasd_result r{};
-                pasd_status st = finish_impl(pl, a.job.L, a.job.E, &r, pl->own_stream);
-                r.status = st;
-                r.latency_s = std::chrono::duration<double>(std::chrono::steady_clock::now() -
-                                                            a.job.t_submit).count();
-                std::unique_lock<std::mutex> lk(c->mu);
-                c->done[a.job.ticket] = r;
-                c->state.erase(a.job.ticket);
-                pl->busy = false;
-                --pl->served;
-                a.launched = -1;
+                r.status = finish_impl(pl, a.job.L, a.job.E, &r, pl->own_stream);
+                publish(c, a, r);
             }
         }
         for (auto it = active.begin(); it != active.end();) {
@@ -1415,6 +1735,13 @@ static void worker_main(pasd_ctx* c) {
             }
         }
         if (!progressed && !active.empty()) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    for (SubBatch& sb : subs) {
+        if (sb.s) cudaStreamSynchronize(sb.s);
+        batch_release(sb.b);
+        if (sb.b.dev) cudaFree(sb.b.dev);
+        if (sb.ev) cudaEventDestroy(sb.ev);
+        if (sb.s) cudaStreamDestroy(sb.s);
     }
 }
 

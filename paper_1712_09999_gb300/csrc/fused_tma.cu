@@ -58,9 +58,8 @@ struct FusedTmaPlan {
 // columns of Urot (one tensor map per height). The next U-step's product
 // G_n' Vrot^T is formed by the M-pass that follows.
 template <int N>
-__global__ void __launch_bounds__(FU_THREADS, 1)
-    fused_tma_kernel(const __grid_constant__ FusedTmaMaps tm, const FusedArgs fa, const int output,
-                     float* const Lout) {
+__device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const FusedArgs& fa, const int output,
+                                               float* const Lout, const int block) {
     DevScalars* sc = fa.sc;
     if (!output && sc->done) return;
     const FusedGeom& g = fa.g;
@@ -83,7 +82,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
 
     int q[N];
     {
-        int r = blockIdx.x;
+        int r = block;
         for (int n = N - 1; n >= 0; --n) { q[n] = r % g.Q[n]; r /= g.Q[n]; }
     }
     int64_t ts[N], te[N];
@@ -416,13 +415,44 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
 #pragma unroll
             for (int n = 0; n < N; ++n) s2[n] += wred[w][3 + n];
         }
-        float* p = fa.part + (size_t)blockIdx.x * fa.part_stride;
+        float* p = fa.part + (size_t)block * fa.part_stride;
         p[0] = mx;
         p[1] = s1;
         p[2] = nfs;
 #pragma unroll
         for (int n = 0; n < N; ++n) p[3 + n] = s2[n];
     }
+}
+
+template <int N>
+__global__ void __launch_bounds__(FU_THREADS, 1)
+    fused_tma_kernel(const __grid_constant__ FusedTmaMaps tm, const FusedArgs fa, const int output,
+                     float* const Lout) {
+    fused_tma_body<N>(tm, fa, output, Lout, blockIdx.x);
+}
+
+// Batched: the CTAs [start, start + nregions) of an entry run that solve's
+// regions; its maps are read from global memory, its arguments from shared.
+struct FusedBatchEntry {
+    FusedTmaMaps maps;
+    FusedArgs args;
+    int start;
+};
+template <int N>
+__global__ void __launch_bounds__(FU_THREADS, 1)
+    fused_tma_kernel_batched(const FusedBatchEntry* e, const int* block_entry) {
+    const FusedBatchEntry& x = e[block_entry[blockIdx.x]];
+    __shared__ __align__(16) FusedArgs s_fa;
+    load_args_to_smem(&s_fa, &x.args);
+    if (s_fa.sc->done) return;
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < N + 2; ++a) tensormap_acquire(&x.maps.tm_x[a]);
+        for (int n = 0; n < N; ++n) {
+            const int sp = (s_fa.sc->kept[n] + 3) & ~3;
+            if (sp) { tensormap_acquire(&x.maps.tm_a[n][sp / 4 - 1]); tensormap_acquire(&x.maps.tm_w[n][sp / 4 - 1]); }
+        }
+    }
+    fused_tma_body<N>(x.maps, s_fa, 0, nullptr, blockIdx.x - x.start);
 }
 
 // ---------------------------------------------------------------------------
@@ -528,6 +558,37 @@ static void launch_tma_n(FusedTmaPlan* p, int output, float* L, cudaStream_t s) 
     size_t smem = (size_t)g.smem_floats * 4 + 1024;
     set_smem_attr((const void*)fused_tma_kernel<N>, (int)smem);
     fused_tma_kernel<N><<<g.nregions, g.nthreads, smem, s>>>(p->maps, p->base, output, L);
+}
+
+size_t fused_batch_entry_bytes() { return sizeof(FusedBatchEntry); }
+int fused_batch_order(const FusedTmaPlan* p) { return p->base.g.N; }
+int fused_batch_ctas(const FusedTmaPlan* p) { return p->base.g.nregions; }
+int fused_batch_threads(const FusedTmaPlan* p) { return p->base.g.nthreads; }
+size_t fused_batch_smem(const FusedTmaPlan* p) { return (size_t)p->base.g.smem_floats * 4 + 1024; }
+void fused_batch_fill(void* entry, const FusedTmaPlan* p, int start) {
+    // built in an aligned local and copied: `entry` points into a byte staging
+    // buffer that need not meet the tensor maps' 64-byte alignment
+    FusedBatchEntry e;
+    std::memset(&e, 0, sizeof(e));
+    e.maps = p->maps;
+    e.args = p->base;
+    e.start = start;
+    std::memcpy(entry, &e, sizeof(e));
+}
+template <int N>
+static void launch_batched_n(const void* entries, const int* block_entry, int grid, int threads, size_t smem,
+                             cudaStream_t s) {
+    set_smem_attr((const void*)fused_tma_kernel_batched<N>, (int)smem);
+    fused_tma_kernel_batched<N><<<grid, threads, smem, s>>>(static_cast<const FusedBatchEntry*>(entries), block_entry);
+}
+void launch_fused_batched(int N, const void* entries, const int* block_entry, int grid, int threads, size_t smem,
+                          cudaStream_t s) {
+    switch (N) {
+        case 2: launch_batched_n<2>(entries, block_entry, grid, threads, smem, s); break;
+        case 3: launch_batched_n<3>(entries, block_entry, grid, threads, smem, s); break;
+        case 4: launch_batched_n<4>(entries, block_entry, grid, threads, smem, s); break;
+        default: break;
+    }
 }
 
 void launch_fused_tma(FusedTmaPlan* p, int output, float* L, cudaStream_t s) {

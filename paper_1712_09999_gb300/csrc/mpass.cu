@@ -255,16 +255,16 @@ __device__ __forceinline__ void mpass_body(const MpassMode& m, int s, int cta, f
     }
 }
 
-__global__ void __launch_bounds__(MP_THREADS) mpass_kernel(const MpassArgs ma) {
+__device__ __forceinline__ void mpass_body(const MpassArgs& ma, const int block) {
     extern __shared__ __align__(16) float smem[];
     const DevScalars* sc = ma.sc;
     if (sc->done) return;
     int k = 0;
-    while (k + 1 < ma.N && (int)blockIdx.x >= ma.cta_start[k + 1]) ++k;
+    while (k + 1 < ma.N && (int)block >= ma.cta_start[k + 1]) ++k;
     const MpassMode& m = ma.m[k];
     const int s = (sc->kept[k] + 3) & ~3;      // kept rows rounded up (Vrot rows past s_n are zero)
     if (s == 0) return;                        // no kept direction: the U-step does not read M_n
-    const int cta = blockIdx.x - ma.cta_start[k];
+    const int cta = block - ma.cta_start[k];
     switch (m.variant) {
         case 0: mpass_body<0>(m, s, cta, smem); break;
         case 1: mpass_body<1>(m, s, cta, smem); break;
@@ -273,12 +273,32 @@ __global__ void __launch_bounds__(MP_THREADS) mpass_kernel(const MpassArgs ma) {
     }
 }
 
+__global__ void __launch_bounds__(MP_THREADS) mpass_kernel(const MpassArgs ma) { mpass_body(ma, blockIdx.x); }
+
+// Batched: CTAs [start, start + ctas) of an entry run one solve's M-pass.
+__global__ void __launch_bounds__(MP_THREADS) mpass_kernel_batched(const MpassPlainBatchEntry* e,
+                                                                   const int* block_entry) {
+    const MpassPlainBatchEntry& x = e[block_entry[blockIdx.x]];
+    __shared__ __align__(16) MpassArgs s_ma;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&x.a);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&s_ma);
+    for (int w = threadIdx.x; w < (int)(sizeof(MpassArgs) / 4); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    mpass_body(s_ma, blockIdx.x - x.start);
+}
+
 int mpass_ctas_per_sm(size_t smem) {
     set_smem_attr((const void*)mpass_kernel, (int)smem);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mpass_kernel, MP_THREADS, smem) != cudaSuccess || n < 1)
         n = 1;
     return n;
+}
+
+void launch_mpass_plain_batched(const MpassPlainBatchEntry* e, const int* block_entry, int grid, size_t smem,
+                                cudaStream_t s) {
+    set_smem_attr((const void*)mpass_kernel_batched, (int)smem);
+    mpass_kernel_batched<<<grid, MP_THREADS, smem, s>>>(e, block_entry);
 }
 
 void launch_mpass(const MpassArgs& a, size_t smem, cudaStream_t s) {
@@ -315,19 +335,18 @@ static inline __host__ __device__ int mt_stage_floats(int IS, int Rp) {
     return mt_g_floats(IS) + (MP_CB * Rp + 8 + 255) / 256 * 256;
 }
 
-__global__ void __launch_bounds__(MP_THREADS) mpass_tma_kernel(const __grid_constant__ MpassTmaMaps maps,
-                                                               const MpassTmaArgs ma) {
+__device__ __forceinline__ void mpass_tma_body(const MpassTmaMaps& maps, const MpassTmaArgs& ma, const int block) {
     extern __shared__ __align__(16) float sm_raw[];
     float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t full[MT_STAGES];
     DevScalars* sc = ma.sc;
     if (sc->done) return;
     int k = 0;
-    while (k + 1 < ma.N && (int)blockIdx.x >= ma.cta_start[k + 1]) ++k;
+    while (k + 1 < ma.N && (int)block >= ma.cta_start[k + 1]) ++k;
     const MpassTmaMode& m = ma.m[k];
     const int s = (sc->kept[k] + 3) & ~3;      // kept rows rounded up (Vrot rows past s_n are zero)
     if (s == 0) return;                        // no kept direction: the U-step does not read M_n
-    const int cta = blockIdx.x - ma.cta_start[k];
+    const int cta = block - ma.cta_start[k];
     const int t = threadIdx.x;
     const int strip = cta % m.nstrips, rg = cta / m.nstrips;
     const int64_t I = m.I;
@@ -482,6 +501,31 @@ __global__ void __launch_bounds__(MP_THREADS) mpass_tma_kernel(const __grid_cons
     }
 }
 
+__global__ void __launch_bounds__(MP_THREADS) mpass_tma_kernel(const __grid_constant__ MpassTmaMaps maps,
+                                                               const MpassTmaArgs ma) {
+    mpass_tma_body(maps, ma, blockIdx.x);
+}
+
+// Batched: CTAs [start, start + ctas) of an entry run one solve's M-pass.
+struct MpassBatchEntry {
+    MpassTmaMaps maps;
+    MpassTmaArgs args;
+    int start;
+};
+__global__ void __launch_bounds__(MP_THREADS) mpass_tma_kernel_batched(const MpassBatchEntry* e, const int* block_entry) {
+    const MpassBatchEntry& x = e[block_entry[blockIdx.x]];
+    __shared__ __align__(16) MpassTmaArgs s_ma;
+    load_args_to_smem(&s_ma, &x.args);
+    const int block = blockIdx.x - x.start;
+    if (threadIdx.x == 0) {
+        int k = 0;
+        while (k + 1 < s_ma.N && block >= s_ma.cta_start[k + 1]) ++k;
+        tensormap_acquire(&x.maps.g[k]);
+        tensormap_acquire(&x.maps.v[k]);
+    }
+    mpass_tma_body(x.maps, s_ma, block);
+}
+
 bool mpass_tma_supported(int64_t I, int64_t post) {
     if (post == 1) return I % 4 == 0;
     return post % 4 == 0 && post >= MP_CB;
@@ -533,6 +577,24 @@ MpassTmaPlan* make_mpass_tma(const MpassTmaArgs& a, const float* const* G, const
         if (!ok) { delete p; return nullptr; }
     }
     return p;
+}
+
+size_t mpass_batch_entry_bytes() { return sizeof(MpassBatchEntry); }
+int mpass_batch_ctas(const MpassTmaPlan* p) { return p->args.cta_start[p->args.N]; }
+size_t mpass_batch_smem(const MpassTmaPlan* p) { return p->smem; }
+void mpass_batch_fill(void* entry, const MpassTmaPlan* p, int start) {
+    // built in an aligned local and copied: `entry` points into a byte staging
+    // buffer that need not meet the tensor maps' 64-byte alignment
+    MpassBatchEntry e;
+    std::memset(&e, 0, sizeof(e));
+    e.maps = p->maps;
+    e.args = p->args;
+    e.start = start;
+    std::memcpy(entry, &e, sizeof(e));
+}
+void launch_mpass_batched(const void* entries, const int* block_entry, int grid, size_t smem, cudaStream_t s) {
+    set_smem_attr((const void*)mpass_tma_kernel_batched, (int)smem);
+    mpass_tma_kernel_batched<<<grid, MP_THREADS, smem, s>>>(static_cast<const MpassBatchEntry*>(entries), block_entry);
 }
 
 void launch_mpass_tma(const MpassTmaPlan* p, cudaStream_t s) {

@@ -339,4 +339,62 @@ FusedTmaPlan* make_fused_tma(const FusedArgs& a, const float* T_copy, char* err,
 void destroy_fused_tma(FusedTmaPlan* p);
 void launch_fused_tma(FusedTmaPlan* p, int output, float* L, cudaStream_t s);
 
+// ----------------------------------------------------------------------------
+// Batched launches: one launch runs one kernel of a loop body for many solves.
+// Each entry holds one solve's arguments for that kernel (and, for the bulk-copy
+// kernels, its tensor maps, read from global memory); `block_entry` maps each
+// CTA of the batched grid to its entry, whose CTAs begin at `start`. An entry's
+// CTAs do exactly the work of that solve's own launch, so the results are the
+// same bit for bit.
+// ----------------------------------------------------------------------------
+struct SmallBatchEntry {        // polar and SVT: one CTA per (solve, mode)
+    SmallModeArgs m;
+    DevScalars* sc;
+    int mode;
+};
+struct FinBatchEntry {
+    FinalizeArgs a;
+    int start;
+};
+struct VrotBatchEntry {
+    VrotArgs a;
+    int start;
+};
+size_t polar_launch_smem(const SmallArgs& a);
+size_t svt_launch_smem(const SmallArgs& a);
+int finalize_ctas(const FinalizeArgs& a);
+int vrot_launch_rb(const VrotArgs& a);
+bool vrot_launch_v4(const VrotArgs& a);
+void launch_polar_batched(const SmallBatchEntry* e, int n, size_t smem, cudaStream_t s);
+void launch_svt_batched(const SmallBatchEntry* e, int n, size_t smem, cudaStream_t s);
+void launch_finalize_batched(const FinBatchEntry* e, const int* block_entry, int grid, cudaStream_t s);
+void launch_vrot_batched(int rb, bool v4, const VrotBatchEntry* e, const int* block_entry, int grid, cudaStream_t s);
+// bulk-copy kernels: entries are opaque here (filled by their files)
+size_t fused_batch_entry_bytes();
+int fused_batch_order(const FusedTmaPlan* p);
+int fused_batch_ctas(const FusedTmaPlan* p);
+int fused_batch_threads(const FusedTmaPlan* p);
+size_t fused_batch_smem(const FusedTmaPlan* p);
+void fused_batch_fill(void* entry, const FusedTmaPlan* p, int start);
+void launch_fused_batched(int N, const void* entries, const int* block_entry, int grid, int threads, size_t smem,
+                          cudaStream_t s);
+size_t apass_batch_entry_bytes();
+int apass_batch_rp(const ApassTmaPlan* p);
+int apass_batch_ctas(const ApassTmaPlan* p);     // -1: not an FMA plan (not batched)
+size_t apass_batch_smem(const ApassTmaPlan* p);
+void apass_batch_fill(void* entry, const ApassTmaPlan* p, int start);
+void launch_apass_batched(int Rp, int nc, const void* entries, const int* block_entry, int grid, size_t smem,
+                          cudaStream_t s);
+struct MpassPlainBatchEntry {   // the M-pass without bulk copies
+    MpassArgs a;
+    int start;
+};
+void launch_mpass_plain_batched(const MpassPlainBatchEntry* e, const int* block_entry, int grid, size_t smem,
+                                cudaStream_t s);
+size_t mpass_batch_entry_bytes();
+int mpass_batch_ctas(const MpassTmaPlan* p);
+size_t mpass_batch_smem(const MpassTmaPlan* p);
+void mpass_batch_fill(void* entry, const MpassTmaPlan* p, int start);
+void launch_mpass_batched(const void* entries, const int* block_entry, int grid, size_t smem, cudaStream_t s);
+
 }  // namespace pasd

@@ -403,11 +403,9 @@ __host__ __device__ inline int polar_ld(int Rp) { return ((Rp / 4) & 1) ? Rp : R
 // (also the scratch of the eigenvector re-orthonormalisation: TILE_SCRATCH floats)
 __host__ __device__ inline int svt_red_floats(int Rp) { return Rp * Rp > TILE_SCRATCH ? Rp * Rp : TILE_SCRATCH; }
 
-__global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
-    DevScalars* sc = sa.sc;
+__device__ __forceinline__ void svt_body(const SmallModeArgs& m, DevScalars* sc, const int mode) {
     if (sc->done) return;
     const double mu = sc->mu;
-    const SmallModeArgs& m = sa.m[blockIdx.x];
     const int R = m.R, Rp = m.Rp, ld = Rp;
     const int t = threadIdx.x;
     extern __shared__ __align__(16) float sm[];
@@ -483,7 +481,7 @@ __global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
     }
     // W exactly I (no rotation, order unchanged): Urot = U W below is an exact copy of U
     const int ident = !__syncthreads_or(moved);
-    if (t == 0) sc->w_ident[blockIdx.x] = ident;
+    if (t == 0) sc->w_ident[mode] = ident;
     if (t < 32) {
         double nuc = 0.0;
         int kept = 0;
@@ -498,8 +496,8 @@ __global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
         }
         if (t == 0) {
             *m.kept = kept;
-            sc->kept[blockIdx.x] = kept;
-            sc->nuclear[blockIdx.x] = nuc;
+            sc->kept[mode] = kept;
+            sc->nuclear[mode] = nuc;
         }
     }
     // 4. Urot = U W (I x Rp): the active subspace in the eigenbasis of the SVT.
@@ -507,6 +505,15 @@ __global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
     //    fold_n(U_n V_n) = Urot[:, :s] Vrot[:s], the refold of rank s.
     //    U's padding columns are zero, so the product runs over Rp.
     tile_AB(m.U, Rp, Rp, Smat, ld, Rp, m.I, m.Urot, Rp, false);
+}
+
+__global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
+    svt_body(sa.m[blockIdx.x], sa.sc, blockIdx.x);
+}
+// one CTA per (solve, mode) entry of the batch
+__global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel_batched(const SmallBatchEntry* e) {
+    const SmallBatchEntry& x = e[blockIdx.x];
+    svt_body(x.m, x.sc, x.mode);
 }
 
 // ---------------------------------------------------------------------------
@@ -519,10 +526,8 @@ __global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
 // A closing Newton-Schulz step re-orthonormalises U. The I x R matrices live in
 // shared memory when they fit, else in the global scratch.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
-    DevScalars* sc = sa.sc;
+__device__ __forceinline__ void polar_body(const SmallModeArgs& m, DevScalars* sc, const int mode) {
     if (sc->done) return;
-    const SmallModeArgs& m = sa.m[blockIdx.x];
     const int R = m.R, Rp = m.Rp, ld = Rp;
     const int64_t I = m.I;
     extern __shared__ __align__(16) float sm[];
@@ -542,7 +547,7 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
     const int q = R - s;
     const int s4 = (s + 3) & ~3, q4 = (q + 3) & ~3;
 
-    if (s == 0 && sc->w_ident[blockIdx.x]) {
+    if (s == 0 && sc->w_ident[mode]) {
         // Nothing kept and the last SVT left the basis exactly as it was (W = I, so
         // Urot = U): Eq. 10 with M_n = 0 and every direction in the null space
         // returns the polar factor of U, which is U itself (a previous U-step's
@@ -619,6 +624,14 @@ __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
     tile_AB(Mw, LD, R, Z, ld, Rp, I, m.U, Rp, false);
 }
 
+__global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
+    polar_body(sa.m[blockIdx.x], sa.sc, blockIdx.x);
+}
+__global__ void __launch_bounds__(SM_THREADS) polar_kernel_batched(const SmallBatchEntry* e) {
+    const SmallBatchEntry& x = e[blockIdx.x];
+    polar_body(x.m, x.sc, x.mode);
+}
+
 static size_t small_base_floats(int maxRp) {
     const int ld = maxRp;
     return (size_t)jacobi_floats(ld) + 2 * (size_t)ld * ld + TILE_SCRATCH;
@@ -632,15 +645,13 @@ size_t polar_smem_bytes(int maxRp, int64_t maxI) {
     return 4 * (small_base_floats(maxRp) + 4 * (size_t)maxI * polar_ld(maxRp));
 }
 
-void launch_svt(const SmallArgs& a, cudaStream_t s) {
+size_t svt_launch_smem(const SmallArgs& a) {
     int maxRp = 4;
     for (int n = 0; n < a.N; ++n) maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
-    size_t smem = svt_smem_bytes(maxRp);
-    set_smem_attr((const void*)svt_kernel, (int)smem);
-    svt_kernel<<<a.N, SM_THREADS, smem, s>>>(a);
+    return svt_smem_bytes(maxRp);
 }
 
-void launch_polar(const SmallArgs& a, cudaStream_t s) {
+size_t polar_launch_smem(const SmallArgs& a) {
     int maxRp = 4;
     int64_t maxI = 1;
     bool any_smem = false;
@@ -648,9 +659,29 @@ void launch_polar(const SmallArgs& a, cudaStream_t s) {
         maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
         if (a.m[n].polar_in_smem) { any_smem = true; maxI = a.m[n].I > maxI ? a.m[n].I : maxI; }
     }
-    size_t smem = any_smem ? polar_smem_bytes(maxRp, maxI) : 4 * small_base_floats(maxRp);
+    return any_smem ? polar_smem_bytes(maxRp, maxI) : 4 * small_base_floats(maxRp);
+}
+
+void launch_svt(const SmallArgs& a, cudaStream_t s) {
+    const size_t smem = svt_launch_smem(a);
+    set_smem_attr((const void*)svt_kernel, (int)smem);
+    svt_kernel<<<a.N, SM_THREADS, smem, s>>>(a);
+}
+
+void launch_polar(const SmallArgs& a, cudaStream_t s) {
+    const size_t smem = polar_launch_smem(a);
     set_smem_attr((const void*)polar_kernel, (int)smem);
     polar_kernel<<<a.N, SM_THREADS, smem, s>>>(a);
+}
+
+void launch_polar_batched(const SmallBatchEntry* e, int n, size_t smem, cudaStream_t s) {
+    set_smem_attr((const void*)polar_kernel_batched, (int)smem);
+    polar_kernel_batched<<<n, SM_THREADS, smem, s>>>(e);
+}
+
+void launch_svt_batched(const SmallBatchEntry* e, int n, size_t smem, cudaStream_t s) {
+    set_smem_attr((const void*)svt_kernel_batched, (int)smem);
+    svt_kernel_batched<<<n, SM_THREADS, smem, s>>>(e);
 }
 
 // ---------------------------------------------------------------------------
@@ -664,14 +695,14 @@ void launch_polar(const SmallArgs& a, cudaStream_t s) {
 constexpr int FIN_THREADS = 256;
 constexpr int FIN_OUT = FIN_THREADS / 4;
 
-__global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(FinalizeArgs fa) {
+__device__ __forceinline__ void finalize_body(const FinalizeArgs& fa, const int block) {
     DevScalars* sc = fa.sc;
     if (sc->done) return;
     const int t = threadIdx.x, nt = blockDim.x;
-    if (blockIdx.x > 0) {
+    if (block > 0) {
         __shared__ float sub[4][FIN_OUT];
         const int ol = t % FIN_OUT, h = t / FIN_OUT;
-        int64_t o = (int64_t)(blockIdx.x - 1) * FIN_OUT + ol;
+        int64_t o = (int64_t)(block - 1) * FIN_OUT + ol;
         int mode = -1;
         int64_t i = 0;
         int r = 0;
@@ -794,11 +825,24 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(FinalizeArgs fa) 
     }
 }
 
-void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
+__global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(FinalizeArgs fa) { finalize_body(fa, blockIdx.x); }
+__global__ void __launch_bounds__(FIN_THREADS) finalize_kernel_batched(const FinBatchEntry* e, const int* block_entry) {
+    const FinBatchEntry& x = e[block_entry[blockIdx.x]];
+    finalize_body(x.a, blockIdx.x - x.start);
+}
+
+int finalize_ctas(const FinalizeArgs& a) {
     int64_t tot = 0;
     for (int n = 0; n < a.N; ++n) tot += a.I[n] * a.R[n];
-    int grid = 1 + (int)((tot + FIN_OUT - 1) / FIN_OUT);
-    finalize_kernel<<<grid, FIN_THREADS, 0, s>>>(a);
+    return 1 + (int)((tot + FIN_OUT - 1) / FIN_OUT);
+}
+
+void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
+    finalize_kernel<<<finalize_ctas(a), FIN_THREADS, 0, s>>>(a);
+}
+
+void launch_finalize_batched(const FinBatchEntry* e, const int* block_entry, int grid, cudaStream_t s) {
+    finalize_kernel_batched<<<grid, FIN_THREADS, 0, s>>>(e, block_entry);
 }
 
 // ---------------------------------------------------------------------------
@@ -816,11 +860,11 @@ __host__ __device__ inline int vrot_cols(int64_t P, int64_t post, int RB) {
 }
 
 template <int RB, bool V4>
-__global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
+__device__ __forceinline__ void vrot_body(const VrotArgs& va, const int block) {
     const DevScalars* sc = va.sc;
     if (sc->done) return;
     int k = 0;
-    while (k + 1 < va.N && (int)blockIdx.x >= va.cta_start[k + 1]) ++k;
+    while (k + 1 < va.N && (int)block >= va.cta_start[k + 1]) ++k;
     const VrotMode& m = va.m[k];
     const int R = m.R, Rp = m.Rp;
     const int s = sc->kept[k];
@@ -837,7 +881,7 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
         Wt[idx] = r < R ? m.F[i] * m.W[r * Rp + i] : 0.f;
     }
     __syncthreads();
-    const int64_t u = (int64_t)(blockIdx.x - va.cta_start[k]) * blockDim.x + threadIdx.x;
+    const int64_t u = (int64_t)(block - va.cta_start[k]) * blockDim.x + threadIdx.x;
     if (V4 && vrot_cols(m.P, m.post, RB) == 4) {
         const int64_t per_row = m.post / 4;
         if (u >= m.P / 4) return;
@@ -928,6 +972,14 @@ __global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) {
     }
 }
 
+template <int RB, bool V4>
+__global__ void __launch_bounds__(256) vrot_kernel(VrotArgs va) { vrot_body<RB, V4>(va, blockIdx.x); }
+template <int RB, bool V4>
+__global__ void __launch_bounds__(256) vrot_kernel_batched(const VrotBatchEntry* e, const int* block_entry) {
+    const VrotBatchEntry& x = e[block_entry[blockIdx.x]];
+    vrot_body<RB, V4>(x.a, blockIdx.x - x.start);
+}
+
 int vrot_rb(int maxRp) {
     return maxRp <= 8 ? 8 : maxRp <= 16 ? 16 : maxRp <= 24 ? 24 : maxRp <= 32 ? 32 : maxRp <= 48 ? 48 : 64;
 }
@@ -936,6 +988,35 @@ int vrot_rb(int maxRp) {
 int vrot_ctas(int64_t P, int64_t post, int maxRp) {
     const int cols = vrot_cols(P, post, vrot_rb(maxRp));
     return (int)((P / cols + 255) / 256);
+}
+
+int vrot_launch_rb(const VrotArgs& a) {
+    int maxRp = 4;
+    for (int n = 0; n < a.N; ++n) maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
+    return vrot_rb(maxRp);
+}
+bool vrot_launch_v4(const VrotArgs& a) {
+    const int rb = vrot_launch_rb(a);
+    bool v4 = false;
+    for (int n = 0; n < a.N; ++n) v4 = v4 || vrot_cols(a.m[n].P, a.m[n].post, rb) == 4;
+    return v4;
+}
+
+template <int RB>
+static void launch_vrot_batched_rb(bool v4, const VrotBatchEntry* e, const int* block_entry, int grid, cudaStream_t s) {
+    if (v4) vrot_kernel_batched<RB, true><<<grid, 256, 0, s>>>(e, block_entry);
+    else vrot_kernel_batched<RB, false><<<grid, 256, 0, s>>>(e, block_entry);
+}
+// every entry of one launch has the same rb = vrot_launch_rb and v4 = vrot_launch_v4
+void launch_vrot_batched(int rb, bool v4, const VrotBatchEntry* e, const int* block_entry, int grid, cudaStream_t s) {
+    switch (rb) {
+        case 8: launch_vrot_batched_rb<8>(v4, e, block_entry, grid, s); break;
+        case 16: launch_vrot_batched_rb<16>(v4, e, block_entry, grid, s); break;
+        case 24: launch_vrot_batched_rb<24>(v4, e, block_entry, grid, s); break;
+        case 32: launch_vrot_batched_rb<32>(v4, e, block_entry, grid, s); break;
+        case 48: launch_vrot_batched_rb<48>(v4, e, block_entry, grid, s); break;
+        default: launch_vrot_batched_rb<64>(v4, e, block_entry, grid, s); break;
+    }
 }
 
 // The four-column path is compiled into the launch only when some mode takes it:

@@ -38,6 +38,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+// Orders this thread's later bulk tensor copies through the tensor map at `map`
+// (in global memory, written before the launch) after that write.
+__device__ __forceinline__ void tensormap_acquire(const void* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(map) : "memory");
+}
+// Copies a kernel-argument struct from global to shared memory (all threads of
+// the CTA, 4-byte words), then synchronises the CTA.
+template <class T>
+__device__ __forceinline__ void load_args_to_smem(T* dst, const T* src) {
+    static_assert(sizeof(T) % 4 == 0, "argument structs are word multiples");
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+}
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }

@@ -60,6 +60,7 @@ class pasd_result(ctypes.Structure):
         ("kept", ctypes.c_int32 * MAX_ORDER),
         ("latency_s", ctypes.c_double),
         ("skipped", ctypes.c_int32),
+        ("batched", ctypes.c_int32),
     ]
 
 
@@ -312,4 +313,4 @@ def result_dict(r: pasd_result, order: int) -> dict:
     return {"status": r.status, "iters": r.iters, "res_inf": r.res_inf, "res_fro_rel": r.res_fro_rel,
             "objective": r.objective, "nuclear": list(r.nuclear)[:order], "l1_E": r.l1_E,
             "mu_final": r.mu_final, "kept": list(r.kept)[:order], "latency_s": r.latency_s,
-            "skipped": r.skipped}
+            "skipped": r.skipped, "batched": r.batched}

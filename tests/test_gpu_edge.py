@@ -166,6 +166,77 @@ def test_mixed_video_shape_matches_oracle(env):
     assert abs(O.rse(g["L"], pr.L0) - O.rse(ref.L, pr.L0)) <= 1e-4
 
 
+# --- batched executor ------------------------------------------------------------------
+
+def _serve_all(P, ctx, jobs, timeout=120):
+    import time
+    tickets = [P.pasd_submit(ctx, *j) for j in jobs]
+    t0 = time.time()
+    results = {}
+    while len(results) < len(tickets) and time.time() - t0 < timeout:
+        for t in tickets:
+            if t not in results:
+                st, r = P.pasd_poll(ctx, t)
+                if st != P.PENDING:
+                    results[t] = (st, r)
+        time.sleep(0.001)
+    return [results.get(t) for t in tickets]
+
+
+def test_batched_executor_uneven_solves_equal_alone(env, monkeypatch):
+    # Solves of different orders, sizes, rank buckets and stop rules, one with a
+    # few-row mode, submitted together: they share the batched launches (one per
+    # kernel and template group) and each result equals the same solve alone, bit
+    # for bit; the solves also equal the per-stream served path's.
+    torch, P, ctx = env
+    # (dims, Tucker ranks, rank bounds, stop rule, flags)
+    cases = [((30, 26, 22), (3, 3, 3), (4, 4, 4), P.STOP_INF_ABS, 0),
+             ((40, 36, 32), (3, 3, 3), (12, 12, 12), P.STOP_INF_ABS, 0),
+             ((12, 10, 3, 20), (2, 2, 2, 2), (3, 3, 2, 4), P.STOP_INF_ABS, 0),
+             ((36, 30, 24), (3, 3, 3), (5, 6, 7), P.STOP_FRO_REL, 0),
+             ((64, 48, 40), (4, 4, 4), (20, 20, 20), P.STOP_INF_ABS, P.F_SKIP_IDLE),
+             ((20, 3, 16), (3, 2, 2), (4, 3, 3), P.STOP_INF_ABS, 0)]
+
+    def params(dims, ranks, stop, flags):
+        return P.make_params(dims, ranks, stop=stop, tol=1e-6 if stop == P.STOP_FRO_REL else 0.0,
+                             max_iter=1000, flags=flags)
+    plans, jobs, alone = [], [], []
+    for i, (dims, tucker, ranks, stop, flags) in enumerate(cases):
+        pr = synth.planted(dims, tucker, 0.1, 70 + i, scale="std", amp=5.0)
+        plan, _ = P.pasd_plan(ctx, params(dims, ranks, stop, flags))
+        T = torch.from_numpy(pr.T).cuda()
+        L, E = torch.empty_like(T), torch.empty_like(T)
+        r0 = P.pasd_solve(plan, T, L, E)
+        alone.append((L.clone(), E.clone(), r0.iters))
+        L.zero_(); E.zero_()
+        plans.append(plan)
+        jobs.append((plan, T, L, E))
+    torch.cuda.synchronize()
+    res = _serve_all(P, ctx, jobs)
+    for i, rr in enumerate(res):
+        assert rr is not None
+        st, r = rr
+        assert st == P.OK and r.batched == 1 and r.iters == alone[i][2]
+        assert torch.equal(jobs[i][2], alone[i][0]) and torch.equal(jobs[i][3], alone[i][1])
+    monkeypatch.setenv("PASD_NO_BATCH", "1")
+    ctx2 = P.pasd_ctx_create(0)
+    monkeypatch.delenv("PASD_NO_BATCH")
+    plans2, jobs2 = [], []
+    for i, (dims, tucker, ranks, stop, flags) in enumerate(cases):
+        plan, _ = P.pasd_plan(ctx2, params(dims, ranks, stop, flags))
+        T = jobs[i][1]
+        plans2.append(plan)
+        jobs2.append((plan, T, torch.empty_like(T), torch.empty_like(T)))
+    res2 = _serve_all(P, ctx2, jobs2)
+    for i, rr in enumerate(res2):
+        st, r = rr
+        assert st == P.OK and r.batched == 0
+        assert torch.equal(jobs2[i][2], alone[i][0]) and torch.equal(jobs2[i][3], alone[i][1])
+    for plan in plans + plans2:
+        P.pasd_plan_destroy(plan)
+    P.pasd_ctx_destroy(ctx2)
+
+
 # --- autotuner -------------------------------------------------------------------------
 
 def test_autotuner_choice_is_cached_reported_and_harmless(env, monkeypatch):
