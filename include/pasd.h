@@ -176,15 +176,18 @@ pasd_status pasd_solve_host(pasd_plan_t* plan, const float* T_host, float* L_hos
  * tensors T, L, E; the caller keeps them alive and untouched until pasd_poll
  * returns something other than PASD_PENDING. A solve is admitted when its
  * plan's footprint fits the context's HBM budget; admitted solves advance
- * together and retire as they converge. Solves whose kernels all have batched
- * forms (the FP32 path on bulk-copy kernels) join one batch: each loop body is
- * one launch per kernel for all of them (grouped by the kernels' template
+ * together and retire as they converge. Solves on the bulk-copy kernels (orders
+ * 2-4, last mode a multiple of 4 or padded to one) join a batch: each loop body
+ * is one launch per kernel for all members (grouped by the kernels' template
  * parameters: rank bucket, tile threads, tensor order), replayed as one
  * captured CUDA graph per body that is rebuilt when solves join or leave at
- * the boundaries of 8-body chunks. The others (mixed precision, layouts on the
- * fallback kernels) run each on a stream of its own. Results are the same bit
- * for bit either way. PASD_NO_BATCH=1 (read by pasd_ctx_create) puts every
- * served solve on its own stream. The solve's
+ * chunk boundaries; kernels without a batched form (few-row modes, the
+ * tensor-core A-pass of mixed precision) are launched per member inside that
+ * body. Solves on the fallback kernels run each on a stream of its own.
+ * Results are the same bit for bit either way. Knobs (read by pasd_ctx_create):
+ * PASD_NO_BATCH=1 puts every served solve on its own stream; PASD_BATCHES
+ * (1-16, default 4) batches run on streams of their own and a new solve joins
+ * the smallest; PASD_BATCH_CHUNK (1-64, default 8) bodies per chunk. The solve's
  * stream is not ordered after any stream of the caller: T must be fully
  * written (its producing stream synchronised) before pasd_submit is called.
  * One plan serves one solve at a time (further submits of it wait in the

@@ -1333,11 +1333,10 @@ extern "C" pasd_status pasd_state_get(pasd_plan_t* pl, int32_t item, int32_t mod
 // ---------------------------------------------------------------------------
 // A plan can join a batch when all its streaming kernels are the bulk-copy FP32
 // ones that have batched forms (few-row modes run as their own launches).
+// A-pass launches without a batched form (the tensor-core A-pass of mixed
+// precision) run inside the batched body as launches of their own.
 static bool batchable(const pasd_plan_t* pl) {
-    if (!pl->arena || !pl->tma || pl->n_ap_plain > 0) return false;
-    for (int q = 0; q < pl->n_ap_tma; ++q)
-        if (apass_batch_ctas(pl->ap_tma[q]) < 0) return false;
-    return true;
+    return pl->arena && pl->tma && pl->n_ap_plain == 0;
 }
 
 struct BatchLaunch {
@@ -1410,9 +1409,12 @@ static void launch_batch_body(BatchExec& b, cudaStream_t s) {
     auto map = [&](size_t off) { return reinterpret_cast<const int*>(d + off); };
     launch_polar_batched(reinterpret_cast<const SmallBatchEntry*>(d + b.small_ent), b.n_small, b.polar_smem, s);
     for (const BatchLaunch& L : b.apass) launch_apass_batched(L.k1, L.k2, ent(L.ent), map(L.map), L.grid, L.smem, s);
-    for (pasd_plan_t* pl : b.members)
+    for (pasd_plan_t* pl : b.members) {
+        for (int q = 0; q < pl->n_ap_tma; ++q)
+            if (apass_batch_ctas(pl->ap_tma[q]) < 0) launch_apass_tma(pl->ap_tma[q], s);
         for (int n = 0; n < pl->N; ++n)
             if (pl->ap_small[n]) launch_apass_small(pl->ap[n], pl->ap_small_grid[n], s);
+    }
     launch_svt_batched(reinterpret_cast<const SmallBatchEntry*>(d + b.small_ent), b.n_small, b.svt_smem, s);
     for (const BatchLaunch& L : b.vrot)
         launch_vrot_batched(L.k1, L.k2 != 0, reinterpret_cast<const VrotBatchEntry*>(d + L.ent), map(L.map), L.grid, s);
@@ -1461,7 +1463,8 @@ static bool batch_build(BatchExec& b, cudaStream_t s) {
     std::map<int, std::vector<FiItem>> fi;
     for (pasd_plan_t* pl : b.members) {
         for (int q = 0; q < pl->n_ap_tma; ++q)
-            ap[{apass_batch_rp(pl->ap_tma[q]), apass_tma_cols(pl->ap_tma[q])}].push_back(ApItem{pl->ap_tma[q]});
+            if (apass_batch_ctas(pl->ap_tma[q]) >= 0)
+                ap[{apass_batch_rp(pl->ap_tma[q]), apass_tma_cols(pl->ap_tma[q])}].push_back(ApItem{pl->ap_tma[q]});
         vr[{vrot_launch_rb(pl->vr), vrot_launch_v4(pl->vr) ? 1 : 0}].push_back(VrItem{pl});
         fu[{fused_batch_order(pl->tma), fused_batch_threads(pl->tma)}].push_back(FuItem{pl->tma});
         if (pl->n_mp_big > 0) {

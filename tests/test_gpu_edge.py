@@ -185,25 +185,28 @@ def _serve_all(P, ctx, jobs, timeout=120):
 
 def test_batched_executor_uneven_solves_equal_alone(env, monkeypatch):
     # Solves of different orders, sizes, rank buckets and stop rules, one with a
-    # few-row mode, submitted together: they share the batched launches (one per
-    # kernel and template group) and each result equals the same solve alone, bit
-    # for bit; the solves also equal the per-stream served path's.
+    # few-row mode, one in mixed precision (its tensor-core A-pass launched on its
+    # own inside the batched body), submitted together: they share the batched
+    # launches (one per kernel and template group) and each result equals the same
+    # solve alone, bit for bit; the solves also equal the per-stream served path's.
     torch, P, ctx = env
-    # (dims, Tucker ranks, rank bounds, stop rule, flags)
-    cases = [((30, 26, 22), (3, 3, 3), (4, 4, 4), P.STOP_INF_ABS, 0),
-             ((40, 36, 32), (3, 3, 3), (12, 12, 12), P.STOP_INF_ABS, 0),
-             ((12, 10, 3, 20), (2, 2, 2, 2), (3, 3, 2, 4), P.STOP_INF_ABS, 0),
-             ((36, 30, 24), (3, 3, 3), (5, 6, 7), P.STOP_FRO_REL, 0),
-             ((64, 48, 40), (4, 4, 4), (20, 20, 20), P.STOP_INF_ABS, P.F_SKIP_IDLE),
-             ((20, 3, 16), (3, 2, 2), (4, 3, 3), P.STOP_INF_ABS, 0)]
+    F, M = P.PREC_FP32, P.PREC_MIXED
+    # (dims, Tucker ranks, rank bounds, stop rule, flags, precision)
+    cases = [((30, 26, 22), (3, 3, 3), (4, 4, 4), P.STOP_INF_ABS, 0, F),
+             ((40, 36, 32), (3, 3, 3), (12, 12, 12), P.STOP_INF_ABS, 0, F),
+             ((12, 10, 3, 20), (2, 2, 2, 2), (3, 3, 2, 4), P.STOP_INF_ABS, 0, F),
+             ((36, 30, 24), (3, 3, 3), (5, 6, 7), P.STOP_FRO_REL, 0, F),
+             ((64, 48, 40), (4, 4, 4), (20, 20, 20), P.STOP_INF_ABS, P.F_SKIP_IDLE, F),
+             ((20, 3, 16), (3, 2, 2), (4, 3, 3), P.STOP_INF_ABS, 0, F),
+             ((48, 40, 36), (3, 3, 3), (8, 8, 8), P.STOP_INF_ABS, 0, M)]
 
-    def params(dims, ranks, stop, flags):
+    def params(dims, ranks, stop, flags, prec):
         return P.make_params(dims, ranks, stop=stop, tol=1e-6 if stop == P.STOP_FRO_REL else 0.0,
-                             max_iter=1000, flags=flags)
+                             max_iter=1000, flags=flags, precision=prec)
     plans, jobs, alone = [], [], []
-    for i, (dims, tucker, ranks, stop, flags) in enumerate(cases):
+    for i, (dims, tucker, ranks, stop, flags, prec) in enumerate(cases):
         pr = synth.planted(dims, tucker, 0.1, 70 + i, scale="std", amp=5.0)
-        plan, _ = P.pasd_plan(ctx, params(dims, ranks, stop, flags))
+        plan, _ = P.pasd_plan(ctx, params(dims, ranks, stop, flags, prec))
         T = torch.from_numpy(pr.T).cuda()
         L, E = torch.empty_like(T), torch.empty_like(T)
         r0 = P.pasd_solve(plan, T, L, E)
@@ -222,8 +225,8 @@ def test_batched_executor_uneven_solves_equal_alone(env, monkeypatch):
     ctx2 = P.pasd_ctx_create(0)
     monkeypatch.delenv("PASD_NO_BATCH")
     plans2, jobs2 = [], []
-    for i, (dims, tucker, ranks, stop, flags) in enumerate(cases):
-        plan, _ = P.pasd_plan(ctx2, params(dims, ranks, stop, flags))
+    for i, (dims, tucker, ranks, stop, flags, prec) in enumerate(cases):
+        plan, _ = P.pasd_plan(ctx2, params(dims, ranks, stop, flags, prec))
         T = jobs[i][1]
         plans2.append(plan)
         jobs2.append((plan, T, torch.empty_like(T), torch.empty_like(T)))
