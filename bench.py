@@ -195,7 +195,9 @@ def run_reference(args):
             "steps": steps, "steps_requested": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * el / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": CONFIG,
+            "data": "synthetic",
+            "config": dict(CONFIG, step="one FP64 loop body on the host cores (a bounded sample of the "
+                                        "181-body solve, whose bodies/s the metric counts)"),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{steps} FP64 loop bodies of the 200^3 workload "
                                        f"after {args.warmup} warm-up bodies"},
@@ -546,10 +548,12 @@ def _video(P, torch, ctx, args):
                     float(np.linalg.norm(pr.L0)))
         P.pasd_begin(plan, T, stream)
         per = P.pasd_profile_iterations(plan, int(r.iters), stream)
+        info = P.pasd_plan_info(plan)
         P.pasd_plan_destroy(plan)
         out[name] = {"iters_per_s": round(r.iters / (ms / 1000.0), 1), "iters": int(r.iters),
                      "ms_per_solve": round(ms, 2), "rse": rse, "kept": list(r.kept)[:4],
-                     "kernel_us_per_body": {k: round(1000 * v / r.iters, 1) for k, v in per.items()}}
+                     "kernel_us_per_body": {k: round(1000 * v / r.iters, 1) for k, v in per.items()},
+                     "plan": {k: info[k] for k in ("autotune", "apass_cols_per_thread", "apass_row_groups")}}
         out["footprint_bytes"] = footprint
     return out
 

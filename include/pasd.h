@@ -98,6 +98,16 @@ typedef struct {
  * trace records (kept 0), counted in `iters` and reported in `skipped`. */
 #define PASD_F_SKIP_IDLE 1u
 
+/* FP64 eigen-solves. The R_n x R_n symmetric eigen-problems of each loop body
+ * (the Gram matrix A_n A_n^T of the SVT after Eq. 13, and M^T M of the U-step's
+ * polar factor, Eq. 10) are solved in double: cyclic Jacobi with correctly
+ * rounded rotations to a relative threshold of 1e-13, and the inverse square
+ * roots of the U-step formed in double, each rounded to float once. The Gram
+ * matrices themselves and every I_n x R_n product stay FP32. Rank bounds up to
+ * 56 (UNSUPPORTED above: the double workspace must fit shared memory). The
+ * default keeps these solves in FP32 (relative Jacobi threshold 1e-6). */
+#define PASD_F_FP64_EIG 2u
+
 typedef struct {
     int32_t status;                       /* pasd_status of the solve                  */
     int32_t iters;                        /* completed loop bodies                     */

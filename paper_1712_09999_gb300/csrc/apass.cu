@@ -407,6 +407,7 @@ struct ApassTmaPlan {
     int kind;      // ApassKind
     int grid;      // persistent grid of the tensor-core kernel (one CTA per SM)
     int nc;        // FMA kernel: columns per thread
+    int ks;        // FMA kernel: thread groups splitting each stage's rows (1 or 2)
     size_t pipe_floats, epi_base_floats;   // shared-memory parts independent of nc
 };
 
@@ -425,7 +426,24 @@ template <int RP> struct AtShape {
     static constexpr int THREADS = AP_BN / COLS;
 };
 
-template <int RP, int NC>
+// KS = 2 splits every stage's AP_BK rows between two groups of NT threads that
+// hold the same columns (twice the warps for the same tiles and registers per
+// thread); group 1 hands its sums to group 0 through shared memory at the end,
+// and A = (group 0's rows) + (group 1's rows) in that order.
+// Resident CTAs the register budget is sized for: as many as hold the
+// accumulators and about 48 more registers a thread, at most 4.
+static constexpr inline __host__ __device__ int at_min_blocks(int RP, int NC, int KS) {
+    return KS == 1 ? 0 : (65536 / ((AP_BN / NC) * KS * (NC * RP + 48)) < 1 ? 1
+                          : 65536 / ((AP_BN / NC) * KS * (NC * RP + 48)) > 4 ? 4
+                          : 65536 / ((AP_BN / NC) * KS * (NC * RP + 48)));
+}
+
+// The row-group split is offered up to this padded rank: beyond it the
+// accumulators of the default columns do not fit the register budget of
+// four resident CTAs.
+constexpr int kSplitMaxRp = 24;
+
+template <int RP, int NC, int KS>
 __device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const ApassTmaArgs& aa, const int block) {
     extern __shared__ __align__(16) float sm_raw[];
     float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 511) & ~uintptr_t(511));
@@ -438,6 +456,8 @@ __device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const A
     if (sc->done) return;
     const int task = block - aa.cta_start[k];
     const int t = threadIdx.x;
+    const int grp = KS == 1 ? 0 : t / NT;        // row group
+    const int lt = KS == 1 ? t : t - grp * NT;   // column slot within the group
     const int64_t I = m.I, post = m.post;
     const int BN = m.BN;
     int64_t a0, b0;
@@ -478,8 +498,8 @@ __device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const A
     if (t == 0)
         for (int s2 = 0; s2 < AT_STAGES - 1 && s2 < nk; ++s2) issue(s2);
 
-    // thread t: columns t + NT q of the task (q < NC); several columns per
-    // thread amortise each broadcast read of a U row over NC x RP multiply-adds
+    // thread lt of its group: columns lt + NT q of the task (q < NC); several columns
+    // per thread amortise each broadcast read of a U row over NC x RP multiply-adds
     float acc[NC][RP];
 #pragma unroll
     for (int q = 0; q < NC; ++q)
@@ -499,9 +519,10 @@ __device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const A
         if (!m.rowmajor) {
             int col[NC];     // a column past the task reads a valid one and is never stored
 #pragma unroll
-            for (int q = 0; q < NC; ++q) col[q] = t + NT * q < BN ? t + NT * q : t;
+            for (int q = 0; q < NC; ++q) col[q] = lt + NT * q < BN ? lt + NT * q : lt;
+            constexpr int KR = AP_BK / KS;
 #pragma unroll 2
-            for (int kk = 0; kk < AP_BK; ++kk) {
+            for (int kk = grp * KR; kk < grp * KR + KR; ++kk) {
                 float g[NC];
 #pragma unroll
                 for (int q = 0; q < NC; ++q) g[q] = gs[kk * BN + col[q]];
@@ -519,13 +540,14 @@ __device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const A
                 }
             }
         } else {
-            const int sw = (t >> 1) & 3;    // the same for every column t + NT q (NT even)
+            const int sw = (lt >> 1) & 3;   // the same for every column lt + NT q (NT even)
+            constexpr int K4 = AP_BK / 4 / KS;
 #pragma unroll
-            for (int k4 = 0; k4 < AP_BK / 4; ++k4) {
+            for (int k4 = grp * K4; k4 < grp * K4 + K4; ++k4) {
                 float gq[NC][4];
 #pragma unroll
                 for (int q = 0; q < NC; ++q) {
-                    const float4 v = *reinterpret_cast<const float4*>(gs + (t + NT * q) * AP_BK + 4 * (k4 ^ sw));
+                    const float4 v = *reinterpret_cast<const float4*>(gs + (lt + NT * q) * AP_BK + 4 * (k4 ^ sw));
                     gq[q][0] = v.x; gq[q][1] = v.y; gq[q][2] = v.z; gq[q][3] = v.w;
                 }
 #pragma unroll
@@ -560,17 +582,41 @@ __device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const A
         return;
     }
     __syncthreads();   // every stage consumed and no copy in flight: smem is free for the epilogue
+    if (KS == 2) {
+        // group 1's sums to group 0 ([q][lt][RP]), added after group 0's own
+        float* hand = smem;
+        if (grp == 1)
+#pragma unroll
+            for (int q = 0; q < NC; ++q)
+#pragma unroll
+                for (int r4 = 0; r4 < RP / 4; ++r4)
+                    *reinterpret_cast<float4*>(hand + (q * NT + lt) * RP + 4 * r4) =
+                        make_float4(acc[q][4 * r4], acc[q][4 * r4 + 1], acc[q][4 * r4 + 2], acc[q][4 * r4 + 3]);
+        __syncthreads();
+        if (grp == 1) return;   // group 0 alone from here (named barrier 1 below)
+#pragma unroll
+        for (int q = 0; q < NC; ++q)
+#pragma unroll
+            for (int r4 = 0; r4 < RP / 4; ++r4) {
+                const float4 h = *reinterpret_cast<const float4*>(hand + (q * NT + lt) * RP + 4 * r4);
+                acc[q][4 * r4 + 0] += h.x;
+                acc[q][4 * r4 + 1] += h.y;
+                acc[q][4 * r4 + 2] += h.z;
+                acc[q][4 * r4 + 3] += h.w;
+            }
+        asm volatile("bar.sync 1, %0;\n" ::"n"(NT) : "memory");   // read before the epilogue overwrites it
+    }
 
     // columns past the task carry no data: zero them for the Gram sums
 #pragma unroll
     for (int q = 0; q < NC; ++q)
-        if (t + NT * q >= ncol)
+        if (lt + NT * q >= ncol)
 #pragma unroll
             for (int r = 0; r < RP; ++r) acc[q][r] = 0.f;
     // ---- store A (layout [pre][Rp][post]) ----
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-        const int c = t + NT * q;
+        const int c = lt + NT * q;
         if (c < ncol) {
             if (m.rowmajor) {
                 float4* dst = reinterpret_cast<float4*>(m.A + (a0 + c) * RP);
@@ -584,13 +630,13 @@ __device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const A
             }
         }
     }
-    gram_epilogue<RP, NT, NC>(acc, smem, m.gram_part + (size_t)task * RP * RP);
+    gram_epilogue<RP, NT, NC, AP_BN, (KS == 2 ? 1 : 0)>(acc, smem, m.gram_part + (size_t)task * RP * RP, lt);
 }
 
-template <int RP, int NC>
-__global__ void __launch_bounds__(AP_BN / NC) apass_tma_kernel(const __grid_constant__ ApassTmaMaps maps,
-                                                               const ApassTmaArgs aa) {
-    apass_tma_body<RP, NC>(maps, aa, blockIdx.x);
+template <int RP, int NC, int KS>
+__global__ void __launch_bounds__(AP_BN / NC * KS, at_min_blocks(RP, NC, KS))
+    apass_tma_kernel(const __grid_constant__ ApassTmaMaps maps, const ApassTmaArgs aa) {
+    apass_tma_body<RP, NC, KS>(maps, aa, blockIdx.x);
 }
 
 // Batched: CTAs [start, start + tasks) of an entry run one solve's A-pass group
@@ -600,8 +646,9 @@ struct ApassBatchEntry {
     ApassTmaArgs args;
     int start;
 };
-template <int RP, int NC>
-__global__ void __launch_bounds__(AP_BN / NC) apass_tma_kernel_batched(const ApassBatchEntry* e, const int* block_entry) {
+template <int RP, int NC, int KS>
+__global__ void __launch_bounds__(AP_BN / NC * KS, at_min_blocks(RP, NC, KS))
+    apass_tma_kernel_batched(const ApassBatchEntry* e, const int* block_entry) {
     const ApassBatchEntry& x = e[block_entry[blockIdx.x]];
     __shared__ __align__(16) ApassTmaArgs s_aa;
     load_args_to_smem(&s_aa, &x.args);
@@ -612,7 +659,7 @@ __global__ void __launch_bounds__(AP_BN / NC) apass_tma_kernel_batched(const Apa
         tensormap_acquire(&x.maps.g[k]);
         tensormap_acquire(&x.maps.u[k]);
     }
-    apass_tma_body<RP, NC>(x.maps, s_aa, block);
+    apass_tma_body<RP, NC, KS>(x.maps, s_aa, block);
 }
 
 // ---------------------------------------------------------------------------
@@ -926,16 +973,21 @@ __global__ void __launch_bounds__(TP_THREADS, 1) apass_tc_kernel(const __grid_co
     if (warp == 1) tmem_dealloc(tm, S::TMEM_COLS);
 }
 
-template <int RP, int NC>
+template <int RP, int NC, int KS>
 static void launch_tma_rp_nc(const ApassTmaPlan& p, cudaStream_t s) {
-    set_smem_attr((const void*)apass_tma_kernel<RP, NC>, (int)p.smem);
-    apass_tma_kernel<RP, NC><<<p.args.cta_start[p.args.count], AP_BN / NC, p.smem, s>>>(p.maps, p.args);
+    set_smem_attr((const void*)apass_tma_kernel<RP, NC, KS>, (int)p.smem);
+    apass_tma_kernel<RP, NC, KS><<<p.args.cta_start[p.args.count], AP_BN / NC * KS, p.smem, s>>>(p.maps, p.args);
 }
+// variants: default columns per thread, half of them, or the default with the
+// rows of each stage split between two thread groups
 template <int RP>
 static void launch_tma_rp(const ApassTmaPlan& p, cudaStream_t s) {
     constexpr int C = AtShape<RP>::COLS;
-    if (p.nc == C) launch_tma_rp_nc<RP, C>(p, s);
-    else launch_tma_rp_nc<RP, C / 2>(p, s);
+    if constexpr (RP <= kSplitMaxRp) {
+        if (p.ks == 2) { launch_tma_rp_nc<RP, C, 2>(p, s); return; }
+    }
+    if (p.nc == C) launch_tma_rp_nc<RP, C, 1>(p, s);
+    else launch_tma_rp_nc<RP, C / 2, 1>(p, s);
 }
 
 template <int RP>
@@ -1072,6 +1124,7 @@ ApassTmaPlan* make_apass_tma(const ApassArgs* a, const int* modes, int count, in
     p->args.cta_start[count] = start;
     p->smem = smem;
     p->nc = p->args.Rp <= 40 ? 4 : 2;
+    p->ks = 1;
     return p;
 }
 
@@ -1089,47 +1142,55 @@ void apass_batch_fill(void* entry, const ApassTmaPlan* p, int start) {
     e.start = start;
     std::memcpy(entry, &e, sizeof(e));
 }
-template <int RP, int NC>
+template <int RP, int NC, int KS>
 static void launch_batched_rp_nc(const void* entries, const int* block_entry, int grid, size_t smem, cudaStream_t s) {
-    set_smem_attr((const void*)apass_tma_kernel_batched<RP, NC>, (int)smem);
-    apass_tma_kernel_batched<RP, NC><<<grid, AP_BN / NC, smem, s>>>(static_cast<const ApassBatchEntry*>(entries),
-                                                                   block_entry);
+    set_smem_attr((const void*)apass_tma_kernel_batched<RP, NC, KS>, (int)smem);
+    apass_tma_kernel_batched<RP, NC, KS><<<grid, AP_BN / NC * KS, smem, s>>>(static_cast<const ApassBatchEntry*>(entries), block_entry);
 }
 template <int RP>
-static void launch_batched_rp(int nc, const void* entries, const int* block_entry, int grid, size_t smem,
+static void launch_batched_rp(int var, const void* entries, const int* block_entry, int grid, size_t smem,
                               cudaStream_t s) {
     constexpr int C = AtShape<RP>::COLS;
-    if (nc == C) launch_batched_rp_nc<RP, C>(entries, block_entry, grid, smem, s);
-    else launch_batched_rp_nc<RP, C / 2>(entries, block_entry, grid, smem, s);
+    const int nc = var % 100, ks = var / 100;
+    if constexpr (RP <= kSplitMaxRp) {
+        if (ks == 2) { launch_batched_rp_nc<RP, C, 2>(entries, block_entry, grid, smem, s); return; }
+    }
+    if (nc == C) launch_batched_rp_nc<RP, C, 1>(entries, block_entry, grid, smem, s);
+    else launch_batched_rp_nc<RP, C / 2, 1>(entries, block_entry, grid, smem, s);
 }
-// every entry of one launch has padded rank Rp and nc columns per thread
-void launch_apass_batched(int Rp, int nc, const void* entries, const int* block_entry, int grid, size_t smem,
+void launch_apass_batched(int Rp, int var, const void* entries, const int* block_entry, int grid, size_t smem,
                           cudaStream_t s) {
     switch (Rp) {
-        case 4: launch_batched_rp<4>(nc, entries, block_entry, grid, smem, s); break;
-        case 8: launch_batched_rp<8>(nc, entries, block_entry, grid, smem, s); break;
-        case 12: launch_batched_rp<12>(nc, entries, block_entry, grid, smem, s); break;
-        case 16: launch_batched_rp<16>(nc, entries, block_entry, grid, smem, s); break;
-        case 20: launch_batched_rp<20>(nc, entries, block_entry, grid, smem, s); break;
-        case 24: launch_batched_rp<24>(nc, entries, block_entry, grid, smem, s); break;
-        case 28: launch_batched_rp<28>(nc, entries, block_entry, grid, smem, s); break;
-        case 32: launch_batched_rp<32>(nc, entries, block_entry, grid, smem, s); break;
-        case 40: launch_batched_rp<40>(nc, entries, block_entry, grid, smem, s); break;
-        case 48: launch_batched_rp<48>(nc, entries, block_entry, grid, smem, s); break;
-        case 56: launch_batched_rp<56>(nc, entries, block_entry, grid, smem, s); break;
-        case 64: launch_batched_rp<64>(nc, entries, block_entry, grid, smem, s); break;
+        case 4: launch_batched_rp<4>(var, entries, block_entry, grid, smem, s); break;
+        case 8: launch_batched_rp<8>(var, entries, block_entry, grid, smem, s); break;
+        case 12: launch_batched_rp<12>(var, entries, block_entry, grid, smem, s); break;
+        case 16: launch_batched_rp<16>(var, entries, block_entry, grid, smem, s); break;
+        case 20: launch_batched_rp<20>(var, entries, block_entry, grid, smem, s); break;
+        case 24: launch_batched_rp<24>(var, entries, block_entry, grid, smem, s); break;
+        case 28: launch_batched_rp<28>(var, entries, block_entry, grid, smem, s); break;
+        case 32: launch_batched_rp<32>(var, entries, block_entry, grid, smem, s); break;
+        case 40: launch_batched_rp<40>(var, entries, block_entry, grid, smem, s); break;
+        case 48: launch_batched_rp<48>(var, entries, block_entry, grid, smem, s); break;
+        case 56: launch_batched_rp<56>(var, entries, block_entry, grid, smem, s); break;
+        case 64: launch_batched_rp<64>(var, entries, block_entry, grid, smem, s); break;
         default: break;
     }
 }
 
 int apass_tma_cols(const ApassTmaPlan* p) { return p->kind == APASS_FFMA ? p->nc : 0; }
+int apass_tma_split(const ApassTmaPlan* p) { return p->kind == APASS_FFMA ? p->ks : 0; }
+int apass_tma_variant(const ApassTmaPlan* p) { return p->kind == APASS_FFMA ? p->nc + 100 * p->ks : 0; }
 
-// Columns per thread of the FMA kernel: its default or half of it.
-void apass_tma_set_cols(ApassTmaPlan* p, int nc) {
+// Columns per thread of the FMA kernel (its default or half of it) and row
+// groups (1, or 2 with the default columns).
+void apass_tma_set_cols(ApassTmaPlan* p, int nc, int ks) {
     if (p->kind != APASS_FFMA) return;
     const int def = p->args.Rp <= 40 ? 4 : 2;
     if (nc != def && nc != def / 2) return;
+    if (ks != 1 && (ks != 2 || nc != def || p->args.Rp > kSplitMaxRp)) return;
     p->nc = nc;
+    p->ks = ks;
+    // the row groups' hand-off ([nc][AP_BN / nc][Rp]) fits in the epilogue's A tile
     const size_t epi = p->epi_base_floats + gram_red_floats(p->args.Rp, AP_BN / nc);
     p->smem = 4 * std::max(p->pipe_floats, epi) + 512;
 }

@@ -145,7 +145,7 @@ struct pasd_plan {
     int default_fused_k = 0;             // CTAs per SM of the planner's default geometry
     int tuned_fused_k = 0;               // CTAs per SM of the geometry in use
     int tuned_mp_waves = 1;
-    int tuned_ap_half = 0;
+    int tuned_ap_var = 0;
     int ap_tma_default_nc[PASD_MAXN];
     bool tuned = false;
     const char* tune_mode = "pending";   // pending (no pasd_begin yet), timed, cached, off
@@ -284,7 +284,11 @@ extern "C" pasd_status pasd_plan(pasd_ctx* c, const pasd_params* pin, pasd_plan_
     if (p.stop_rule < 0 || p.stop_rule > 2) return fail(PASD_ERR_INVALID_ARG, "bad stop rule");
     if (p.precision != PASD_PREC_FP32 && p.precision != PASD_PREC_MIXED)
         return fail(PASD_ERR_INVALID_ARG, "bad precision");
-    if (p.flags & ~(uint32_t)PASD_F_SKIP_IDLE) return fail(PASD_ERR_INVALID_ARG, "unknown flag bits");
+    if (p.flags & ~(uint32_t)(PASD_F_SKIP_IDLE | PASD_F_FP64_EIG)) return fail(PASD_ERR_INVALID_ARG, "unknown flag bits");
+    if (p.flags & PASD_F_FP64_EIG)
+        for (int n = 0; n < N; ++n)
+            if (p.rank_bound[n] > 56)
+                return fail(PASD_ERR_UNSUPPORTED, "PASD_F_FP64_EIG: rank bounds above 56 do not fit shared memory");
 
     pasd_plan_t* pl = new pasd_plan_t();
     pl->ctx = c;
@@ -576,7 +580,7 @@ static void enqueue_iteration(pasd_plan_t* pl, cudaStream_t s) {
 struct TuneChoice {
     int fused_k;     // resident CTAs per SM of the fused pass's geometry
     int mp_waves;    // waves of M-pass CTAs
-    int ap_half;     // 1: the A-pass FMA kernel with half its default columns per thread
+    int ap_var;      // A-pass FMA kernel: 0 default, 1 half the columns per thread, 2 rows split in two groups
 };
 static std::mutex g_tune_mu;
 static std::map<std::string, TuneChoice> g_tune_cache;
@@ -670,16 +674,37 @@ static void apply_tune(pasd_plan_t* pl, const TuneChoice& c) {
         const int cur = apass_tma_cols(pl->ap_tma[q]);
         if (cur == 0) continue;
         const int def = pl->ap_tma_default_nc[q];
-        apass_tma_set_cols(pl->ap_tma[q], c.ap_half ? def / 2 : def);
+        apass_tma_set_cols(pl->ap_tma[q], c.ap_var == 1 ? def / 2 : def, c.ap_var == 2 ? 2 : 1);
     }
-    pl->tuned_ap_half = c.ap_half;
+    pl->tuned_ap_var = c.ap_var;
 }
 
 // Times the candidates on the plan's own buffers (before its first pasd_begin
 // fills them) and keeps one only if it beats the planner's default by more than
 // 3%, so timing noise between near-equal shapes does not flip the choice; the
 // choice is cached per device and problem shape.
+// PASD_TUNE_APASS=0|1|2 forces the FP32 A-pass variant of every plan (default
+// columns, half the columns, rows split in two groups) over the timed or cached
+// choice, for comparisons; it does not enter the cache.
+static void force_apass_variant(pasd_plan_t* pl) {
+    const char* f = std::getenv("PASD_TUNE_APASS");
+    if (!f || f[0] < '0' || f[0] > '2' || f[1] != 0) return;
+    const int var = f[0] - '0';
+    for (int q = 0; q < pl->n_ap_tma; ++q) {
+        const int def = pl->ap_tma_default_nc[q];
+        if (def == 0) continue;
+        apass_tma_set_cols(pl->ap_tma[q], var == 1 ? def / 2 : def, var == 2 ? 2 : 1);
+    }
+    pl->tuned_ap_var = var;
+}
+
+static void autotune_impl(pasd_plan_t* pl);
 static void autotune(pasd_plan_t* pl) {
+    autotune_impl(pl);
+    force_apass_variant(pl);
+}
+
+static void autotune_impl(pasd_plan_t* pl) {
     pl->tuned = true;
     pl->tuned_fused_k = pl->default_fused_k;
     pl->tuned_mp_waves = 1;
@@ -717,32 +742,58 @@ static void autotune(pasd_plan_t* pl) {
         }
         if (t_def == t_def && best < 0.97f * t_def) choice.fused_k = best_k;
     }
+    // The M-pass and the A-pass read G_n (D floats per mode), which can fit in L2
+    // when they are launched back to back; in a loop body each runs after the
+    // fused pass has streamed (2N + 3) 4D bytes through it. So each of their
+    // candidates is timed behind an idle fused pass, whose own time is subtracted.
+    FusedTmaPlan* evict = nullptr;
+    if (pl->tma) {
+        FusedArgs fe = pl->fu;
+        fe.sc = pl->tune_sc;
+        evict = make_fused_tma(fe, pl->Tc, err, sizeof(err));
+    }
+    // mean time of f() behind the eviction pass, under the tuning scalars as set
+    auto behind_evict = [&](auto f) {
+        if (!evict) return time_launches(s, f, 5);
+        const float te = time_launches(s, [&] { launch_fused_tma(evict, 0, nullptr, s); }, 5);
+        return time_launches(s, [&] {
+            launch_fused_tma(evict, 0, nullptr, s);
+            f();
+        }, 5) - te;
+    };
     if (pl->mp_tma) {
-        set_tune_scalars(pl, true);
+        set_tune_scalars(pl, true);   // the M-pass as in an active body
         float tw[3] = {NAN, NAN, NAN};
         for (int waves = 1; waves <= 2; ++waves) {
             MpassTmaPlan* mp = make_mpass_candidate(pl, mpass_candidate(pl, waves, pl->tune_sc));
             if (!mp) continue;
-            tw[waves] = time_launches(s, [&] { launch_mpass_tma(mp, s); }, 3);
+            tw[waves] = behind_evict([&] { launch_mpass_tma(mp, s); });
             destroy_mpass_tma(mp);
         }
         if (tw[1] == tw[1] && tw[2] == tw[2] && tw[2] < 0.97f * tw[1]) choice.mp_waves = 2;
     }
+    set_tune_scalars(pl, false);
     if (pl->n_ap_tma > 0 && pl->ap_kind == APASS_FFMA) {
         // the A-pass reads only the done flag, which is clear before the first pasd_begin
-        float th[2] = {NAN, NAN};
-        for (int half = 0; half < 2; ++half) {
+        float th[3] = {NAN, NAN, NAN};
+        for (int var = 0; var < 3; ++var) {
             for (int q = 0; q < pl->n_ap_tma; ++q) {
                 const int def = pl->ap_tma_default_nc[q];
-                apass_tma_set_cols(pl->ap_tma[q], half ? def / 2 : def);
+                apass_tma_set_cols(pl->ap_tma[q], var == 1 ? def / 2 : def, var == 2 ? 2 : 1);
             }
-            th[half] = time_launches(s, [&] { launch_apass_all(pl, s); }, 3);
+            th[var] = behind_evict([&] { launch_apass_all(pl, s); });
         }
-        for (int q = 0; q < pl->n_ap_tma; ++q) apass_tma_set_cols(pl->ap_tma[q], pl->ap_tma_default_nc[q]);
-        if (th[0] == th[0] && th[1] == th[1] && th[1] < 0.97f * th[0]) choice.ap_half = 1;
+        for (int q = 0; q < pl->n_ap_tma; ++q) apass_tma_set_cols(pl->ap_tma[q], pl->ap_tma_default_nc[q], 1);
+        float best = th[0];
+        for (int var = 1; var < 3; ++var)
+            if (th[0] == th[0] && th[var] == th[var] && th[var] < 0.97f * th[0] && th[var] < best) {
+                best = th[var];
+                choice.ap_var = var;
+            }
     }
     cudaStreamSynchronize(s);
     cudaGetLastError();
+    if (evict) destroy_fused_tma(evict);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache.emplace(key, choice);
@@ -874,7 +925,9 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
         for (int n = 0; n < N; ++n) {
             const ModeGeom& g = pl->m[n];
             fi.mp_part[n] = pl->mp[n]; fi.I[n] = g.I; fi.R[n] = g.R; fi.Rp[n] = g.Rp; fi.Mred[n] = pl->Mred[n];
-            sa.m[n].polar_in_smem = polar_smem_bytes(maxRp, g.I) <= std::min<size_t>(pl->ctx->smem_optin, 200 * 1024);
+            sa.m[n].fp64_eig = (pl->p.flags & PASD_F_FP64_EIG) ? 1 : 0;
+            sa.m[n].polar_in_smem = polar_smem_bytes(maxRp, g.I, sa.m[n].fp64_eig != 0) <=
+                                    std::min<size_t>(pl->ctx->smem_optin, 200 * 1024);
         }
     }
     if (pl->want_tma) {
@@ -1026,17 +1079,21 @@ extern "C" pasd_status pasd_plan_info(const pasd_plan_t* pl, char* buf, size_t l
         if (pl->ap_small[n]) few += (few.empty() ? "" : ",") + std::to_string(n);
     }
     int mp_ctas = pl->mp_use_tma ? pl->mpt.cta_start[pl->N] : pl->mpa.cta_start[pl->N];
-    std::string apc;
-    for (int q = 0; q < pl->n_ap_tma; ++q) apc += (q ? "," : "") + std::to_string(apass_tma_cols(pl->ap_tma[q]));
+    std::string apc, aps;
+    for (int q = 0; q < pl->n_ap_tma; ++q) {
+        apc += (q ? "," : "") + std::to_string(apass_tma_cols(pl->ap_tma[q]));
+        aps += (q ? "," : "") + std::to_string(apass_tma_split(pl->ap_tma[q]));
+    }
     char tmp[1024];
     snprintf(tmp, sizeof(tmp),
              "{\"autotune\": \"%s\", \"fused\": {\"tma\": %d, \"ctas_per_sm\": %d, \"box\": [%s], \"regions\": %d, "
              "\"threads\": %d, \"candidates\": %d}, \"mpass\": {\"tma\": %d, \"waves\": %d, \"ctas\": %d}, "
-             "\"apass_cols_per_thread\": [%s], \"fewrow_modes\": [%s], \"launches_per_iter\": %d}",
+             "\"apass_cols_per_thread\": [%s], \"apass_row_groups\": [%s], \"fewrow_modes\": [%s], "
+             "\"launches_per_iter\": %d}",
              pl->tune_mode, pl->tma != nullptr || (!pl->arena && pl->want_tma) ? 1 : 0,
              pl->tuned ? pl->tuned_fused_k : pl->default_fused_k, box.c_str(), g.nregions,
              g.tma ? g.nthreads : FU_THREADS, pl->n_fcand, pl->mp_use_tma ? 1 : 0, pl->tuned_mp_waves, mp_ctas,
-             apc.c_str(), few.c_str(), pl->ap_launches + pl->mp_launches + 5);
+             apc.c_str(), aps.c_str(), few.c_str(), pl->ap_launches + pl->mp_launches + 5);
     if (std::strlen(tmp) + 1 > len) return fail(PASD_ERR_INVALID_ARG, "buffer too small");
     std::memcpy(buf, tmp, std::strlen(tmp) + 1);
     return PASD_OK;
@@ -1334,9 +1391,10 @@ extern "C" pasd_status pasd_state_get(pasd_plan_t* pl, int32_t item, int32_t mod
 // A plan can join a batch when all its streaming kernels are the bulk-copy FP32
 // ones that have batched forms (few-row modes run as their own launches).
 // A-pass launches without a batched form (the tensor-core A-pass of mixed
-// precision) run inside the batched body as launches of their own.
+// precision) run inside the batched body as launches of their own; the batched
+// polar and SVT kernels are the FP32 ones, so FP64 eigen-solve plans run alone.
 static bool batchable(const pasd_plan_t* pl) {
-    return pl->arena && pl->tma && pl->n_ap_plain == 0;
+    return pl->arena && pl->tma && pl->n_ap_plain == 0 && !(pl->p.flags & PASD_F_FP64_EIG);
 }
 
 struct BatchLaunch {
@@ -1464,7 +1522,7 @@ static bool batch_build(BatchExec& b, cudaStream_t s) {
     for (pasd_plan_t* pl : b.members) {
         for (int q = 0; q < pl->n_ap_tma; ++q)
             if (apass_batch_ctas(pl->ap_tma[q]) >= 0)
-                ap[{apass_batch_rp(pl->ap_tma[q]), apass_tma_cols(pl->ap_tma[q])}].push_back(ApItem{pl->ap_tma[q]});
+                ap[{apass_batch_rp(pl->ap_tma[q]), apass_tma_variant(pl->ap_tma[q])}].push_back(ApItem{pl->ap_tma[q]});
         vr[{vrot_launch_rb(pl->vr), vrot_launch_v4(pl->vr) ? 1 : 0}].push_back(VrItem{pl});
         fu[{fused_batch_order(pl->tma), fused_batch_threads(pl->tma)}].push_back(FuItem{pl->tma});
         if (pl->n_mp_big > 0) {

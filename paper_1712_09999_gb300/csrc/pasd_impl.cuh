@@ -29,6 +29,7 @@ namespace pasd {
 // remembered, so launches on the hot path make no driver call for it.
 void set_smem_attr(const void* kernel, int bytes);
 
+
 // Scalars that live on the device so that a captured iteration graph can be
 // replayed without host involvement.
 struct DevScalars {
@@ -102,7 +103,9 @@ void launch_apass_tma(const ApassTmaPlan* p, cudaStream_t s);
 // FMA kernel's columns per thread (0 for the tensor-core kernel); the setter
 // accepts the default or half of it (an autotuner candidate)
 int apass_tma_cols(const ApassTmaPlan* p);
-void apass_tma_set_cols(ApassTmaPlan* p, int nc);
+int apass_tma_split(const ApassTmaPlan* p);
+int apass_tma_variant(const ApassTmaPlan* p);   // columns per thread + 100 x row groups (batch key)
+void apass_tma_set_cols(ApassTmaPlan* p, int nc, int ks = 1);
 void destroy_apass_tma(ApassTmaPlan* p);
 // All modes in as few launches as possible (one per distinct padded rank);
 // returns the number of launches.
@@ -142,6 +145,7 @@ struct SmallModeArgs {
     float* scratch;        // 4 * I * Rp floats (U-step matrices when not in smem)
     int32_t* kept;         // device int (per mode)
     int polar_in_smem;     // 1: the U-step keeps its I x R matrices in shared memory
+    int fp64_eig;          // 1: the R x R eigen-solves in double (PASD_F_FP64_EIG)
 };
 
 struct SmallArgs {
@@ -169,7 +173,7 @@ struct FinalizeArgs {
     int R[PASD_MAXN], Rp[PASD_MAXN];
     float* Mred[PASD_MAXN];            // [I][Rp]
 };
-size_t polar_smem_bytes(int maxRp, int64_t maxI);
+size_t polar_smem_bytes(int maxRp, int64_t maxI, bool fp64);
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 void launch_init_state(DevScalars* sc, const float* T, double mu0, int N, float** U,
                        const int64_t* I, const int* R, const int* Rp, float** W, float** F,
@@ -383,7 +387,8 @@ int apass_batch_rp(const ApassTmaPlan* p);
 int apass_batch_ctas(const ApassTmaPlan* p);     // -1: not an FMA plan (not batched)
 size_t apass_batch_smem(const ApassTmaPlan* p);
 void apass_batch_fill(void* entry, const ApassTmaPlan* p, int start);
-void launch_apass_batched(int Rp, int nc, const void* entries, const int* block_entry, int grid, size_t smem,
+// every entry of one launch has padded rank Rp and variant `var` (apass_tma_variant)
+void launch_apass_batched(int Rp, int var, const void* entries, const int* block_entry, int grid, size_t smem,
                           cudaStream_t s);
 struct MpassPlainBatchEntry {   // the M-pass without bulk copies
     MpassArgs a;

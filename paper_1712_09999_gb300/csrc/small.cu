@@ -393,6 +393,110 @@ __device__ EigBufs sym_eig_orth(JacobiBufs& jb, int n, int ld, float tol, int ma
     return EigBufs{eb.A, out};
 }
 
+// ---------------------------------------------------------------------------
+// FP64 eigen-solve (PASD_F_FP64_EIG). The n x n float matrix in jb.A (an FP32
+// Gram matrix) is solved in double: the same round-robin cyclic Jacobi, with
+// correctly rounded rotations and the relative threshold 1e-13, then the
+// eigenvalues and eigenvectors are rounded to float into jb.A / jb.V for the
+// FP32 steps that follow (the double results stay in `dw` for
+// inv_sqrt_from_eig_d). `dw` holds jacobi_d_floats(ld) floats (8-byte aligned).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int jacobi_d_floats(int ld) { return 8 * ld * ld + 4 * ld; }
+struct EigBufsD {
+    EigBufs f;               // float copies (jb.A, jb.V)
+    const double* A;         // eigenvalues on the diagonal
+    const double* V;         // eigenvectors (columns)
+};
+__device__ EigBufsD sym_eig_fp64(JacobiBufs& jb, int n, int ld, float* dwf) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    double* A = reinterpret_cast<double*>(dwf);
+    double* V = A + ld * ld;
+    double* A2 = V + ld * ld;
+    double* V2 = A2 + ld * ld;
+    double* cs = V2 + ld * ld;
+    const double tol = 1e-13;
+    const int m = n + (n & 1);
+    for (int idx = t; idx < ld * ld; idx += nt) {
+        const int i = idx / ld, j = idx % ld;
+        A[idx] = (i < n && j < n) ? (double)jb.A[idx] : 0.0;
+        V[idx] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (m >= 2) {
+        for (int sweep = 0; sweep < 40; ++sweep) {
+            int need = 0;
+            for (int idx = t; idx < n * n; idx += nt) {
+                const int i = idx / n, j = idx % n;
+                if (i < j) {
+                    const double apq = A[i * ld + j];
+                    need |= (apq != 0.0 && fabs(apq) > tol * sqrt(fabs(A[i * ld + i] * A[j * ld + j])));
+                }
+            }
+            if (!__syncthreads_or(need)) break;
+            for (int round = 0; round < m - 1; ++round) {
+                int rot = 0;
+                if (t < m) {
+                    const int pi = rr_partner(t, round, m);
+                    const int p = min(t, pi), q = max(t, pi);
+                    const double app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
+                    double c = 1.0, sn = 0.0;
+                    if (apq != 0.0 && fabs(apq) > tol * sqrt(fabs(app * aqq))) {
+                        const double theta = (aqq - app) / (2.0 * apq);
+                        const double tt = fabs(theta) > 1e150 ? 0.5 / theta
+                                                              : copysign(1.0 / (fabs(theta) + sqrt(fma(theta, theta, 1.0))), theta);
+                        c = 1.0 / sqrt(fma(tt, tt, 1.0));
+                        sn = tt * c;
+                        rot = 1;
+                    }
+                    cs[2 * t] = c;
+                    cs[2 * t + 1] = (t == p) ? -sn : sn;
+                }
+                if (!__syncthreads_or(rot)) continue;
+                for (int idx = t; idx < m * m; idx += nt) {
+                    const int i = idx / m, j = idx % m;
+                    const int pi = rr_partner(i, round, m), pj = rr_partner(j, round, m);
+                    const double ci = cs[2 * i], si = cs[2 * i + 1], cj = cs[2 * j], sj = cs[2 * j + 1];
+                    // symmetric in (i, j) with explicit rounding: A stays exactly symmetric
+                    const double t1 = __dmul_rn(__dmul_rn(ci, cj), A[i * ld + j]);
+                    const double t2 = __dmul_rn(__dmul_rn(ci, sj), A[i * ld + pj]);
+                    const double t3 = __dmul_rn(__dmul_rn(si, cj), A[pi * ld + j]);
+                    const double t4 = __dmul_rn(__dmul_rn(si, sj), A[pi * ld + pj]);
+                    double v = __dadd_rn(__dadd_rn(t1, __dadd_rn(t2, t3)), t4);
+                    if (pi == j && si != 0.0) v = 0.0;
+                    A2[i * ld + j] = v;
+                    if (i < n) V2[i * ld + j] = fma(V[i * ld + pj], sj, V[i * ld + j] * cj);
+                }
+                __syncthreads();
+                double* tA = A; A = A2; A2 = tA;
+                double* tV = V; V = V2; V2 = tV;
+            }
+        }
+    }
+    for (int idx = t; idx < ld * ld; idx += nt) {
+        jb.A[idx] = (float)A[idx];
+        jb.V[idx] = (float)V[idx];
+    }
+    __syncthreads();
+    return EigBufsD{EigBufs{jb.A, jb.V}, A, V};
+}
+
+// inv_sqrt_from_eig on the double eigen-system, rounded to float once.
+__device__ void inv_sqrt_from_eig_d(const double* D, const double* Q, int n, int ld, float* Z) {
+    const int n4 = (n + 3) & ~3;
+    for (int idx = threadIdx.x; idx < n4 * n4; idx += blockDim.x) {
+        const int i = idx / n4, j = idx % n4;
+        double s = 0.0;
+        if (i < n && j < n)
+            for (int k = 0; k < n; ++k) {
+                const double w = D[k * ld + k];
+                const double f = w > 0.0 ? 1.0 / sqrt(w) : 0.0;
+                s = fma(Q[i * ld + k] * f, Q[j * ld + k], s);
+            }
+        Z[i * ld + j] = (float)s;
+    }
+    __syncthreads();
+}
+
 // Row stride of the I x R matrices of the U-step in shared memory: a multiple of
 // 4 with (stride / 4) odd, so float4 rows of consecutive rows hit distinct banks.
 __host__ __device__ inline int polar_ld(int Rp) { return ((Rp / 4) & 1) ? Rp : Rp + 4; }
@@ -403,6 +507,7 @@ __host__ __device__ inline int polar_ld(int Rp) { return ((Rp / 4) & 1) ? Rp : R
 // (also the scratch of the eigenvector re-orthonormalisation: TILE_SCRATCH floats)
 __host__ __device__ inline int svt_red_floats(int Rp) { return Rp * Rp > TILE_SCRATCH ? Rp * Rp : TILE_SCRATCH; }
 
+template <bool FP64>
 __device__ __forceinline__ void svt_body(const SmallModeArgs& m, DevScalars* sc, const int mode) {
     if (sc->done) return;
     const double mu = sc->mu;
@@ -453,7 +558,8 @@ __device__ __forceinline__ void svt_body(const SmallModeArgs& m, DevScalars* sc,
         __syncthreads();
     }
     // 2. eigen-decomposition
-    const EigBufs eb = sym_eig_orth(jb, R, ld, 1e-6f, 30, red);
+    const EigBufs eb = FP64 ? sym_eig_fp64(jb, R, ld, red + svt_red_floats(Rp)).f
+                            : sym_eig_orth(jb, R, ld, 1e-6f, 30, red);
     const float* Ae = eb.A;
     const float* Ve = eb.V;
     sort_desc(Ae, R, ld, perm);
@@ -507,13 +613,14 @@ __device__ __forceinline__ void svt_body(const SmallModeArgs& m, DevScalars* sc,
     tile_AB(m.U, Rp, Rp, Smat, ld, Rp, m.I, m.Urot, Rp, false);
 }
 
+template <bool FP64>
 __global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel(SmallArgs sa) {
-    svt_body(sa.m[blockIdx.x], sa.sc, blockIdx.x);
+    svt_body<FP64>(sa.m[blockIdx.x], sa.sc, blockIdx.x);
 }
 // one CTA per (solve, mode) entry of the batch
 __global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel_batched(const SmallBatchEntry* e) {
     const SmallBatchEntry& x = e[blockIdx.x];
-    svt_body(x.m, x.sc, x.mode);
+    svt_body<false>(x.m, x.sc, x.mode);
 }
 
 // ---------------------------------------------------------------------------
@@ -526,6 +633,7 @@ __global__ void __launch_bounds__(SM_THREADS, 1) svt_kernel_batched(const SmallB
 // A closing Newton-Schulz step re-orthonormalises U. The I x R matrices live in
 // shared memory when they fit, else in the global scratch.
 // ---------------------------------------------------------------------------
+template <bool FP64>
 __device__ __forceinline__ void polar_body(const SmallModeArgs& m, DevScalars* sc, const int mode) {
     if (sc->done) return;
     const int R = m.R, Rp = m.Rp, ld = Rp;
@@ -538,6 +646,7 @@ __device__ __forceinline__ void polar_body(const SmallModeArgs& m, DevScalars* s
     float* big = tsc + TILE_SCRATCH;            // 4 x I x LD when it fits
     const bool in_smem = m.polar_in_smem != 0;
     const int LD = in_smem ? polar_ld(Rp) : Rp;
+    float* dw = in_smem ? big + 4 * I * LD : big; // FP64 eigen-solve workspace (PASD_F_FP64_EIG)
     float* Mw = in_smem ? big : m.scratch;      // [P1 | X]
     float* Pw = Mw + I * LD;                    // M in the W basis
     float* Bw = Pw + I * LD;                    // (U W)[:, s:], then (I - P1 P1^T) of it
@@ -585,10 +694,13 @@ __device__ __forceinline__ void polar_body(const SmallModeArgs& m, DevScalars* s
     if (s > 0) {
         // B1 = M^T M, Z1 = B1^{-1/2}, P1 = M Z1
         tile_AtB(Pw, LD, s, Pw, LD, s, I, jb.A, ld, true, tsc);
-        const EigBufs eb = sym_eig_orth(jb, s, ld, 1e-6f, 30, tsc);
-        const float* Ae = eb.A;
-        const float* Ve = eb.V;
-        inv_sqrt_from_eig(Ae, Ve, s, ld, Z);
+        if (FP64) {
+            const EigBufsD ed = sym_eig_fp64(jb, s, ld, dw);
+            inv_sqrt_from_eig_d(ed.A, ed.V, s, ld, Z);
+        } else {
+            const EigBufs eb = sym_eig_orth(jb, s, ld, 1e-6f, 30, tsc);
+            inv_sqrt_from_eig(eb.A, eb.V, s, ld, Z);
+        }
         tile_AB(Pw, LD, s, Z, ld, s4, I, Mw, LD, false);
         __syncthreads();
     }
@@ -601,10 +713,13 @@ __device__ __forceinline__ void polar_body(const SmallModeArgs& m, DevScalars* s
             __syncthreads();
         }
         tile_AtB(Bw, LD, q, Bw, LD, q, I, jb.A, ld, true, tsc);
-        const EigBufs eb = sym_eig_orth(jb, q, ld, 1e-6f, 30, tsc);
-        const float* Ae = eb.A;
-        const float* Ve = eb.V;
-        inv_sqrt_from_eig(Ae, Ve, q, ld, Z);
+        if (FP64) {
+            const EigBufsD ed = sym_eig_fp64(jb, q, ld, dw);
+            inv_sqrt_from_eig_d(ed.A, ed.V, q, ld, Z);
+        } else {
+            const EigBufs eb = sym_eig_orth(jb, q, ld, 1e-6f, 30, tsc);
+            inv_sqrt_from_eig(eb.A, eb.V, q, ld, Z);
+        }
         tile_AB(Bw, LD, q, Z, ld, q4, I, Xb, LD, false);
         __syncthreads();
         for (int idx = threadIdx.x; idx < (int)I * q; idx += blockDim.x) {
@@ -624,54 +739,72 @@ __device__ __forceinline__ void polar_body(const SmallModeArgs& m, DevScalars* s
     tile_AB(Mw, LD, R, Z, ld, Rp, I, m.U, Rp, false);
 }
 
+template <bool FP64>
 __global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
-    polar_body(sa.m[blockIdx.x], sa.sc, blockIdx.x);
+    polar_body<FP64>(sa.m[blockIdx.x], sa.sc, blockIdx.x);
 }
 __global__ void __launch_bounds__(SM_THREADS) polar_kernel_batched(const SmallBatchEntry* e) {
     const SmallBatchEntry& x = e[blockIdx.x];
-    polar_body(x.m, x.sc, x.mode);
+    polar_body<false>(x.m, x.sc, x.mode);
 }
 
 static size_t small_base_floats(int maxRp) {
     const int ld = maxRp;
     return (size_t)jacobi_floats(ld) + 2 * (size_t)ld * ld + TILE_SCRATCH;
 }
-static size_t svt_smem_bytes(int maxRp) {
+static size_t svt_smem_bytes(int maxRp, bool fp64) {
     const int ld = maxRp;
-    return 4 * ((size_t)jacobi_floats(ld) + (size_t)ld * ld + 2 * (size_t)ld + svt_red_floats(maxRp));
+    return 4 * ((size_t)jacobi_floats(ld) + (size_t)ld * ld + 2 * (size_t)ld + svt_red_floats(maxRp) +
+                (fp64 ? jacobi_d_floats(ld) : 0));
 }
 // Bytes of shared memory the U-step needs with its I x R matrices resident.
-size_t polar_smem_bytes(int maxRp, int64_t maxI) {
-    return 4 * (small_base_floats(maxRp) + 4 * (size_t)maxI * polar_ld(maxRp));
+size_t polar_smem_bytes(int maxRp, int64_t maxI, bool fp64) {
+    return 4 * (small_base_floats(maxRp) + 4 * (size_t)maxI * polar_ld(maxRp) + (fp64 ? jacobi_d_floats(maxRp) : 0));
 }
 
 size_t svt_launch_smem(const SmallArgs& a) {
     int maxRp = 4;
-    for (int n = 0; n < a.N; ++n) maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
-    return svt_smem_bytes(maxRp);
+    bool fp64 = false;
+    for (int n = 0; n < a.N; ++n) {
+        maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
+        fp64 = fp64 || a.m[n].fp64_eig;
+    }
+    return svt_smem_bytes(maxRp, fp64);
 }
 
 size_t polar_launch_smem(const SmallArgs& a) {
     int maxRp = 4;
     int64_t maxI = 1;
-    bool any_smem = false;
+    bool any_smem = false, fp64 = false;
     for (int n = 0; n < a.N; ++n) {
         maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
+        fp64 = fp64 || a.m[n].fp64_eig;
         if (a.m[n].polar_in_smem) { any_smem = true; maxI = a.m[n].I > maxI ? a.m[n].I : maxI; }
     }
-    return any_smem ? polar_smem_bytes(maxRp, maxI) : 4 * small_base_floats(maxRp);
+    return any_smem ? polar_smem_bytes(maxRp, maxI, fp64)
+                    : 4 * (small_base_floats(maxRp) + (fp64 ? jacobi_d_floats(maxRp) : 0));
 }
 
 void launch_svt(const SmallArgs& a, cudaStream_t s) {
     const size_t smem = svt_launch_smem(a);
-    set_smem_attr((const void*)svt_kernel, (int)smem);
-    svt_kernel<<<a.N, SM_THREADS, smem, s>>>(a);
+    if (a.m[0].fp64_eig) {
+        set_smem_attr((const void*)svt_kernel<true>, (int)smem);
+        svt_kernel<true><<<a.N, SM_THREADS, smem, s>>>(a);
+    } else {
+        set_smem_attr((const void*)svt_kernel<false>, (int)smem);
+        svt_kernel<false><<<a.N, SM_THREADS, smem, s>>>(a);
+    }
 }
 
 void launch_polar(const SmallArgs& a, cudaStream_t s) {
     const size_t smem = polar_launch_smem(a);
-    set_smem_attr((const void*)polar_kernel, (int)smem);
-    polar_kernel<<<a.N, SM_THREADS, smem, s>>>(a);
+    if (a.m[0].fp64_eig) {
+        set_smem_attr((const void*)polar_kernel<true>, (int)smem);
+        polar_kernel<true><<<a.N, SM_THREADS, smem, s>>>(a);
+    } else {
+        set_smem_attr((const void*)polar_kernel<false>, (int)smem);
+        polar_kernel<false><<<a.N, SM_THREADS, smem, s>>>(a);
+    }
 }
 
 void launch_polar_batched(const SmallBatchEntry* e, int n, size_t smem, cudaStream_t s) {

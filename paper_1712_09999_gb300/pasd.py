@@ -23,6 +23,7 @@ ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE = -1, -2, -3, -4
 ERR_TIMEOUT, ERR_BUSY, ERR_UNKNOWN_TICKET, ERR_UNSUPPORTED = -5, -6, -7, -8
 PREC_FP32, PREC_MIXED = 0, 1
 F_SKIP_IDLE = 1
+F_FP64_EIG = 2
 STOP_INF_ABS, STOP_FRO_REL, STOP_FIXED_ITERS = 0, 1, 2
 STATE_U, STATE_A, STATE_W, STATE_SIGMA, STATE_F, STATE_E, STATE_Y, STATE_MU, STATE_KEPT, STATE_TRACE = range(10)
 

@@ -275,6 +275,77 @@ def test_autotuner_choice_is_cached_reported_and_harmless(env, monkeypatch):
     assert rel(E.cpu().numpy(), outs[0][1].cpu().numpy()) <= 1e-6
 
 
+@pytest.mark.parametrize("dims,ranks", [((64, 48, 40), (8, 8, 8)), ((40, 36, 32), (20, 20, 20)),
+                                         ((24, 20, 16), (12, 12, 12))])
+def test_apass_variants_agree_and_batch(env, monkeypatch, dims, ranks):
+    # The FP32 A-pass variants the autotuner picks from (half the columns per
+    # thread; each stage's rows split between two thread groups whose sums are
+    # added at the end) only regroup the partial sums of A = U^T G: the kept counts
+    # of every body equal the default's and L, E agree to rounding. A solve on the
+    # split variant served in the batched executor equals the same solve alone.
+    torch, P, ctx = env
+    pr = synth.planted(dims, (4, 4, 4), 0.1, 11, scale="std", amp=5.0)
+    params = P.make_params(dims, ranks, stop=P.STOP_FIXED_ITERS, max_iter=150)
+    T = torch.from_numpy(pr.T).cuda()
+    res = {}
+    for var in ("0", "1", "2"):
+        monkeypatch.setenv("PASD_TUNE_APASS", var)
+        plan, _ = P.pasd_plan(ctx, params)
+        L, E = torch.empty_like(T), torch.empty_like(T)
+        r = P.pasd_solve(plan, T, L, E)
+        info = P.pasd_plan_info(plan)
+        trace = np.zeros((r.iters, P.TRACE_STRIDE))
+        P.pasd_state_get(plan, P.STATE_TRACE, 0, trace)
+        res[var] = (L, E, trace[:, 5:8].astype(int).tolist())
+        assert all(g == (2 if var == "2" else 1) for g in info["apass_row_groups"])
+        if var == "2":
+            L2, E2 = torch.empty_like(T), torch.empty_like(T)
+            (st, rr), = _serve_all(P, ctx, [(plan, T, L2, E2)])
+            assert st == P.OK and rr.batched == 1
+            assert torch.equal(L2, L) and torch.equal(E2, E)
+        P.pasd_plan_destroy(plan)
+    monkeypatch.delenv("PASD_TUNE_APASS")
+    L0, E0, k0 = res["0"]
+    for var in ("1", "2"):
+        L, E, k = res[var]
+        assert k == k0
+        assert rel(L.cpu().numpy(), L0.cpu().numpy()) <= 1e-5
+        assert rel(E.cpu().numpy(), E0.cpu().numpy()) <= 1e-5
+
+
+# --- FP64 eigen-solves -------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,tucker,ranks,rho,stop,iters", [
+    ((24, 20, 16), (3, 3, 2), (4, 4, 3), 0.1, 0, 1000),
+    ((64, 48, 40), (4, 4, 4), (20, 20, 20), 0.1, 1, 1000),
+    ((12, 10, 3, 20), (2, 2, 2, 2), (3, 3, 2, 4), 0.1, 0, 1000),
+    ((100, 100, 100), (40, 40, 40), (48, 48, 48), 0.02, 2, 250),   # rank bucket 48, a non-recovering cell
+])
+def test_fp64_eigensolves_match_oracle(env, dims, tucker, ranks, rho, stop, iters):
+    # PASD_F_FP64_EIG: the R x R Jacobi solves of the SVT and the U-step in double.
+    # Same bar as the FP32 path against the FP64 oracle.
+    torch, P, ctx = env
+    if rho == 0.02:
+        pr = synth.table1(dims, rho, seed=900 + tucker[0], r=tucker[0])
+    else:
+        pr = synth.planted(dims, tucker, rho, 21, scale="std", amp=5.0)
+    lam = O.paper_lambdas(dims)
+    ref = O.pasd(pr.T, O.Params(ranks=ranks, lambdas=lam, stop=STOPS[stop], max_iter=iters,
+                                tol=1e-6 if stop == 1 else 1e-5))
+    tie_margin(ref.trace, lam, f"fp64 eig {dims}")
+    g = _gpu(env, pr.T, ranks, stop=stop, max_iter=iters, tol=1e-6 if stop == 1 else 0.0, flags=P.F_FP64_EIG)
+    _check(g, ref, len(dims))
+
+
+def test_fp64_eigensolves_rank_limit(env):
+    torch, P, ctx = env
+    plan, _ = P.pasd_plan(ctx, P.make_params((64, 60, 58), (56, 56, 56), flags=P.F_FP64_EIG))
+    P.pasd_plan_destroy(plan)
+    with pytest.raises(P.PasdError) as ei:
+        P.pasd_plan(ctx, P.make_params((64, 60, 58), (57, 8, 8), flags=P.F_FP64_EIG))
+    assert ei.value.status == P.ERR_UNSUPPORTED
+
+
 # --- failure paths of the ABI -------------------------------------------------------
 
 def test_invalid_weights_are_rejected(env):
