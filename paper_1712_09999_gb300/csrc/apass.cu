@@ -500,11 +500,13 @@ __device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const A
 
     // thread lt of its group: columns lt + NT q of the task (q < NC); several columns
     // per thread amortise each broadcast read of a U row over NC x RP multiply-adds
-    float acc[NC][RP];
+    // accumulators in pairs (r, r + 1): each paired FMA (__ffma2_rn) does two of
+    // the multiply-adds, each rounded as fmaf would, in one instruction
+    float2 acc2[NC][RP / 2];
 #pragma unroll
     for (int q = 0; q < NC; ++q)
 #pragma unroll
-        for (int r = 0; r < RP; ++r) acc[q][r] = 0.f;
+        for (int r = 0; r < RP / 2; ++r) acc2[q][r] = make_float2(0.f, 0.f);
     bool failed = false;
     int fail_kc = 0;
     for (int kc = 0; kc < nk; ++kc) {
@@ -523,19 +525,21 @@ __device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const A
             constexpr int KR = AP_BK / KS;
 #pragma unroll 2
             for (int kk = grp * KR; kk < grp * KR + KR; ++kk) {
-                float g[NC];
+                float2 g[NC];
 #pragma unroll
-                for (int q = 0; q < NC; ++q) g[q] = gs[kk * BN + col[q]];
+                for (int q = 0; q < NC; ++q) {
+                    const float v = gs[kk * BN + col[q]];
+                    g[q] = make_float2(v, v);
+                }
                 const float4* u4 = reinterpret_cast<const float4*>(us + kk * RP);
 #pragma unroll
                 for (int r4 = 0; r4 < RP / 4; ++r4) {
                     const float4 u = u4[r4];
+                    const float2 uxy = make_float2(u.x, u.y), uzw = make_float2(u.z, u.w);
 #pragma unroll
                     for (int q = 0; q < NC; ++q) {
-                        acc[q][4 * r4 + 0] = fmaf(g[q], u.x, acc[q][4 * r4 + 0]);
-                        acc[q][4 * r4 + 1] = fmaf(g[q], u.y, acc[q][4 * r4 + 1]);
-                        acc[q][4 * r4 + 2] = fmaf(g[q], u.z, acc[q][4 * r4 + 2]);
-                        acc[q][4 * r4 + 3] = fmaf(g[q], u.w, acc[q][4 * r4 + 3]);
+                        acc2[q][2 * r4 + 0] = __ffma2_rn(g[q], uxy, acc2[q][2 * r4 + 0]);
+                        acc2[q][2 * r4 + 1] = __ffma2_rn(g[q], uzw, acc2[q][2 * r4 + 1]);
                     }
                 }
             }
@@ -556,12 +560,12 @@ __device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const A
 #pragma unroll
                     for (int r4 = 0; r4 < RP / 4; ++r4) {
                         const float4 u = u4[r4];
+                        const float2 uxy = make_float2(u.x, u.y), uzw = make_float2(u.z, u.w);
 #pragma unroll
                         for (int q = 0; q < NC; ++q) {
-                            acc[q][4 * r4 + 0] = fmaf(gq[q][kk], u.x, acc[q][4 * r4 + 0]);
-                            acc[q][4 * r4 + 1] = fmaf(gq[q][kk], u.y, acc[q][4 * r4 + 1]);
-                            acc[q][4 * r4 + 2] = fmaf(gq[q][kk], u.z, acc[q][4 * r4 + 2]);
-                            acc[q][4 * r4 + 3] = fmaf(gq[q][kk], u.w, acc[q][4 * r4 + 3]);
+                            const float2 gg = make_float2(gq[q][kk], gq[q][kk]);
+                            acc2[q][2 * r4 + 0] = __ffma2_rn(gg, uxy, acc2[q][2 * r4 + 0]);
+                            acc2[q][2 * r4 + 1] = __ffma2_rn(gg, uzw, acc2[q][2 * r4 + 1]);
                         }
                     }
                 }
@@ -582,6 +586,14 @@ __device__ __forceinline__ void apass_tma_body(const ApassTmaMaps& maps, const A
         return;
     }
     __syncthreads();   // every stage consumed and no copy in flight: smem is free for the epilogue
+    float acc[NC][RP];
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+#pragma unroll
+        for (int r = 0; r < RP / 2; ++r) {
+            acc[q][2 * r] = acc2[q][r].x;
+            acc[q][2 * r + 1] = acc2[q][r].y;
+        }
     if (KS == 2) {
         // group 1's sums to group 0 ([q][lt][RP]), added after group 0's own
         float* hand = smem;

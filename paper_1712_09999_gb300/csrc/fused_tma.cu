@@ -204,11 +204,18 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
         for (int n = 0; n < N; ++n) o[n] = tile_o[st][n];
 
         // ---- Z_n for the thread's 8 elements (j = d2 * 4 + d1), rank sp_n ----
+        // Z_n in pairs (z2) for the modes before the last, whose products pair up
+        // along the contiguous mode; the last mode's chains stay scalar (z)
         float z[N][8];
+        float2 z2[N][4];
 #pragma unroll
         for (int n = 0; n < N; ++n)
 #pragma unroll
             for (int j = 0; j < 8; ++j) z[n][j] = 0.f;
+#pragma unroll
+        for (int n = 0; n < N; ++n)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) z2[n][j] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int n = 0; n < N; ++n) {
             const int h = sp[n];
@@ -249,15 +256,14 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
                         const float w0s[4] = {w0.x, w0.y, w0.z, w0.w}, w1s[4] = {w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
+                            // paired FMAs: each lane rounds as fmaf, in the same order
                             const float4 a = *reinterpret_cast<const float4*>(Ab + (r + kk) * rs);
-                            z[n][0] = fmaf(w0s[kk], a.x, z[n][0]);
-                            z[n][1] = fmaf(w0s[kk], a.y, z[n][1]);
-                            z[n][2] = fmaf(w0s[kk], a.z, z[n][2]);
-                            z[n][3] = fmaf(w0s[kk], a.w, z[n][3]);
-                            z[n][4] = fmaf(w1s[kk], a.x, z[n][4]);
-                            z[n][5] = fmaf(w1s[kk], a.y, z[n][5]);
-                            z[n][6] = fmaf(w1s[kk], a.z, z[n][6]);
-                            z[n][7] = fmaf(w1s[kk], a.w, z[n][7]);
+                            const float2 axy = make_float2(a.x, a.y), azw = make_float2(a.z, a.w);
+                            const float2 w0 = make_float2(w0s[kk], w0s[kk]), w1 = make_float2(w1s[kk], w1s[kk]);
+                            z2[n][0] = __ffma2_rn(w0, axy, z2[n][0]);
+                            z2[n][1] = __ffma2_rn(w0, azw, z2[n][1]);
+                            z2[n][2] = __ffma2_rn(w1, axy, z2[n][2]);
+                            z2[n][3] = __ffma2_rn(w1, azw, z2[n][3]);
                         }
                     }
                 } else {
@@ -267,19 +273,26 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
                         const float ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
+                            const float2 w2 = make_float2(ws[kk], ws[kk]);
 #pragma unroll
                             for (int d2 = 0; d2 < 2; ++d2) {
                                 const float4 a = *reinterpret_cast<const float4*>(Ab + (r + kk) * rs + d2 * s2);
-                                z[n][d2 * 4 + 0] = fmaf(ws[kk], a.x, z[n][d2 * 4 + 0]);
-                                z[n][d2 * 4 + 1] = fmaf(ws[kk], a.y, z[n][d2 * 4 + 1]);
-                                z[n][d2 * 4 + 2] = fmaf(ws[kk], a.z, z[n][d2 * 4 + 2]);
-                                z[n][d2 * 4 + 3] = fmaf(ws[kk], a.w, z[n][d2 * 4 + 3]);
+                                z2[n][2 * d2] = __ffma2_rn(w2, make_float2(a.x, a.y), z2[n][2 * d2]);
+                                z2[n][2 * d2 + 1] = __ffma2_rn(w2, make_float2(a.z, a.w), z2[n][2 * d2 + 1]);
                             }
                         }
                     }
                 }
             }
         }
+
+#pragma unroll
+        for (int n = 0; n < N - 1; ++n)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                z[n][2 * j] = z2[n][j].x;
+                z[n][2 * j + 1] = z2[n][j].y;
+            }
 
         if (output) {
             // L = sum_n alpha_n Z_n / sum alpha_n, stored directly (once per solve)
