@@ -1497,9 +1497,8 @@ static void batch_release(BatchExec& b) {
 
 // Rebuilds the device tables and the body graph for the current members.
 static bool batch_build(BatchExec& b, cudaStream_t s) {
-    batch_release(b);
     b.host.clear();
-    if (b.members.empty()) return true;
+    if (b.members.empty()) { batch_release(b); return true; }
     // polar / SVT: one CTA per (solve, mode)
     {
         std::vector<SmallBatchEntry> e;
@@ -1566,17 +1565,34 @@ static bool batch_build(BatchExec& b, cudaStream_t s) {
         },
         [](const FiItem&) { return (size_t)0; }, [](const int&, BatchLaunch&) {});
     if (b.host.size() > b.dev_bytes) {
+        // grows by doubling: cudaFree waits for the whole device, other batches included
+        const size_t want = std::max(b.host.size(), 2 * b.dev_bytes);
         if (b.dev) cudaFree(b.dev);
         b.dev = nullptr;
         b.dev_bytes = 0;
-        if (cudaMalloc(&b.dev, b.host.size()) != cudaSuccess) return false;
-        b.dev_bytes = b.host.size();
+        if (cudaMalloc(&b.dev, want) != cudaSuccess) return false;
+        b.dev_bytes = want;
+        batch_release(b);   // the old graph's launches point into the freed table
     }
     if (cudaMemcpyAsync(b.dev, b.host.data(), b.host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) return false;
     if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+    cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return false;
     launch_batch_body(b, s);
-    if (cudaStreamEndCapture(s, &b.graph) != cudaSuccess) return false;
+    if (cudaStreamEndCapture(s, &g) != cudaSuccess) return false;
+    // same launches as the graph in use (kernels and order), new grids and entries:
+    // update the executable graph in place instead of instantiating a new one
+    if (b.exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(b.exec, g, &info) == cudaSuccess) {
+            cudaGraphDestroy(b.graph);
+            b.graph = g;
+            return true;
+        }
+        cudaGetLastError();
+        batch_release(b);
+    }
+    b.graph = g;
     return cudaGraphInstantiate(&b.exec, b.graph, 0) == cudaSuccess;
 }
 
