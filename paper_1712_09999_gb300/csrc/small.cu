@@ -113,7 +113,7 @@ __device__ __forceinline__ int pair_rotation(const float* A, int ld, int i, int 
 }
 
 // pc: m ints, cs: 2 m floats of shared scratch for the round's rotations.
-__device__ EigBufs block_jacobi(float* A, float* V, float* A2, float* V2, int* pc, float* cs, int n, int ld,
+__device__ __forceinline__ EigBufs block_jacobi_body(float* A, float* V, float* A2, float* V2, int* pc, float* cs, int n, int ld,
                                 float tol, int max_sweeps) {
     const int t = threadIdx.x, nt = blockDim.x;
     const int m = n + (n & 1);
@@ -170,11 +170,11 @@ __device__ EigBufs block_jacobi(float* A, float* V, float* A2, float* V2, int* p
     return EigBufs{A, V};
 }
 
-// Symmetric eigen-solve of the n x n matrix in A (block-wide Jacobi; a single
-// warp running the same rounds measured about twice as slow on 20 x 20 here).
-__device__ __forceinline__ EigBufs sym_eig(float* A, float* V, float* A2, float* V2, int* pc, float* cs,
-                                           int n, int ld, float tol, int max_sweeps) {
-    return block_jacobi(A, V, A2, V2, pc, cs, n, ld, tol, max_sweeps);
+// Out-of-line copy for the U-step, which runs two eigen-solves; the SVT inlines
+// the body (one call site, and the call costs it more than the code size).
+__device__ __noinline__ EigBufs block_jacobi(float* A, float* V, float* A2, float* V2, int* pc, float* cs, int n,
+                                            int ld, float tol, int max_sweeps) {
+    return block_jacobi_body(A, V, A2, V2, pc, cs, n, ld, tol, max_sweeps);
 }
 
 // Descending order of the diagonal of A (n x n, ld): perm[rank] = index.
@@ -195,20 +195,23 @@ __device__ void sort_desc(const float* A, int n, int ld, int* perm) {
     __syncthreads();
 }
 
+// The helpers below are out of line (__noinline__): the U-step calls them several
+// times each, and inlined copies made that kernel wait on instruction fetch.
+//
 // C (na x nb, ldc) = X[:, :na]^T Y[:, :nb] over `rows` rows (row strides ldx,
 // ldy, multiples of 4; 16-byte aligned bases). The entries of C up to the next
 // multiples of 4 are written as zeros. 4 x 4 register tiles, rows split S ways,
 // split sums added in a fixed order. With `sym` (X == Y, na == nb) only tiles
 // on and above the diagonal are formed and mirrored. Ends with a barrier.
-__device__ void tile_AtB(const float* X, int ldx, int na, const float* Y, int ldy, int nb, int64_t rows,
+__device__ __noinline__ void tile_AtB(const float* X, int ldx, int na, const float* Y, int ldy, int nb, int64_t rows,
                          float* C, int ldc, bool sym, float* scratch) {
     const int t = threadIdx.x, nt = blockDim.x;
     const int ta = (na + 3) / 4, tb = (nb + 3) / 4;
     const int ntile = sym ? ta * (ta + 1) / 2 : ta * tb;
-    int S = 1;
-    while (ntile * S * 2 <= TILE_SCRATCH / 16 && ntile * S * 2 <= nt && S * 2 <= rows) S *= 2;
+    int S = 1, lgS = 0;
+    while (ntile * S * 2 <= TILE_SCRATCH / 16 && ntile * S * 2 <= nt && S * 2 <= rows) { S *= 2; ++lgS; }
     for (int w = t; w < ntile * S; w += nt) {
-        const int tile = w / S, sp = w % S;
+        const int tile = w >> lgS, sp = w & (S - 1);
         int a4, b4;
         if (sym) {
             a4 = 0;
@@ -219,7 +222,7 @@ __device__ void tile_AtB(const float* X, int ldx, int na, const float* Y, int ld
             a4 = tile / tb;
             b4 = tile % tb;
         }
-        const int r0 = (int)(rows * sp / S), r1 = (int)(rows * (sp + 1) / S);
+        const int r0 = (int)((rows * sp) >> lgS), r1 = (int)((rows * (sp + 1)) >> lgS);   // S is a power of two
         float acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -254,8 +257,17 @@ __device__ void tile_AtB(const float* X, int ldx, int na, const float* Y, int ld
         const int a4 = a >> 2, b4 = b >> 2;
         const int tile = sym ? a4 * ta - a4 * (a4 - 1) / 2 + (b4 - a4) : a4 * tb + b4;
         const float* src = scratch + (size_t)tile * S * 16 + (a & 3) * 4 + (b & 3);
+        // the split sums in order, loaded eight at a time ahead of their adds
         float s = 0.f;
-        for (int sp = 0; sp < S; ++sp) s += src[sp * 16];
+        int sp = 0;
+        for (; sp + 8 <= S; sp += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = src[(sp + u) * 16];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
+        }
+        for (; sp < S; ++sp) s += src[sp * 16];
         C[a * ldc + b] = s;
         if (sym) C[b * ldc + a] = s;
     }
@@ -265,7 +277,7 @@ __device__ void tile_AtB(const float* X, int ldx, int na, const float* Y, int ld
 // Y[:, :cols] = X[:, :inner] S  (or Y -= X S with `sub`), rows x cols, cols a
 // multiple of 4; S is inner x cols (row stride lds, a multiple of 4). One
 // thread per row and group of 4 columns. No barrier.
-__device__ void tile_AB(const float* X, int ldx, int inner, const float* S, int lds, int cols, int64_t rows,
+__device__ __noinline__ void tile_AB(const float* X, int ldx, int inner, const float* S, int lds, int cols, int64_t rows,
                         float* Y, int ldy, bool sub) {
     const int c4n = cols / 4;
     const int tot = (int)rows * c4n;
@@ -314,12 +326,13 @@ __device__ void tile_AB(const float* X, int ldx, int inner, const float* S, int 
 // rotation at all V = I and the step returns I exactly. `scratch` holds
 // TILE_SCRATCH floats.
 constexpr int kOrthMinN = 24;
+template <bool INLINE_SOLVE = false>
 __device__ EigBufs sym_eig_orth(JacobiBufs& jb, int n, int ld, float tol, int max_sweeps, float* scratch);
 
 // Z = Q diag(w^{-1/2}) Q^T for the n x n eigen-system (Q columns, eigenvalues w
 // on the diagonal of D); entries up to the next multiple of 4 are zero.
 // Nonpositive eigenvalues (rank loss) map to 0. Ends with a barrier.
-__device__ void inv_sqrt_from_eig(const float* D, const float* Q, int n, int ld, float* Z) {
+__device__ __noinline__ void inv_sqrt_from_eig(const float* D, const float* Q, int n, int ld, float* Z) {
     const int n4 = (n + 3) & ~3;
     for (int idx = threadIdx.x; idx < n4 * n4; idx += blockDim.x) {
         const int i = idx / n4, j = idx % n4;
@@ -340,7 +353,7 @@ __device__ void inv_sqrt_from_eig(const float* D, const float* Q, int n, int ld,
 // global reads overlap instead of forming a chain)
 // (32-bit index arithmetic: the planner accepts a mode only when
 // I_n x (Rp_n + 4) stays below 2^31.)
-__device__ void copy_cols(const float* src, int lds, int c0, int w, int64_t rows, float* dst, int ldd) {
+__device__ __noinline__ void copy_cols(const float* src, int lds, int c0, int w, int64_t rows, float* dst, int ldd) {
     const int w4 = (w + 3) & ~3;
     const int tot = (int)rows * w4;
     const int step = blockDim.x;
@@ -375,8 +388,10 @@ __device__ JacobiBufs carve_jacobi(float* base, int ld) {
 // (a multiple of 4 floats, so what follows stays 16-byte aligned)
 __host__ __device__ constexpr int jacobi_floats(int ld) { return 4 * ld * ld + 4 * ld; }
 
+template <bool INLINE_SOLVE>
 __device__ EigBufs sym_eig_orth(JacobiBufs& jb, int n, int ld, float tol, int max_sweeps, float* scratch) {
-    const EigBufs eb = block_jacobi(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, n, ld, tol, max_sweeps);
+    const EigBufs eb = INLINE_SOLVE ? block_jacobi_body(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, n, ld, tol, max_sweeps)
+                                    : block_jacobi(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, n, ld, tol, max_sweeps);
     if (n <= kOrthMinN) return eb;
     // the pair of buffers the last round did not leave its result in
     float* K = eb.A == jb.A ? jb.A2 : jb.A;
@@ -559,7 +574,7 @@ __device__ __forceinline__ void svt_body(const SmallModeArgs& m, DevScalars* sc,
     }
     // 2. eigen-decomposition
     const EigBufs eb = FP64 ? sym_eig_fp64(jb, R, ld, red + svt_red_floats(Rp)).f
-                            : sym_eig_orth(jb, R, ld, 1e-6f, 30, red);
+                            : sym_eig_orth<true>(jb, R, ld, 1e-6f, 30, red);
     const float* Ae = eb.A;
     const float* Ve = eb.V;
     sort_desc(Ae, R, ld, perm);
@@ -740,10 +755,10 @@ __device__ __forceinline__ void polar_body(const SmallModeArgs& m, DevScalars* s
 }
 
 template <bool FP64>
-__global__ void __launch_bounds__(SM_THREADS) polar_kernel(SmallArgs sa) {
+__global__ void __launch_bounds__(SM_THREADS, 1) polar_kernel(SmallArgs sa) {
     polar_body<FP64>(sa.m[blockIdx.x], sa.sc, blockIdx.x);
 }
-__global__ void __launch_bounds__(SM_THREADS) polar_kernel_batched(const SmallBatchEntry* e) {
+__global__ void __launch_bounds__(SM_THREADS, 1) polar_kernel_batched(const SmallBatchEntry* e) {
     const SmallBatchEntry& x = e[blockIdx.x];
     polar_body<false>(x.m, x.sc, x.mode);
 }
