@@ -467,27 +467,29 @@ def _sweep(P, torch, ctx, args):
                         "generated on the GPU (seed 11)", "rows": rows}
 
 
-def _phase(P, torch, ctx, args):
+def _phase(P, torch, ctx, args, ranks=None, rhos=None, trials=None):
     """Phase-transition map on 100^3 (the paper's Fig. 1 setting with this
     repository's random streams): Tucker rank r = 2..50 step 2 (R_n = floor(1.2 r)),
     corruption fraction 2..50% step 2 (U[-1,1] additive), `phase_trials` trials per
     cell, success when the recovery error is at most 1e-3. Solves run through
-    pasd_submit, `phase_slots` at a time per rank, with the idle-start skip."""
+    pasd_submit, `phase_slots` at a time per rank, with the idle-start skip. The
+    default run maps a coarser grid (`ranks`, `rhos`, `trials` given)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     from paper_1712_09999_gb300 import synth
-    ranks = list(range(2, 51, 2))
-    rhos = [k / 100 for k in range(2, 51, 2)]
+    ranks = ranks or list(range(2, 51, 2))
+    rhos = rhos or [k / 100 for k in range(2, 51, 2)]
+    trials = trials or args.phase_trials
     grid = []
     t0 = time.perf_counter()
     n_solves = 0
     for r in ranks:
         R = int(1.2 * r)
         slots = []
-        for _ in range(args.phase_slots):
+        for _ in range(min(args.phase_slots, len(rhos) * trials)):
             plan, _ = P.pasd_plan(ctx, P.make_params((100,) * 3, (R,) * 3, tol=1e-5, max_iter=1000,
                                                      flags=P.F_SKIP_IDLE))
             slots.append((plan, torch.empty((100,) * 3, device=dev), torch.empty((100,) * 3, device=dev)))
-        jobs = [(rho, tr) for rho in rhos for tr in range(args.phase_trials)]
+        jobs = [(rho, tr) for rho in rhos for tr in range(trials)]
         ok = {rho: 0 for rho in rhos}
         free = list(range(len(slots)))
         pending = {}
@@ -513,9 +515,9 @@ def _phase(P, torch, ctx, args):
             time.sleep(0.0001)
         for plan, _, _ in slots:
             P.pasd_plan_destroy(plan)
-        grid.append([ok[rho] / args.phase_trials for rho in rhos])
-    return {"workload": "100^3, Tucker rank r = 2..50 step 2 (R = floor(1.2 r)), corruption 2..50% step 2, "
-                        f"{args.phase_trials} trials per cell, success: RSE <= 1e-3", "ranks": ranks,
+        grid.append([ok[rho] / trials for rho in rhos])
+    return {"workload": f"100^3, Tucker rank r in {ranks} (R = floor(1.2 r)), corruption {rhos}, "
+                        f"{trials} trials per cell, success: RSE <= 1e-3", "ranks": ranks,
             "rhos": rhos, "success": grid, "solves": n_solves, "seconds": round(time.perf_counter() - t0, 1)}
 
 
@@ -720,6 +722,10 @@ def run_ours(args):
         line["sweep"] = _sweep(P, torch, ctx, args)
     if rank == 0 and args.phase:
         line["phase"] = _phase(P, torch, ctx, args)
+    elif rank == 0 and not args.no_phase_small:
+        # a coarse cut of the phase map (Fig. 1 setting) in every default run
+        line["phase_small"] = _phase(P, torch, ctx, args, ranks=[6, 14, 22, 30, 38, 46],
+                                     rhos=[0.05, 0.15, 0.25, 0.35, 0.45], trials=2)
     if rank == 0 and not args.no_video:
         line["video"] = _video(P, torch, ctx, args)
     if rank == 0 and not args.no_batched:
@@ -797,6 +803,7 @@ def main():
     ap.add_argument("--sweep-sides", type=int, nargs="+", default=[100, 200, 300, 400, 500, 600, 800])
     ap.add_argument("--phase", action="store_true", help="phase-transition map on 100^3")
     ap.add_argument("--phase-trials", type=int, default=10)
+    ap.add_argument("--no-phase-small", action="store_true", help="skip the coarse phase map of the default run")
     ap.add_argument("--phase-slots", type=int, default=16)
     ap.add_argument("--oracle-one-core", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
