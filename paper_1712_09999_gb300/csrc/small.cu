@@ -51,8 +51,7 @@ constexpr int TILE_SCRATCH = 4096;   // floats of split partial sums for tile_At
 // rounding, so A stays exactly symmetric.
 // ---------------------------------------------------------------------------
 struct JacobiBufs {
-    float *A, *V, *A2, *V2, *cs;
-    int* pc;
+    float *A, *V, *A2, *V2, *cs;   // cs: 2 ld floats, the round's rotations
 };
 // Buffers holding the eigenvalues (diagonal) and eigenvectors (columns) on return.
 struct EigBufs {
@@ -112,8 +111,8 @@ __device__ __forceinline__ int pair_rotation(const float* A, int ld, int i, int 
     return rot;
 }
 
-// pc: m ints, cs: 2 m floats of shared scratch for the round's rotations.
-__device__ __forceinline__ EigBufs block_jacobi_body(float* A, float* V, float* A2, float* V2, int* pc, float* cs, int n, int ld,
+// cs: 2 m floats of shared scratch for the round's rotations.
+__device__ __forceinline__ EigBufs block_jacobi_body(float* A, float* V, float* A2, float* V2, float* cs, int n, int ld,
                                 float tol, int max_sweeps) {
     const int t = threadIdx.x, nt = blockDim.x;
     const int m = n + (n & 1);
@@ -146,7 +145,7 @@ __device__ __forceinline__ EigBufs block_jacobi_body(float* A, float* V, float* 
                     cs[2 * t + 1] = si;
                 }
                 if (!__syncthreads_or(rot)) continue;
-                // the partners come from the round-robin formula, not from pc[], so
+                // the partners come from the round-robin formula, not from a table, so
                 // the loads below do not wait on another shared-memory load
                 for (int idx = t; idx < m * m; idx += nt) {
                     const int i = idx < nt ? fi : idx / m, j = idx < nt ? fj : idx % m;
@@ -172,9 +171,9 @@ __device__ __forceinline__ EigBufs block_jacobi_body(float* A, float* V, float* 
 
 // Out-of-line copy for the U-step, which runs two eigen-solves; the SVT inlines
 // the body (one call site, and the call costs it more than the code size).
-__device__ __noinline__ EigBufs block_jacobi(float* A, float* V, float* A2, float* V2, int* pc, float* cs, int n,
+__device__ __noinline__ EigBufs block_jacobi(float* A, float* V, float* A2, float* V2, float* cs, int n,
                                             int ld, float tol, int max_sweeps) {
-    return block_jacobi_body(A, V, A2, V2, pc, cs, n, ld, tol, max_sweeps);
+    return block_jacobi_body(A, V, A2, V2, cs, n, ld, tol, max_sweeps);
 }
 
 // Descending order of the diagonal of A (n x n, ld): perm[rank] = index.
@@ -382,16 +381,15 @@ __device__ JacobiBufs carve_jacobi(float* base, int ld) {
     b.A2 = b.V + ld * ld;
     b.V2 = b.A2 + ld * ld;
     b.cs = b.V2 + ld * ld;
-    b.pc = reinterpret_cast<int*>(b.cs + 2 * ld);
     return b;
 }
 // (a multiple of 4 floats, so what follows stays 16-byte aligned)
-__host__ __device__ constexpr int jacobi_floats(int ld) { return 4 * ld * ld + 4 * ld; }
+__host__ __device__ constexpr int jacobi_floats(int ld) { return 4 * ld * ld + 4 * ld; }   // A, V, A2, V2, cs (+ 2 ld spare)
 
 template <bool INLINE_SOLVE>
 __device__ EigBufs sym_eig_orth(JacobiBufs& jb, int n, int ld, float tol, int max_sweeps, float* scratch) {
-    const EigBufs eb = INLINE_SOLVE ? block_jacobi_body(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, n, ld, tol, max_sweeps)
-                                    : block_jacobi(jb.A, jb.V, jb.A2, jb.V2, jb.pc, jb.cs, n, ld, tol, max_sweeps);
+    const EigBufs eb = INLINE_SOLVE ? block_jacobi_body(jb.A, jb.V, jb.A2, jb.V2, jb.cs, n, ld, tol, max_sweeps)
+                                    : block_jacobi(jb.A, jb.V, jb.A2, jb.V2, jb.cs, n, ld, tol, max_sweeps);
     if (n <= kOrthMinN) return eb;
     // the pair of buffers the last round did not leave its result in
     float* K = eb.A == jb.A ? jb.A2 : jb.A;
