@@ -744,8 +744,9 @@ def run_profile_workload(args):
     """For ncu: plan a workload, run `pre` loop bodies, then `iters` more, exit.
     --workload cube200 (default): the 200^3 workload; video: the 144x176x3x300
     colour-video shape with R = (20, 20, 3, 5). Launch order per body: polar,
-    A-pass (one launch per group of modes with the same padded rank), SVT, Vrot,
-    fused pass, M-pass, finalize; pasd_begin launches 3 kernels first. --mixed
+    A-pass (one launch per group of modes with the same padded rank), SVT, Vrot
+    (one launch per rank bucket), fused pass, M-pass, finalize; pasd_begin
+    launches 3 kernels first. --mixed
     plans it with mixed precision."""
     import torch
     import __graft_entry__ as ge

@@ -172,6 +172,7 @@ struct pasd_plan {
     int nparts_max = 0;                  // residual partials: room for every fused geometry
     int ap_launches = 1;
     int mp_launches = 1;
+    int vr_launches = 1;
     // idle-start skip (PASD_F_SKIP_IDLE): armed by pasd_begin, run after the first body
     float* idle_g = nullptr;
     IdleSkipArgs idle{};
@@ -567,7 +568,7 @@ static void enqueue_iteration(pasd_plan_t* pl, cudaStream_t s) {
     launch_polar(pl->small, s);
     pl->ap_launches = launch_apass_all(pl, s);
     launch_svt(pl->small, s);
-    launch_vrot(pl->vr, s);
+    pl->vr_launches = launch_vrot(pl->vr, s);
     launch_fused_pass(pl, 0, nullptr, s);
     pl->mp_launches = launch_mpass_any(pl, s);
     launch_finalize(pl->fin, s);
@@ -893,7 +894,7 @@ static pasd_status ensure_allocated(pasd_plan_t* pl) {
         const ModeGeom& g = pl->m[n];
         VrotMode& vm = va.m[n];
         vm.A = pl->A[n]; vm.V = pl->Vr[n]; vm.W = pl->W[n]; vm.F = pl->F[n];
-        vm.P = g.P; vm.post = g.post; vm.R = g.R; vm.Rp = g.Rp;
+        vm.P = g.P; vm.post = g.post; vm.R = g.R; vm.Rp = g.Rp; vm.mode = n;
         va.cta_start[n + 1] = va.cta_start[n] + vrot_ctas(g.P, g.post, vr_maxRp);
     }
     pl->mpa.sc = pl->sc;
@@ -1093,14 +1094,14 @@ extern "C" pasd_status pasd_plan_info(const pasd_plan_t* pl, char* buf, size_t l
              pl->tune_mode, pl->tma != nullptr || (!pl->arena && pl->want_tma) ? 1 : 0,
              pl->tuned ? pl->tuned_fused_k : pl->default_fused_k, box.c_str(), g.nregions,
              g.tma ? g.nthreads : FU_THREADS, pl->n_fcand, pl->mp_use_tma ? 1 : 0, pl->tuned_mp_waves, mp_ctas,
-             apc.c_str(), aps.c_str(), few.c_str(), pl->ap_launches + pl->mp_launches + 5);
+             apc.c_str(), aps.c_str(), few.c_str(), pl->ap_launches + pl->mp_launches + pl->vr_launches + 4);
     if (std::strlen(tmp) + 1 > len) return fail(PASD_ERR_INVALID_ARG, "buffer too small");
     std::memcpy(buf, tmp, std::strlen(tmp) + 1);
     return PASD_OK;
 }
 
 extern "C" int32_t pasd_launches_per_iter(const pasd_plan_t* pl) {
-    return pl ? pl->ap_launches + pl->mp_launches + 5 : 0;
+    return pl ? pl->ap_launches + pl->mp_launches + pl->vr_launches + 4 : 0;
 }
 
 // ---------------------------------------------------------------------------

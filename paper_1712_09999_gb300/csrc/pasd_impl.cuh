@@ -203,6 +203,7 @@ struct VrotMode {
     const float* F;        // Rp
     int64_t P, post;
     int R, Rp;
+    int mode;              // index of the mode in the plan (its kept count)
 };
 struct VrotArgs {
     int N;
@@ -210,7 +211,9 @@ struct VrotArgs {
     VrotMode m[PASD_MAXN];
     int cta_start[PASD_MAXN + 1];
 };
-void launch_vrot(const VrotArgs& a, cudaStream_t s);
+// One launch per rank bucket of the modes (a mode's loops are sized by its own
+// bucket); returns the number of launches.
+int launch_vrot(const VrotArgs& a, cudaStream_t s);
 // CTAs the Vrot launch gives a mode of P columns (maxRp: the largest Rp of the plan)
 int vrot_ctas(int64_t P, int64_t post, int maxRp);
 void launch_norm_fro(const float* T, int64_t D, float* part, int nparts, DevScalars* sc,

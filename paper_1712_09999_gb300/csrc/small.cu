@@ -1013,7 +1013,7 @@ __device__ __forceinline__ void vrot_body(const VrotArgs& va, const int block) {
     while (k + 1 < va.N && (int)block >= va.cta_start[k + 1]) ++k;
     const VrotMode& m = va.m[k];
     const int R = m.R, Rp = m.Rp;
-    const int s = sc->kept[k];
+    const int s = sc->kept[m.mode];
     // consumers read the first round4(s) rows only (rows s .. round4(s) - 1 are
     // zero); with nothing kept there is nothing to write
     const int s4 = (s + 3) & ~3;
@@ -1176,17 +1176,30 @@ static void launch_vrot_rb(const VrotArgs& a, cudaStream_t s) {
     else vrot_kernel<RB, false><<<grid, 256, 0, s>>>(a);
 }
 
-void launch_vrot(const VrotArgs& a, cudaStream_t s) {
-    int maxRp = 4;
-    for (int n = 0; n < a.N; ++n) maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
-    switch (vrot_rb(maxRp)) {
-        case 8: launch_vrot_rb<8>(a, s); break;
-        case 16: launch_vrot_rb<16>(a, s); break;
-        case 24: launch_vrot_rb<24>(a, s); break;
-        case 32: launch_vrot_rb<32>(a, s); break;
-        case 48: launch_vrot_rb<48>(a, s); break;
-        default: launch_vrot_rb<64>(a, s); break;
+int launch_vrot(const VrotArgs& a, cudaStream_t s) {
+    int launches = 0;
+    for (const int rb : {8, 16, 24, 32, 48, 64}) {
+        VrotArgs g = a;
+        g.N = 0;
+        g.cta_start[0] = 0;
+        for (int n = 0; n < a.N; ++n) {
+            if (vrot_rb(a.m[n].Rp) != rb) continue;
+            g.m[g.N] = a.m[n];
+            g.cta_start[g.N + 1] = g.cta_start[g.N] + vrot_ctas(a.m[n].P, a.m[n].post, rb);
+            ++g.N;
+        }
+        if (g.N == 0) continue;
+        switch (rb) {
+            case 8: launch_vrot_rb<8>(g, s); break;
+            case 16: launch_vrot_rb<16>(g, s); break;
+            case 24: launch_vrot_rb<24>(g, s); break;
+            case 32: launch_vrot_rb<32>(g, s); break;
+            case 48: launch_vrot_rb<48>(g, s); break;
+            default: launch_vrot_rb<64>(g, s); break;
+        }
+        ++launches;
     }
+    return launches;
 }
 
 // ---------------------------------------------------------------------------
