@@ -145,7 +145,6 @@ struct pasd_plan {
     int default_fused_k = 0;             // CTAs per SM of the planner's default geometry
     int tuned_fused_k = 0;               // CTAs per SM of the geometry in use
     int tuned_mp_waves = 1;
-    int tuned_ap_var = 0;
     int ap_tma_default_nc[PASD_MAXN];
     bool tuned = false;
     const char* tune_mode = "pending";   // pending (no pasd_begin yet), timed, cached, off
@@ -581,7 +580,9 @@ static void enqueue_iteration(pasd_plan_t* pl, cudaStream_t s) {
 struct TuneChoice {
     int fused_k;     // resident CTAs per SM of the fused pass's geometry
     int mp_waves;    // waves of M-pass CTAs
-    int ap_var;      // A-pass FMA kernel: 0 default, 1 half the columns per thread, 2 rows split in two groups
+    // A-pass FMA kernel, per launch group (modes of one padded rank): 0 default,
+    // 1 half the columns per thread, 2 rows split in two thread groups
+    int ap_var[PASD_MAXN];
 };
 static std::mutex g_tune_mu;
 static std::map<std::string, TuneChoice> g_tune_cache;
@@ -675,9 +676,8 @@ static void apply_tune(pasd_plan_t* pl, const TuneChoice& c) {
         const int cur = apass_tma_cols(pl->ap_tma[q]);
         if (cur == 0) continue;
         const int def = pl->ap_tma_default_nc[q];
-        apass_tma_set_cols(pl->ap_tma[q], c.ap_var == 1 ? def / 2 : def, c.ap_var == 2 ? 2 : 1);
+        apass_tma_set_cols(pl->ap_tma[q], c.ap_var[q] == 1 ? def / 2 : def, c.ap_var[q] == 2 ? 2 : 1);
     }
-    pl->tuned_ap_var = c.ap_var;
 }
 
 // Times the candidates on the plan's own buffers (before its first pasd_begin
@@ -696,7 +696,6 @@ static void force_apass_variant(pasd_plan_t* pl) {
         if (def == 0) continue;
         apass_tma_set_cols(pl->ap_tma[q], var == 1 ? def / 2 : def, var == 2 ? 2 : 1);
     }
-    pl->tuned_ap_var = var;
 }
 
 static void autotune_impl(pasd_plan_t* pl);
@@ -720,7 +719,7 @@ static void autotune_impl(pasd_plan_t* pl) {
     }
     pl->tune_mode = "timed";
     cudaStream_t s = pl->cap_stream;
-    TuneChoice choice{pl->default_fused_k, 1, 0};
+    TuneChoice choice{pl->default_fused_k, 1, {0}};
     char err[256];
     if (pl->tma && pl->n_fcand > 1) {
         float t_def = NAN, best = INFINITY;
@@ -776,21 +775,23 @@ static void autotune_impl(pasd_plan_t* pl) {
     set_tune_scalars(pl, false);
     if (pl->n_ap_tma > 0 && pl->ap_kind == APASS_FFMA) {
         // the A-pass reads only the done flag, which is clear before the first pasd_begin
-        float th[3] = {NAN, NAN, NAN};
-        for (int var = 0; var < 3; ++var) {
-            for (int q = 0; q < pl->n_ap_tma; ++q) {
-                const int def = pl->ap_tma_default_nc[q];
+        // each launch group (modes of one padded rank) takes its own variant
+        for (int q = 0; q < pl->n_ap_tma; ++q) {
+            const int def = pl->ap_tma_default_nc[q];
+            if (def == 0) continue;
+            float th[3] = {NAN, NAN, NAN};
+            for (int var = 0; var < 3; ++var) {
                 apass_tma_set_cols(pl->ap_tma[q], var == 1 ? def / 2 : def, var == 2 ? 2 : 1);
+                th[var] = behind_evict([&] { launch_apass_tma(pl->ap_tma[q], s); });
             }
-            th[var] = behind_evict([&] { launch_apass_all(pl, s); });
+            apass_tma_set_cols(pl->ap_tma[q], def, 1);
+            float best = th[0];
+            for (int var = 1; var < 3; ++var)
+                if (th[0] == th[0] && th[var] == th[var] && th[var] < 0.97f * th[0] && th[var] < best) {
+                    best = th[var];
+                    choice.ap_var[q] = var;
+                }
         }
-        for (int q = 0; q < pl->n_ap_tma; ++q) apass_tma_set_cols(pl->ap_tma[q], pl->ap_tma_default_nc[q], 1);
-        float best = th[0];
-        for (int var = 1; var < 3; ++var)
-            if (th[0] == th[0] && th[var] == th[var] && th[var] < 0.97f * th[0] && th[var] < best) {
-                best = th[var];
-                choice.ap_var = var;
-            }
     }
     cudaStreamSynchronize(s);
     cudaGetLastError();
