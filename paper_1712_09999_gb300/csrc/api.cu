@@ -1457,7 +1457,7 @@ static void layout_groups(BatchExec& b, std::vector<BatchLaunch>& out, const std
 }
 
 struct ApItem { const ApassTmaPlan* p; };
-struct VrItem { const pasd_plan_t* pl; };
+struct VrItem { VrotArgs a; };   // one rank bucket of a plan's modes
 struct FuItem { const FusedTmaPlan* p; };
 struct MpItem { const MpassTmaPlan* p; };
 struct MqItem { const pasd_plan_t* pl; };
@@ -1524,7 +1524,13 @@ static bool batch_build(BatchExec& b, cudaStream_t s) {
         for (int q = 0; q < pl->n_ap_tma; ++q)
             if (apass_batch_ctas(pl->ap_tma[q]) >= 0)
                 ap[{apass_batch_rp(pl->ap_tma[q]), apass_tma_variant(pl->ap_tma[q])}].push_back(ApItem{pl->ap_tma[q]});
-        vr[{vrot_launch_rb(pl->vr), vrot_launch_v4(pl->vr) ? 1 : 0}].push_back(VrItem{pl});
+        {
+            VrotArgs sub[PASD_MAXN];
+            int rbs[PASD_MAXN];
+            bool v4s[PASD_MAXN];
+            const int ns = vrot_split(pl->vr, sub, rbs, v4s);
+            for (int k = 0; k < ns; ++k) vr[{rbs[k], v4s[k] ? 1 : 0}].push_back(VrItem{sub[k]});
+        }
         fu[{fused_batch_order(pl->tma), fused_batch_threads(pl->tma)}].push_back(FuItem{pl->tma});
         if (pl->n_mp_big > 0) {
             if (pl->mp_tma) mp[0].push_back(MpItem{pl->mp_tma});
@@ -1538,9 +1544,9 @@ static bool batch_build(BatchExec& b, cudaStream_t s) {
         [](void* e, const ApItem& i, int st) { apass_batch_fill(e, i.p, st); },
         [](const ApItem& i) { return apass_batch_smem(i.p); }, pair_keys);
     layout_groups<std::pair<int, int>, VrItem>(
-        b, b.vrot, vr, sizeof(VrotBatchEntry), [](const VrItem& i) { return i.pl->vr.cta_start[i.pl->N]; },
+        b, b.vrot, vr, sizeof(VrotBatchEntry), [](const VrItem& i) { return i.a.cta_start[i.a.N]; },
         [](void* e, const VrItem& i, int st) {
-            VrotBatchEntry v{i.pl->vr, st};
+            VrotBatchEntry v{i.a, st};
             std::memcpy(e, &v, sizeof(v));
         },
         [](const VrItem&) { return (size_t)0; }, pair_keys);

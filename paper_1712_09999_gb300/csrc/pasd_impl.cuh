@@ -214,6 +214,9 @@ struct VrotArgs {
 // One launch per rank bucket of the modes (a mode's loops are sized by its own
 // bucket); returns the number of launches.
 int launch_vrot(const VrotArgs& a, cudaStream_t s);
+// The modes of `a` split by rank bucket: sub-arguments, bucket and whether the
+// four-column path is needed, at most one per bucket; returns their number.
+int vrot_split(const VrotArgs& a, VrotArgs* out, int* rb_out, bool* v4_out);
 // CTAs the Vrot launch gives a mode of P columns (maxRp: the largest Rp of the plan)
 int vrot_ctas(int64_t P, int64_t post, int maxRp);
 void launch_norm_fro(const float* T, int64_t D, float* part, int nparts, DevScalars* sc,
@@ -370,8 +373,6 @@ struct VrotBatchEntry {
 size_t polar_launch_smem(const SmallArgs& a);
 size_t svt_launch_smem(const SmallArgs& a);
 int finalize_ctas(const FinalizeArgs& a);
-int vrot_launch_rb(const VrotArgs& a);
-bool vrot_launch_v4(const VrotArgs& a);
 void launch_polar_batched(const SmallBatchEntry* e, int n, size_t smem, cudaStream_t s);
 void launch_svt_batched(const SmallBatchEntry* e, int n, size_t smem, cudaStream_t s);
 void launch_finalize_batched(const FinBatchEntry* e, const int* block_entry, int grid, cudaStream_t s);

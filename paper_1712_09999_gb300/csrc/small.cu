@@ -1136,24 +1136,12 @@ int vrot_ctas(int64_t P, int64_t post, int maxRp) {
     return (int)((P / cols + 255) / 256);
 }
 
-int vrot_launch_rb(const VrotArgs& a) {
-    int maxRp = 4;
-    for (int n = 0; n < a.N; ++n) maxRp = a.m[n].Rp > maxRp ? a.m[n].Rp : maxRp;
-    return vrot_rb(maxRp);
-}
-bool vrot_launch_v4(const VrotArgs& a) {
-    const int rb = vrot_launch_rb(a);
-    bool v4 = false;
-    for (int n = 0; n < a.N; ++n) v4 = v4 || vrot_cols(a.m[n].P, a.m[n].post, rb) == 4;
-    return v4;
-}
-
 template <int RB>
 static void launch_vrot_batched_rb(bool v4, const VrotBatchEntry* e, const int* block_entry, int grid, cudaStream_t s) {
     if (v4) vrot_kernel_batched<RB, true><<<grid, 256, 0, s>>>(e, block_entry);
     else vrot_kernel_batched<RB, false><<<grid, 256, 0, s>>>(e, block_entry);
 }
-// every entry of one launch has the same rb = vrot_launch_rb and v4 = vrot_launch_v4
+// every entry of one launch has the same rank bucket rb and four-column flag v4 (vrot_split)
 void launch_vrot_batched(int rb, bool v4, const VrotBatchEntry* e, const int* block_entry, int grid, cudaStream_t s) {
     switch (rb) {
         case 8: launch_vrot_batched_rb<8>(v4, e, block_entry, grid, s); break;
@@ -1176,20 +1164,37 @@ static void launch_vrot_rb(const VrotArgs& a, cudaStream_t s) {
     else vrot_kernel<RB, false><<<grid, 256, 0, s>>>(a);
 }
 
-int launch_vrot(const VrotArgs& a, cudaStream_t s) {
-    int launches = 0;
+int vrot_split(const VrotArgs& a, VrotArgs* out, int* rb_out, bool* v4_out) {
+    int k = 0;
     for (const int rb : {8, 16, 24, 32, 48, 64}) {
         VrotArgs g = a;
         g.N = 0;
         g.cta_start[0] = 0;
+        bool v4 = false;
         for (int n = 0; n < a.N; ++n) {
             if (vrot_rb(a.m[n].Rp) != rb) continue;
             g.m[g.N] = a.m[n];
             g.cta_start[g.N + 1] = g.cta_start[g.N] + vrot_ctas(a.m[n].P, a.m[n].post, rb);
+            v4 = v4 || vrot_cols(a.m[n].P, a.m[n].post, rb) == 4;
             ++g.N;
         }
         if (g.N == 0) continue;
-        switch (rb) {
+        out[k] = g;
+        rb_out[k] = rb;
+        v4_out[k] = v4;
+        ++k;
+    }
+    return k;
+}
+
+int launch_vrot(const VrotArgs& a, cudaStream_t s) {
+    VrotArgs sub[PASD_MAXN];
+    int rbs[PASD_MAXN];
+    bool v4s[PASD_MAXN];
+    const int ns = vrot_split(a, sub, rbs, v4s);
+    for (int k = 0; k < ns; ++k) {
+        const VrotArgs& g = sub[k];
+        switch (rbs[k]) {
             case 8: launch_vrot_rb<8>(g, s); break;
             case 16: launch_vrot_rb<16>(g, s); break;
             case 24: launch_vrot_rb<24>(g, s); break;
@@ -1197,9 +1202,8 @@ int launch_vrot(const VrotArgs& a, cudaStream_t s) {
             case 48: launch_vrot_rb<48>(g, s); break;
             default: launch_vrot_rb<64>(g, s); break;
         }
-        ++launches;
     }
-    return launches;
+    return ns;
 }
 
 // ---------------------------------------------------------------------------
