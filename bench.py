@@ -14,8 +14,10 @@ the loop streams (T, E, G_1..G_3: 160 MB) exceed the 129 MB L2, so no L2 flush i
 added between steps.
 
 Extra keys: roofline of the dominant kernel (algorithmic bytes of the fused
-elementwise pass over its CUDA-event durations, every launch of one solve, with
-the idle and active bodies also reported apart), clocks sampled during the timed
+elementwise pass, the bandwidth floor's (2N + 2) 4 D + 4 sum_n R_n P_n, over its
+CUDA-event durations, every launch of one solve, with the idle and active bodies
+also reported apart; impl_frac counts the bytes this design's pass moves
+instead, one more read of E and only the kept rows of Vrot), clocks sampled during the timed
 region, e2e (whole solves through pasd_solve_host with pinned host buffers),
 cpu_baseline (the FP64 oracle on the host cores, a bounded sample), table1 (the
 paper's Table 1 workloads, 100^3 and 50^4, with the paper's own PASD results as
@@ -655,11 +657,14 @@ def run_ours(args):
     tr = np.zeros((k_conv, P.TRACE_STRIDE))
     P.pasd_state_get(plan, P.STATE_TRACE, 0, tr)
     kept = tr[:, 5:5 + N]
-    # algorithmic bytes of one fused pass: read T, G_1..G_N, write E, G_1..G_N, read
-    # E (the previous iterate, which the multiplier update needs), read the kept rows
-    # of each Vrot_n once (kept counts of that body)
-    alg = np.array([(2 * N + 3) * 4 * D + 4 * sum(float(s) * (D // I) for s, I in zip(kept[b], DIMS))
-                    for b in range(k_conv)])
+    # algorithmic bytes of one fused pass, the bandwidth floor's second phase: read T
+    # and Y_1..Y_N, write E and Y_1..Y_N, read the rank-R_n refold operands once:
+    # (2N + 2) 4 D + 4 sum_n R_n P_n, the same for every body
+    alg = np.full(k_conv, (2 * N + 2) * 4.0 * D + 4.0 * sum(R * (D // I) for R, I in zip(RANKS, DIMS)))
+    # bytes this design's pass moves: also the previous E (the multiplier update reads
+    # it, the multipliers being stored as G_n) and only the kept rows of each Vrot_n
+    impl = np.array([(2 * N + 3) * 4 * D + 4 * sum(float(s) * (D // I) for s, I in zip(kept[b], DIMS))
+                     for b in range(k_conv)])
     fused = np.array([pb["fused"] for pb in per_body]) / 1000.0        # seconds per launch
     active = kept.sum(axis=1) > 0
     peak, peak_kind = _peaks()
@@ -669,6 +674,7 @@ def run_ours(args):
                 "frac": round(float(alg[mask].sum() / fused[mask].sum() / 1e9 / peak), 3)}
 
     achieved = float(alg.sum() / fused.sum() / 1e9)
+    impl_achieved = float(impl.sum() / fused.sum() / 1e9)
     tr_idle, tr_active = _fused_traffic()
     traffic = None
     if tr_idle is not None and tr_active is not None:
@@ -676,6 +682,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": "fused elementwise pass",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_kind": peak_kind, "traffic": traffic, "alg_bytes_per_launch": float(alg.mean()),
+                "impl_bytes_per_launch": float(impl.mean()), "impl_frac": round(impl_achieved / peak, 4),
                 "launch_ms": float(fused.mean() * 1000),
                 "averaged_over": f"every launch of one {k_conv}-body solve",
                 "phases": {"idle": phase(~active), "active": phase(active)},
