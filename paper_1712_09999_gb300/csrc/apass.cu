@@ -734,10 +734,6 @@ struct TcShape {
     static_assert(NOPS >= 2, "A-pass tensor-core stages do not fit shared memory");
 };
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // Column range, a-row and contraction length of global task `gt`.
 struct TcTask {
     int k;            // mode slot

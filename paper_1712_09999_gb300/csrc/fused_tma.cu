@@ -48,6 +48,9 @@ struct FusedTmaPlan {
     FusedArgs base;
 };
 
+// CTA size: the consumer warps over the g.nthreads micro-boxes, then the producer warp
+static int fused_block_threads(const FusedGeom& g) { return ((g.nthreads + 31) / 32 + 1) * 32; }
+
 
 // ---------------------------------------------------------------------------
 // kernel
@@ -66,10 +69,18 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
     extern __shared__ __align__(1024) float sm_raw[];
     // stage buffers aligned to 1024 bytes (the launch adds 1 KB of slack)
     float* sm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full_bar[kMaxStages];
+    __shared__ __align__(8) uint64_t full_bar[kMaxStages];    // stage filled (copies landed)
+    __shared__ __align__(8) uint64_t empty_bar[kMaxStages];   // stage read by every consumer warp
     __shared__ int tile_o[kMaxStages][N];   // origins of the tiles in the stages
+    __shared__ int s_fail;
+    __shared__ long long s_fail_it;
     const int t = threadIdx.x;
-    const int nthr = blockDim.x;
+    // warp roles: ncw consumer warps own the micro-boxes (threads t < nthr), the
+    // last warp issues every copy, so no consumer waits on a copy's issue
+    const int nthr = g.nthreads;
+    const int ncw = (nthr + 31) >> 5;
+    const bool producer = t >= ncw * 32;
+    const bool comp = t < nthr;
     const int B = g.B;
 
     int sp[N];                         // kept count rounded up to 4 (0: mode has no low-rank part)
@@ -130,13 +141,11 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
 #pragma unroll
     for (int n = 0; n < N; ++n) res2[n] = 0.f;
 
-    // Refill schedule. With nothing kept (pure streaming) a stage holds only the
-    // element tiles, so the same shared memory holds up to kMaxStages of them:
-    // the refills run nst - 1 tiles ahead, each issued before the current tile
-    // is awaited, and a second barrier per tile releases the stage. With a
-    // refold to compute, two full stages alternate: a tile's arithmetic covers
-    // one copy's latency and the refill goes out after the wait, whose barrier
-    // also releases the stage.
+    // Stages. With nothing kept (pure streaming) a stage holds only the element
+    // tiles, so the same shared memory holds up to kMaxStages of them; with a
+    // refold to compute, two full stages alternate. The producer lane fills a
+    // stage as soon as every consumer warp has released it (empty barrier), so
+    // copies run up to nst tiles ahead of the arithmetic.
     bool early = !output;
 #pragma unroll
     for (int n = 0; n < N; ++n) early = early && sp[n] == 0;
@@ -148,14 +157,18 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
         if (nst >= 2 && g.xs_off == 0) sstride = xs_stride; else nst = 2;
     }
     if (t == 0) {
-        for (int i = 0; i < nst; ++i) mbar_init(&full_bar[i], 1);
+        for (int i = 0; i < nst; ++i) {
+            mbar_init(&full_bar[i], 1);
+            mbar_init(&empty_bar[i], ncw);
+        }
+        s_fail = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
     const uint32_t polls = fa.wait_polls ? fa.wait_polls : kWaitPolls;
+    // producer lane: origins, odometer, barrier arming and the copies of one tile
     auto issue = [&](int st) {
-        if (fa.test_no_copy) return;   // test hook: no arrival, no copy in flight
         int o[N];
 #pragma unroll
         for (int n = 0; n < N; ++n) { o[n] = tc[n] * g.b[n]; tile_o[st][n] = o[n]; }
@@ -186,23 +199,32 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
         }
     };
 
+    int64_t issued = 0;      // producer lane: tiles whose copies went out
+    if (producer) {
+        if ((t & 31) == 0 && !fa.test_no_copy) {   // test hook: no arrival, no copy in flight
+            for (int64_t i = 0; i < ntile; ++i) {
+                const int st = (int)(i % nst);
+                // stage st last held tile i - nst: wait until every consumer warp read it
+                if (i >= nst && !mbar_wait_bounded(&empty_bar[st], (uint32_t)((i / nst - 1) & 1), polls)) break;
+                issue(st);
+                issued = i + 1;
+            }
+        }
+    }
     bool failed = false;
     int64_t fail_it = 0;     // the tile whose copy did not land
-    if (t == 0)
-        for (int i = 0; i < (early ? nst - 1 : 1) && i < ntile; ++i) issue(i);
-    for (int64_t it = 0; it < ntile; ++it) {
+    for (int64_t it = 0; !producer && it < ntile; ++it) {
         const int st = (int)(it % nst);
         const uint32_t par = (uint32_t)((it / nst) & 1);
-        if (early && t == 0 && it + nst - 1 < ntile) issue((int)((it + nst - 1) % nst));
         bool ok = mbar_wait_bounded(&full_bar[st], par, polls);
-        if (__syncthreads_or(!ok)) { failed = true; fail_it = it; break; }
-        if (!early && t == 0 && it + 1 < ntile) issue(st ^ 1);
+        if (bar_red_or(!ok, 1, ncw * 32)) { failed = true; fail_it = it; break; }
         float* stg = sm + st * sstride;
         float* Xs = stg + g.xs_off;
         int o[N];
 #pragma unroll
         for (int n = 0; n < N; ++n) o[n] = tile_o[st][n];
 
+        if (comp) {
         // ---- Z_n for the thread's 8 elements (j = d2 * 4 + d1), rank sp_n ----
         // Z_n in pairs (z2) for the modes before the last, whose products pair up
         // along the contiguous mode; the last mode's chains stay scalar (z)
@@ -316,8 +338,7 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
                     }
                 }
             }
-            continue;
-        }
+        } else {
 
         // ---- elementwise update; results to HBM from registers ----
         //   gz_n = G_n - Z_n,  Ebar = mean_n(G_n + E - Z_n) = E + mean(gz),
@@ -377,15 +398,23 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
                     *reinterpret_cast<float4*>(fa.G[n] + e) = make_float4(gv[n][0], gv[n][1], gv[n][2], gv[n][3]);
             }
         }
-        if (early) __syncthreads();   // stage st fully read: the next iteration refills it first
+        }   // update
+        }   // comp
+        // stage st fully read by this warp
+        __syncwarp();
+        if ((t & 31) == 0) mbar_arrive(&empty_bar[st]);
     }
-    if (failed) {
+    if (t == 0 && failed) {
+        s_fail = 1;
+        s_fail_it = fail_it;
+    }
+    __syncthreads();
+    if (s_fail) {
         // a copy never arrived: record it and leave once every tile issued from the
-        // failed one on (early: nst - 1 ahead, else none ahead) has been waited for
-        // in its own phase, bounded, so no copy lands after the CTA has exited
-        if (t == 0) {
-            const int64_t last = early ? fail_it + nst - 1 : fail_it;
-            for (int64_t c = fail_it; c <= last && c < ntile; ++c)
+        // failed one on (at most nst, one per stage) has been waited for in its own
+        // phase, bounded, so no copy lands after the CTA has exited
+        if (producer && (t & 31) == 0) {
+            for (int64_t c = s_fail_it; c < issued; ++c)
                 mbar_wait_bounded(&full_bar[c % nst], (uint32_t)((c / nst) & 1), polls);
             sc->status = -5;   // PASD_ERR_TIMEOUT
             sc->done = 1;
@@ -396,7 +425,7 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
     if (output) return;
 
     // ---- block reductions of the residual statistics ----
-    __shared__ float wred[FU_THREADS / 32][PASD_MAXN + 3];
+    __shared__ float wred[FU_THREADS / 32][PASD_MAXN + 3];   // consumer warps
     const int nonfin = !isfinite(chk);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -409,7 +438,7 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) nf |= __shfl_down_sync(0xffffffffu, nf, off);
     const int wid = t >> 5, lane = t & 31;
-    if (lane == 0) {
+    if (lane == 0 && !producer) {
         wred[wid][0] = resmax;
         wred[wid][1] = l1;
         wred[wid][2] = (float)nf;
@@ -421,7 +450,7 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
         float mx = 0.f, s1 = 0.f, nfs = 0.f, s2[N];
 #pragma unroll
         for (int n = 0; n < N; ++n) s2[n] = 0.f;
-        for (int w = 0; w < (nthr + 31) / 32; ++w) {
+        for (int w = 0; w < ncw; ++w) {
             mx = fmaxf(mx, wred[w][0]);
             s1 += wred[w][1];
             nfs = fmaxf(nfs, wred[w][2]);
@@ -438,7 +467,7 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
 }
 
 template <int N>
-__global__ void __launch_bounds__(FU_THREADS, 1)
+__global__ void __launch_bounds__(FU_THREADS + 32, 1)
     fused_tma_kernel(const __grid_constant__ FusedTmaMaps tm, const FusedArgs fa, const int output,
                      float* const Lout) {
     fused_tma_body<N>(tm, fa, output, Lout, blockIdx.x);
@@ -452,13 +481,13 @@ struct FusedBatchEntry {
     int start;
 };
 template <int N>
-__global__ void __launch_bounds__(FU_THREADS, 1)
+__global__ void __launch_bounds__(FU_THREADS + 32, 1)
     fused_tma_kernel_batched(const FusedBatchEntry* e, const int* block_entry) {
     const FusedBatchEntry& x = e[block_entry[blockIdx.x]];
     __shared__ __align__(16) FusedArgs s_fa;
     load_args_to_smem(&s_fa, &x.args);
     if (s_fa.sc->done) return;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == blockDim.x - 32) {   // the producer lane, which issues the copies
         for (int a = 0; a < N + 2; ++a) tensormap_acquire(&x.maps.tm_x[a]);
         for (int n = 0; n < N; ++n) {
             const int sp = (s_fa.sc->kept[n] + 3) & ~3;
@@ -570,13 +599,13 @@ static void launch_tma_n(FusedTmaPlan* p, int output, float* L, cudaStream_t s) 
     const FusedGeom& g = p->base.g;
     size_t smem = (size_t)g.smem_floats * 4 + 1024;
     set_smem_attr((const void*)fused_tma_kernel<N>, (int)smem);
-    fused_tma_kernel<N><<<g.nregions, g.nthreads, smem, s>>>(p->maps, p->base, output, L);
+    fused_tma_kernel<N><<<g.nregions, fused_block_threads(g), smem, s>>>(p->maps, p->base, output, L);
 }
 
 size_t fused_batch_entry_bytes() { return sizeof(FusedBatchEntry); }
 int fused_batch_order(const FusedTmaPlan* p) { return p->base.g.N; }
 int fused_batch_ctas(const FusedTmaPlan* p) { return p->base.g.nregions; }
-int fused_batch_threads(const FusedTmaPlan* p) { return p->base.g.nthreads; }
+int fused_batch_threads(const FusedTmaPlan* p) { return fused_block_threads(p->base.g); }
 size_t fused_batch_smem(const FusedTmaPlan* p) { return (size_t)p->base.g.smem_floats * 4 + 1024; }
 void fused_batch_fill(void* entry, const FusedTmaPlan* p, int start) {
     // built in an aligned local and copied: `entry` points into a byte staging
