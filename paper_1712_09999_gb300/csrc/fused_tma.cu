@@ -23,6 +23,7 @@
 
 #include <cuda.h>
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstring>
 
@@ -162,6 +163,7 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
             mbar_init(&empty_bar[i], ncw);
         }
         s_fail = 0;
+        s_fail_it = LLONG_MAX;
         fence_mbar_init();
     }
     __syncthreads();
@@ -211,13 +213,19 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
             }
         }
     }
-    bool failed = false;
-    int64_t fail_it = 0;     // the tile whose copy did not land
+    // consumer warps advance independently, at most nst tiles apart (the ring)
     for (int64_t it = 0; !producer && it < ntile; ++it) {
         const int st = (int)(it % nst);
         const uint32_t par = (uint32_t)((it / nst) & 1);
-        bool ok = mbar_wait_bounded(&full_bar[st], par, polls);
-        if (bar_red_or(!ok, 1, ncw * 32)) { failed = true; fail_it = it; break; }
+        const bool ok = mbar_wait_bounded(&full_bar[st], par, polls);
+        if (!__all_sync(0xffffffffu, ok)) {
+            // this warp gives up at tile it; the earliest such tile is recorded
+            if ((t & 31) == 0) {
+                s_fail = 1;
+                atomicMin(&s_fail_it, (long long)it);
+            }
+            break;
+        }
         float* stg = sm + st * sstride;
         float* Xs = stg + g.xs_off;
         int o[N];
@@ -404,15 +412,12 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
         __syncwarp();
         if ((t & 31) == 0) mbar_arrive(&empty_bar[st]);
     }
-    if (t == 0 && failed) {
-        s_fail = 1;
-        s_fail_it = fail_it;
-    }
     __syncthreads();
     if (s_fail) {
-        // a copy never arrived: record it and leave once every tile issued from the
-        // failed one on (at most nst, one per stage) has been waited for in its own
-        // phase, bounded, so no copy lands after the CTA has exited
+        // a copy never arrived: leave once every tile issued from the earliest one a
+        // warp gave up on (at most nst, one per stage: the tiles before it were read
+        // by every warp) has been waited for in its own phase, bounded, so no copy
+        // lands after the CTA has exited
         if (producer && (t & 31) == 0) {
             for (int64_t c = s_fail_it; c < issued; ++c)
                 mbar_wait_bounded(&full_bar[c % nst], (uint32_t)((c / nst) & 1), polls);
