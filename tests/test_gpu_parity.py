@@ -154,14 +154,16 @@ def test_video_shape_matches_oracle(env):
     # Colour-video-shaped tensor (height, width, channel, frame) at reduced size:
     # rank-1 background in the frame mode, moving rectangles replacing ~4% of the
     # voxels; R = (10, 10, 3, 5) (the channel mode at R_n = I_n), the paper's
-    # default lambda_n. Kept counts identical at every iteration and L within 1e-5,
+    # default lambda_n. Kept counts identical at every iteration and L within 2e-5,
     # at a fixed 150 bodies (past the activation at body 54) and at Algorithm 1's
     # stop rule (same stopping body, recovery error within 1e-4). Here E is dense at
     # the 1e-2 level (it absorbs the background's per-frame gain) and is formed from
     # differences of O(0.3) values: rounding only the FP64 oracle's state to FP32
-    # after every body already moves E by 4e-5 relative
+    # after every body already moves E by 4e-5 relative and L by 8e-6
     # (tests/test_oracle_pins.py::test_fp32_state_floor_dense_sparse_part), so E is
-    # held to 1e-4, the FP32 storage floor of this workload.
+    # held to 1e-4 and L to 2e-5, 2.5 times the FP32 storage floor of this workload
+    # (measured on the GPU: 7e-6 to 1.2e-5, depending on which A-pass partial sums the
+    # autotuner picks for the shape).
     # A stop one body apart is accepted only as a tie (_stop_tie), and L, E are
     # then compared with the oracle run to the GPU's stopping body.
     pr = synth.video(height=36, width=44, frames=40, n_rect=4, seed=3)
@@ -177,7 +179,7 @@ def test_video_shape_matches_oracle(env):
         gk = g["trace"][:, 5:9].astype(int).tolist()
         assert g["res"].iters == ref.iters
         assert gk == [s.kept for s in ref.trace]
-        assert _rel(g["L"], ref.L) <= TOL
+        assert _rel(g["L"], ref.L) <= 2e-5
         assert _rel(g["E"], ref.E) <= 1e-4
     assert abs(O.rse(g["L"], pr.L0) - O.rse(ref.L, pr.L0)) <= 1e-4
 
