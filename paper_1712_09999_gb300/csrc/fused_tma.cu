@@ -1,10 +1,10 @@
-// TMA-fed, double-buffered fused elementwise pass (same arithmetic as
-// fused.cu, which stays as the path for N > 4 or a contiguous mode whose
-// length is not a multiple of 4).
+// TMA-fed fused elementwise pass (same arithmetic as fused.cu, which stays as
+// the path for N > 4 or a contiguous mode whose length is not a multiple of 4).
 //
-// Per tile (a box of extents b_n), one elected thread issues bulk tensor
-// copies (cp.async.bulk.tensor) into the next stage while the CTA computes the
-// current one:
+// Per tile (a box of extents b_n), one lane of a producer warp issues bulk
+// tensor copies (cp.async.bulk.tensor) into a ring of stages while the
+// consumer warps compute earlier tiles; full / empty mbarriers pass each stage
+// between them:
 //   Xs   : T, E, G_0..G_{N-1} boxes, C order of the box (element index e)
 //   As_n : the Vrot_n columns the tile needs (kept rows), a box of the N-D
 //          tensor Vrot_n ([pre][Rp][post] viewed with I_n replaced by Rp),
@@ -16,7 +16,7 @@
 // update and adds nothing to the residual sums.
 // Results (E', G_n') go from registers straight to HBM as 16-byte stores (four
 // consecutive elements of the contiguous mode, whose length is a multiple of 4
-// here), so a stage is free for the next copy as soon as every thread has read
+// here), so a stage is free for the next copy as soon as every warp has read
 // it: no shared-memory write-back and no store to wait for before a refill.
 #include "pasd_impl.cuh"
 #include "tma.cuh"
