@@ -146,6 +146,10 @@ bool plan_geom_impl(FusedGeom& g, int N, const int64_t* I, const int* Rp, int nu
             g.out_tx_bytes = (uint32_t)(4 * txo);
             g.smem_floats = 2 * g.stage_floats;
             g.tma = 1;
+            // With (b_{N-1} / 4) (b_{N-2} / 2) < 8 the eight lanes of a quarter-warp
+            // read element-tile rows 32 floats apart (the same banks): give each
+            // thread groups 4 t and 4 t + B / 2 instead (split along mode 0).
+            g.split0 = (N >= 3 && b[0] >= 2 && (b[N - 1] / 4) * (b[N - 2] / 2) < 8) ? 1 : 0;
             // +1 KB so the kernel can align its stages to 1024 bytes
             if ((size_t)g.smem_floats * 4 + 1024 <= smem_limit) return true;
             continue;

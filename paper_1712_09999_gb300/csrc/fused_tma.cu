@@ -61,7 +61,7 @@ static int fused_block_threads(const FusedGeom& g) { return ((g.nthreads + 31) /
 // sp_n = round_up(s_n, 4) multiply-adds and loads only sp_n rows of Vrot and
 // columns of Urot (one tensor map per height). The next U-step's product
 // G_n' Vrot^T is formed by the M-pass that follows.
-template <int N>
+template <int N, int SM>
 __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const FusedArgs& fa, const int output,
                                                float* const Lout, const int block) {
     DevScalars* sc = fa.sc;
@@ -110,15 +110,22 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
 #pragma unroll
     for (int n = 0; n < N; ++n) tc[n] = (int)ts[n];
 
-    // micro-box of this thread: 4 consecutive elements along mode N-1 and two
-    // rows dstep = b_{N-2} / 2 apart along mode N-2, so the 8 lanes of a
-    // quarter-warp read 8 consecutive 16-byte groups (no bank conflicts) in the
-    // element tiles and in the Vrot slices of the modes before N-2
-    const int dstep = g.b[N - 2] / 2;
+    // micro-box of this thread: two groups of 4 consecutive elements along mode
+    // N-1, half = b_SM / 2 apart along the split mode SM. With SM = N-2 the 8
+    // lanes of a quarter-warp read 8 consecutive 16-byte groups (no bank
+    // conflicts) in the element tiles and in the Vrot slices of the modes before
+    // N-2 when (b_{N-1} / 4) (b_{N-2} / 2) >= 8; otherwise (SM = 0) thread t takes
+    // elements 4 t .. 4 t + 3 of the tile's first half and the same of its second
+    const int half = g.b[SM] / 2;
     int u0[N];
+    if (SM == N - 2) {
 #pragma unroll
-    for (int n = 0; n < N; ++n)
-        u0[n] = ((t >> g.mbsh[n]) & (g.b[n] / g.mb[n] - 1)) * (n == N - 2 ? 1 : g.mb[n]);
+        for (int n = 0; n < N; ++n)
+            u0[n] = ((t >> g.mbsh[n]) & (g.b[n] / g.mb[n] - 1)) * (n == N - 2 ? 1 : g.mb[n]);
+    } else {
+#pragma unroll
+        for (int n = 0; n < N; ++n) u0[n] = ((4 * t) >> g.esh[n]) & (g.b[n] - 1);
+    }
     int e0 = 0;
 #pragma unroll
     for (int n = 0; n < N; ++n) e0 += u0[n] << g.esh[n];
@@ -255,7 +262,7 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
             if (n == N - 1) {
                 const float* Wt = Ws + u0[n] * h;
                 const float* At = As + cb[n] * h;
-                const int a2 = (dstep << g.csh[n][N - 2]) * h;    // column of the second row
+                const int a2 = (half << g.csh[n][SM]) * h;    // column of the second group
                 for (int r = 0; r < h; r += 4) {
                     float4 w[4];
 #pragma unroll
@@ -279,10 +286,10 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
                 const int rs = 1 << H;
                 const float* Ab = As + ((chi * h) << H) + clo;
                 const float* Wt = Ws + u0[n] * h;
-                if (n == N - 2) {
+                if (n == SM) {
                     for (int r = 0; r < h; r += 4) {
                         const float4 w0 = *reinterpret_cast<const float4*>(Wt + r);
-                        const float4 w1 = *reinterpret_cast<const float4*>(Wt + dstep * h + r);
+                        const float4 w1 = *reinterpret_cast<const float4*>(Wt + half * h + r);
                         const float w0s[4] = {w0.x, w0.y, w0.z, w0.w}, w1s[4] = {w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
@@ -297,7 +304,9 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
                         }
                     }
                 } else {
-                    const int s2 = dstep << g.csh[n][N - 2];
+                    // the second group's column: a post mode of n moves c_lo, a pre
+                    // mode (SM = 0 < n) moves c_hi, whose stride is h rows of 2^H
+                    const int s2 = SM > n ? (half << g.csh[n][SM]) : (half << g.csh[n][SM]) * h;
                     for (int r = 0; r < h; r += 4) {
                         const float4 w = *reinterpret_cast<const float4*>(Wt + r);
                         const float ws[4] = {w.x, w.y, w.z, w.w};
@@ -331,11 +340,12 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
 #pragma unroll
             for (int n = 0; n < N; ++n) tbase += (int64_t)(o[n] + u0[n]) * g.stride[n];
 #pragma unroll
-            for (int n = 0; n < N - 2; ++n) vbase = vbase && (o[n] + u0[n] < g.I[n]);
+            for (int n = 0; n < N - 1; ++n)
+                if (n != SM) vbase = vbase && (o[n] + u0[n] < g.I[n]);
 #pragma unroll
             for (int d2 = 0; d2 < 2; ++d2) {
-                const bool v2 = vbase && (o[N - 2] + u0[N - 2] + d2 * dstep < g.I[N - 2]);
-                const int64_t rowoff = tbase + (int64_t)(d2 * dstep) * g.stride[N - 2];
+                const bool v2 = vbase && (o[SM] + u0[SM] + d2 * half < g.I[SM]);
+                const int64_t rowoff = tbase + (int64_t)(d2 * half) * g.stride[SM];
 #pragma unroll
                 for (int d1 = 0; d1 < 4; ++d1) {
                     if (v2 && (o[N - 1] + u0[N - 1] + d1 < g.I[N - 1])) {
@@ -357,10 +367,11 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
 #pragma unroll
         for (int n = 0; n < N; ++n) gbase += (int64_t)(o[n] + u0[n]) * g.stride[n];
 #pragma unroll
-        for (int n = 0; n < N - 2; ++n) valid = valid && (o[n] + u0[n] < g.I[n]);
+        for (int n = 0; n < N - 1; ++n)
+            if (n != SM) valid = valid && (o[n] + u0[n] < g.I[n]);
 #pragma unroll
         for (int d2 = 0; d2 < 2; ++d2) {
-            const int eb = e0 + ((d2 * dstep) << g.esh[N - 2]);
+            const int eb = e0 + ((d2 * half) << g.esh[SM]);
             float4 x = *reinterpret_cast<const float4*>(Xs + eb);
             const float tv[4] = {x.x, x.y, x.z, x.w};
             x = *reinterpret_cast<const float4*>(Xs + B + eb);
@@ -398,8 +409,8 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
                 l1 += fabsf(e);
                 chk += e;
             }
-            if (valid && o[N - 2] + u0[N - 2] + d2 * dstep < g.I[N - 2]) {
-                const int64_t e = gbase + (int64_t)(d2 * dstep) * g.stride[N - 2];
+            if (valid && o[SM] + u0[SM] + d2 * half < g.I[SM]) {
+                const int64_t e = gbase + (int64_t)(d2 * half) * g.stride[SM];
                 *reinterpret_cast<float4*>(fa.E + e) = make_float4(en[0], en[1], en[2], en[3]);
 #pragma unroll
                 for (int n = 0; n < N; ++n)
@@ -471,11 +482,11 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
     }
 }
 
-template <int N>
+template <int N, int SM>
 __global__ void __launch_bounds__(FU_THREADS + 32, 1)
     fused_tma_kernel(const __grid_constant__ FusedTmaMaps tm, const FusedArgs fa, const int output,
                      float* const Lout) {
-    fused_tma_body<N>(tm, fa, output, Lout, blockIdx.x);
+    fused_tma_body<N, SM>(tm, fa, output, Lout, blockIdx.x);
 }
 
 // Batched: the CTAs [start, start + nregions) of an entry run that solve's
@@ -485,7 +496,7 @@ struct FusedBatchEntry {
     FusedArgs args;
     int start;
 };
-template <int N>
+template <int N, int SM>
 __global__ void __launch_bounds__(FU_THREADS + 32, 1)
     fused_tma_kernel_batched(const FusedBatchEntry* e, const int* block_entry) {
     const FusedBatchEntry& x = e[block_entry[blockIdx.x]];
@@ -499,7 +510,7 @@ __global__ void __launch_bounds__(FU_THREADS + 32, 1)
             if (sp) { tensormap_acquire(&x.maps.tm_a[n][sp / 4 - 1]); tensormap_acquire(&x.maps.tm_w[n][sp / 4 - 1]); }
         }
     }
-    fused_tma_body<N>(x.maps, s_fa, 0, nullptr, blockIdx.x - x.start);
+    fused_tma_body<N, SM>(x.maps, s_fa, 0, nullptr, blockIdx.x - x.start);
 }
 
 // ---------------------------------------------------------------------------
@@ -599,16 +610,16 @@ FusedTmaPlan* make_fused_tma(const FusedArgs& a, const float* T_copy, char* err,
 
 void destroy_fused_tma(FusedTmaPlan* p) { delete p; }
 
-template <int N>
+template <int N, int SM>
 static void launch_tma_n(FusedTmaPlan* p, int output, float* L, cudaStream_t s) {
     const FusedGeom& g = p->base.g;
     size_t smem = (size_t)g.smem_floats * 4 + 1024;
-    set_smem_attr((const void*)fused_tma_kernel<N>, (int)smem);
-    fused_tma_kernel<N><<<g.nregions, fused_block_threads(g), smem, s>>>(p->maps, p->base, output, L);
+    set_smem_attr((const void*)fused_tma_kernel<N, SM>, (int)smem);
+    fused_tma_kernel<N, SM><<<g.nregions, fused_block_threads(g), smem, s>>>(p->maps, p->base, output, L);
 }
 
 size_t fused_batch_entry_bytes() { return sizeof(FusedBatchEntry); }
-int fused_batch_order(const FusedTmaPlan* p) { return p->base.g.N; }
+int fused_batch_order(const FusedTmaPlan* p) { return p->base.g.N + 8 * p->base.g.split0; }
 int fused_batch_ctas(const FusedTmaPlan* p) { return p->base.g.nregions; }
 int fused_batch_threads(const FusedTmaPlan* p) { return fused_block_threads(p->base.g); }
 size_t fused_batch_smem(const FusedTmaPlan* p) { return (size_t)p->base.g.smem_floats * 4 + 1024; }
@@ -622,27 +633,30 @@ void fused_batch_fill(void* entry, const FusedTmaPlan* p, int start) {
     e.start = start;
     std::memcpy(entry, &e, sizeof(e));
 }
-template <int N>
+template <int N, int SM>
 static void launch_batched_n(const void* entries, const int* block_entry, int grid, int threads, size_t smem,
                              cudaStream_t s) {
-    set_smem_attr((const void*)fused_tma_kernel_batched<N>, (int)smem);
-    fused_tma_kernel_batched<N><<<grid, threads, smem, s>>>(static_cast<const FusedBatchEntry*>(entries), block_entry);
+    set_smem_attr((const void*)fused_tma_kernel_batched<N, SM>, (int)smem);
+    fused_tma_kernel_batched<N, SM><<<grid, threads, smem, s>>>(static_cast<const FusedBatchEntry*>(entries), block_entry);
 }
-void launch_fused_batched(int N, const void* entries, const int* block_entry, int grid, int threads, size_t smem,
+// order = N + 8 split0 (fused_batch_order): every entry of one launch shares it
+void launch_fused_batched(int order, const void* entries, const int* block_entry, int grid, int threads, size_t smem,
                           cudaStream_t s) {
-    switch (N) {
-        case 2: launch_batched_n<2>(entries, block_entry, grid, threads, smem, s); break;
-        case 3: launch_batched_n<3>(entries, block_entry, grid, threads, smem, s); break;
-        case 4: launch_batched_n<4>(entries, block_entry, grid, threads, smem, s); break;
+    switch (order) {
+        case 2: launch_batched_n<2, 0>(entries, block_entry, grid, threads, smem, s); break;
+        case 3: launch_batched_n<3, 1>(entries, block_entry, grid, threads, smem, s); break;
+        case 4: launch_batched_n<4, 2>(entries, block_entry, grid, threads, smem, s); break;
+        case 8 + 3: launch_batched_n<3, 0>(entries, block_entry, grid, threads, smem, s); break;
+        case 8 + 4: launch_batched_n<4, 0>(entries, block_entry, grid, threads, smem, s); break;
         default: break;
     }
 }
 
 void launch_fused_tma(FusedTmaPlan* p, int output, float* L, cudaStream_t s) {
     switch (p->base.g.N) {
-        case 2: launch_tma_n<2>(p, output, L, s); break;
-        case 3: launch_tma_n<3>(p, output, L, s); break;
-        case 4: launch_tma_n<4>(p, output, L, s); break;
+        case 2: launch_tma_n<2, 0>(p, output, L, s); break;
+        case 3: if (p->base.g.split0) launch_tma_n<3, 0>(p, output, L, s); else launch_tma_n<3, 1>(p, output, L, s); break;
+        case 4: if (p->base.g.split0) launch_tma_n<4, 0>(p, output, L, s); else launch_tma_n<4, 2>(p, output, L, s); break;
         default: break;
     }
 }

@@ -308,6 +308,8 @@ struct FusedGeom {
     // TMA-pipelined variant (two stages of [Xs | As_n | Ws_n], see fused_tma.cu)
     int tma;                             // 1 when the TMA kernel is used
     int nthreads;                        // B / 8
+    int split0;                          // 1: a thread's two element groups lie B / 2 apart
+                                         // (mode 0), not b_{N-2} / 2 apart along mode N-2
     int stage_floats;                    // floats per stage
     int xs_off;                          // element tiles (T, E, G_0..G_{N-1}) inside a stage
     uint32_t stage_tx_bytes;             // bytes one stage's TMA loads deliver
@@ -379,12 +381,12 @@ void launch_finalize_batched(const FinBatchEntry* e, const int* block_entry, int
 void launch_vrot_batched(int rb, bool v4, const VrotBatchEntry* e, const int* block_entry, int grid, cudaStream_t s);
 // bulk-copy kernels: entries are opaque here (filled by their files)
 size_t fused_batch_entry_bytes();
-int fused_batch_order(const FusedTmaPlan* p);
+int fused_batch_order(const FusedTmaPlan* p);   // N + 8 split0: one kernel per value
 int fused_batch_ctas(const FusedTmaPlan* p);
 int fused_batch_threads(const FusedTmaPlan* p);
 size_t fused_batch_smem(const FusedTmaPlan* p);
 void fused_batch_fill(void* entry, const FusedTmaPlan* p, int start);
-void launch_fused_batched(int N, const void* entries, const int* block_entry, int grid, int threads, size_t smem,
+void launch_fused_batched(int order, const void* entries, const int* block_entry, int grid, int threads, size_t smem,
                           cudaStream_t s);
 size_t apass_batch_entry_bytes();
 int apass_batch_rp(const ApassTmaPlan* p);

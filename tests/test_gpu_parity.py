@@ -115,6 +115,9 @@ def test_cube50_workload_fixed_and_converged(env):
     # 12- or 20-row Vrot, with more split-K slices than at full height
     ((40, 36, 32), (3, 3, 3), (12, 12, 12)),
     ((64, 48, 40), (4, 4, 4), (20, 20, 20)),
+    # a short mode before the last (tile 32 x 4 x 8): a thread's two element
+    # groups lie half a tile apart along mode 0 instead of along mode 1
+    ((48, 6, 24), (3, 2, 3), (6, 4, 6)),
 ])
 def test_shapes_match_oracle(env, dims, tucker, ranks):
     pr = synth.planted(dims, tucker, 0.1, 3, scale="std", amp=5.0)
