@@ -105,7 +105,7 @@ __device__ __forceinline__ void fused_tma_body(const FusedTmaMaps& tm, const Fus
         te[n] = (int64_t)(q[n] + 1) * g.nt[n] / g.Q[n];
         ntile *= te[n] - ts[n];
     }
-    // odometer over the region's tiles (C order), advanced by the issuing thread
+    // odometer over the region's tiles (C order), advanced by the producer lane
     int tc[N];
 #pragma unroll
     for (int n = 0; n < N; ++n) tc[n] = (int)ts[n];
